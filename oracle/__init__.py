@@ -1,0 +1,313 @@
+"""CPU oracle for population annealing of the 2D Ising ferromagnet (arXiv:2102.06611).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+``cpu_baseline`` / ``--impl reference`` leg may import this package.  The product path
+(``paper_2102_06611_gb300``) never imports it and shares no code with it.
+
+The arithmetic lives in plain C (``pa_oracle.c``, ``exact_ising.c``), built with gcc
+and ``-ffp-contract=off`` so that every binary64 multiply and add is rounded on its own.
+This module only marshals arguments through ctypes and adds nothing to the method.
+
+Parity pins (``tests/test_oracle_*.py``):
+  * Philox4x32-10: the published known-answer vectors of Salmon et al. (SC'11).
+  * ``exp``: <= 1 ulp against libm and against a 60-digit decimal reference.
+  * energies: ground state, antiferromagnetic state, stripes, single flips.
+  * Metropolis sweep: level distribution at L=4 against brute-force Boltzmann weights.
+  * Q_i / free energy: ln Z from enumeration, transfer matrix and Kaufman's closed form.
+  * copy numbers: mean equals tau_hat (Sec. II), Poisson pmf chi-square.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborapa.so")
+_SOURCES = ["pa_oracle.c", "exact_ising.c"]
+_lock = threading.Lock()
+_lib = None
+
+STREAM_INIT, STREAM_SWEEP, STREAM_RESAMPLE, STREAM_POISSON = 0, 1, 2, 3
+NEAREST, POISSON = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (no FMA contraction, -O2)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if not force and os.path.exists(_LIB_PATH):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(_LIB_PATH) >= newest:
+            return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("lnQ", ctypes.c_double), ("S", ctypes.c_double),
+                ("kmin", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("R_new", ctypes.c_int64)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            P = ctypes.POINTER
+            u32p, i32p, i64p, u64p, i8p, dp = (P(ctypes.c_uint32), P(ctypes.c_int32),
+                                                P(ctypes.c_int64), P(ctypes.c_uint64),
+                                                P(ctypes.c_int8), P(ctypes.c_double))
+            vp = ctypes.c_void_p
+            sig = {
+                "orc_philox4x32_10": (None, [u32p, u32p, u32p]),
+                "orc_exp": (ctypes.c_double, [ctypes.c_double]),
+                "orc_metropolis_threshold": (ctypes.c_uint64, [ctypes.c_double]),
+                "orc_energy_mag": (None, [ctypes.c_int, i8p, i32p, i32p]),
+                "orc_hash": (ctypes.c_uint64, [ctypes.c_int, i8p]),
+                "orc_pack": (None, [ctypes.c_int, i8p, u32p]),
+                "orc_unpack": (None, [ctypes.c_int, u32p, i8p]),
+                "orc_init_replica": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, i8p]),
+                "orc_sweep_replica": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                             ctypes.c_uint32, ctypes.c_double, ctypes.c_int, i8p]),
+                "orc_poisson": (ctypes.c_int64, [ctypes.c_double, ctypes.c_uint64,
+                                                 ctypes.c_uint32, ctypes.c_uint32]),
+                "orc_resample_levels": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                                       i32p, ctypes.c_double, ctypes.c_double,
+                                                       ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                                       ctypes.c_int64, i32p, P(_Info)]),
+                "orc_pa_create": (vp, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_uint64, ctypes.c_int]),
+                "orc_pa_destroy": (None, [vp]),
+                "orc_pa_init": (None, [vp]),
+                "orc_pa_resample": (ctypes.c_int, [vp, ctypes.c_double]),
+                "orc_pa_sweep": (None, [vp, ctypes.c_int]),
+                "orc_pa_observables": (None, [vp, dp, i64p]),
+                "orc_pa_R": (ctypes.c_int64, [vp]),
+                "orc_pa_R_prev": (ctypes.c_int64, [vp]),
+                "orc_pa_status": (ctypes.c_int, [vp]),
+                "orc_pa_sum_lnQ": (ctypes.c_double, [vp]),
+                "orc_pa_histogram": (None, [vp, i32p]),
+                "orc_pa_hashes": (None, [vp, u64p]),
+                "orc_pa_get": (None, [vp, i32p, i32p, i32p]),
+                "orc_pa_counts": (None, [vp, i32p]),
+                "orc_pa_spins": (None, [vp, ctypes.c_int64, ctypes.c_int64, i8p]),
+                "orc_pa_set": (ctypes.c_int, [vp, ctypes.c_int64, i8p, i32p, ctypes.c_uint32,
+                                              ctypes.c_double, ctypes.c_double]),
+                "orc_bruteforce": (ctypes.c_int, [ctypes.c_int, i64p, i64p, i64p]),
+                "orc_transfer_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
+                "orc_kaufman_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
+                "orc_kaufman_thermo": (None, [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+# ----------------------------------------------------------------------------- primitives
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                            _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def exp(x: float) -> float:
+    return lib().orc_exp(float(x))
+
+
+def metropolis_threshold(y: float) -> int:
+    return int(lib().orc_metropolis_threshold(float(y)))
+
+
+def energy_mag(L: int, s: np.ndarray):
+    s = np.ascontiguousarray(s, dtype=np.int8).reshape(L * L)
+    E, M = ctypes.c_int32(), ctypes.c_int32()
+    lib().orc_energy_mag(L, _ptr(s, ctypes.c_int8), ctypes.byref(E), ctypes.byref(M))
+    return E.value, M.value
+
+
+def replica_hash(L: int, s: np.ndarray) -> int:
+    s = np.ascontiguousarray(s, dtype=np.int8).reshape(L * L)
+    return int(lib().orc_hash(L, _ptr(s, ctypes.c_int8)))
+
+
+def pack(L: int, s: np.ndarray) -> np.ndarray:
+    s = np.ascontiguousarray(s, dtype=np.int8).reshape(L * L)
+    out = np.zeros(L * ((L + 31) // 32), dtype=np.uint32)
+    lib().orc_pack(L, _ptr(s, ctypes.c_int8), _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def unpack(L: int, words: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    s = np.zeros(L * L, dtype=np.int8)
+    lib().orc_unpack(L, _ptr(w, ctypes.c_uint32), _ptr(s, ctypes.c_int8))
+    return s
+
+
+def init_replica(L: int, seed: int, j: int) -> np.ndarray:
+    s = np.zeros(L * L, dtype=np.int8)
+    lib().orc_init_replica(L, seed, j, _ptr(s, ctypes.c_int8))
+    return s
+
+
+def sweep_replica(L: int, seed: int, step: int, slot: int, beta: float, theta: int,
+                  s: np.ndarray) -> np.ndarray:
+    out = np.array(s, dtype=np.int8, copy=True).reshape(L * L)
+    lib().orc_sweep_replica(L, seed, step, slot, float(beta), int(theta),
+                            _ptr(out, ctypes.c_int8))
+    return out
+
+
+def poisson(lam: float, seed: int, j: int, step: int) -> int:
+    return int(lib().orc_poisson(float(lam), seed, j, step))
+
+
+def resample_levels(L, R_target, levels, beta_prev, beta_new, step, seed, kind, capacity):
+    """Step 2 of the method from given levels: returns (status, counts, lnQ, S, kmin, R_new)."""
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    counts = np.zeros(len(lv), dtype=np.int32)
+    info = _Info()
+    st = lib().orc_resample_levels(L, R_target, len(lv), _ptr(lv, ctypes.c_int32),
+                                   float(beta_prev), float(beta_new), step, seed, kind,
+                                   capacity, _ptr(counts, ctypes.c_int32), ctypes.byref(info))
+    return st, counts, info.lnQ, info.S, info.kmin, info.R_new
+
+
+# ----------------------------------------------------------------------------- exact
+def bruteforce(L: int):
+    N = L * L
+    g = np.zeros(N + 1, np.int64)
+    sa = np.zeros(N + 1, np.int64)
+    s2 = np.zeros(N + 1, np.int64)
+    if lib().orc_bruteforce(L, _ptr(g, ctypes.c_int64), _ptr(sa, ctypes.c_int64),
+                            _ptr(s2, ctypes.c_int64)):
+        raise ValueError("lattice too large to enumerate")
+    return g, sa, s2
+
+
+def transfer_lnZ(L: int, beta: float) -> float:
+    return lib().orc_transfer_lnZ(L, float(beta))
+
+
+def kaufman_lnZ(L: int, beta: float) -> float:
+    return lib().orc_kaufman_lnZ(L, float(beta))
+
+
+def kaufman_thermo(L: int, beta: float, h: float = 2e-4):
+    """(<E>, C per spin, ln Z) of the periodic L x L lattice from Kaufman's closed form."""
+    out = np.zeros(3)
+    lib().orc_kaufman_thermo(L, float(beta), float(h), _ptr(out, ctypes.c_double))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+# ----------------------------------------------------------------------------- full PA
+OBS_FIELDS = ["beta", "dbeta", "R", "e", "C", "m", "m2", "chi", "lnQ", "minus_betaF",
+              "families", "rho_t", "step", "theta"]
+
+
+class PA:
+    """Plain single-threaded population annealing run (Sec. II steps 1-5)."""
+
+    def __init__(self, L: int, R: int, seed: int, kind: int = NEAREST, capacity: int | None = None):
+        if capacity is None:
+            capacity = default_capacity(R)
+        self.L, self.N, self.R_target, self.capacity = L, L * L, R, capacity
+        self._h = lib().orc_pa_create(L, R, capacity, seed, kind)
+        if not self._h:
+            raise ValueError("invalid oracle configuration")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_pa_destroy(h)
+            self._h = None
+
+    def init(self):
+        lib().orc_pa_init(self._h)
+
+    def resample(self, beta_new: float) -> int:
+        return lib().orc_pa_resample(self._h, float(beta_new))
+
+    def sweep(self, theta: int):
+        lib().orc_pa_sweep(self._h, int(theta))
+
+    @property
+    def R(self) -> int:
+        return int(lib().orc_pa_R(self._h))
+
+    @property
+    def R_prev(self) -> int:
+        return int(lib().orc_pa_R_prev(self._h))
+
+    def observables(self) -> dict:
+        out = np.zeros(14)
+        isums = np.zeros(6, np.int64)
+        lib().orc_pa_observables(self._h, _ptr(out, ctypes.c_double), _ptr(isums, ctypes.c_int64))
+        d = dict(zip(OBS_FIELDS, out.tolist()))
+        d["sums"] = isums
+        return d
+
+    def histogram(self) -> np.ndarray:
+        h = np.zeros(self.N + 1, np.int32)
+        lib().orc_pa_histogram(self._h, _ptr(h, ctypes.c_int32))
+        return h
+
+    def hashes(self) -> np.ndarray:
+        out = np.zeros(self.R, np.uint64)
+        lib().orc_pa_hashes(self._h, _ptr(out, ctypes.c_uint64))
+        return out
+
+    def state(self):
+        R = self.R
+        E, M, F = (np.zeros(R, np.int32) for _ in range(3))
+        lib().orc_pa_get(self._h, _ptr(E, ctypes.c_int32), _ptr(M, ctypes.c_int32),
+                         _ptr(F, ctypes.c_int32))
+        return E, M, F
+
+    def counts(self) -> np.ndarray:
+        out = np.zeros(self.R_prev, np.int32)
+        lib().orc_pa_counts(self._h, _ptr(out, ctypes.c_int32))
+        return out
+
+    def spins(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = self.R - first
+        out = np.zeros(count * self.N, np.int8)
+        lib().orc_pa_spins(self._h, first, count, _ptr(out, ctypes.c_int8))
+        return out.reshape(count, self.L, self.L)
+
+    def set_population(self, spins: np.ndarray, fam: np.ndarray, step: int, beta: float,
+                       sum_lnQ: float = 0.0):
+        s = np.ascontiguousarray(spins, dtype=np.int8)
+        f = np.ascontiguousarray(fam, dtype=np.int32)
+        R = len(f)
+        if lib().orc_pa_set(self._h, R, _ptr(s, ctypes.c_int8), _ptr(f, ctypes.c_int32),
+                            step, float(beta), float(sum_lnQ)):
+            raise ValueError("population does not fit")
+
+
+def default_capacity(R: int) -> int:
+    """Buffer capacity for a fluctuating population: R + ceil(10 sqrt R) + 64."""
+    import math
+    return R + int(math.ceil(10.0 * math.sqrt(R))) + 64

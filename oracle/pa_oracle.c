@@ -1,0 +1,576 @@
+/*
+ * pa_oracle.c -- plain, slow, single-threaded CPU population annealing (PA) for the
+ * 2D Ising ferromagnet (J = 1, L x L, periodic), written from Weigel, Barash, Shchur,
+ * Janke, "Understanding population annealing Monte Carlo simulations" (arXiv:2102.06611).
+ *
+ * TEST INFRASTRUCTURE.  This file is the oracle the CUDA path is checked against.  Only
+ * tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference leg may load
+ * it.  It shares no code, header or constant generator with the CUDA library; where a
+ * definition must agree bit for bit (Philox4x32-10, the deterministic exp, the random-
+ * number keying, the decision rules) it is written here independently from the same
+ * published definition.
+ *
+ * Spins are one int8 per site (+1 / -1), replica-major, row-major: s[j*N + r*L + c].
+ * Everything is done site by site in the paper's order; nothing is blocked or fused.
+ *
+ * Paper passages followed:
+ *   Sec. II steps 1-5 (population annealing loop), Eq. (Q) normalisation Q_i,
+ *   Eq. (taus) rescaled copy means, Eq. (resampling-factors) nearest-integer copies,
+ *   Poisson resampling (Sec. II, Machta's variant), Eq. (hamiltonian), Sec. III
+ *   observables e, C_V, m, chi, Sec. V families and Eq. (rhot), Sec. VII
+ *   Eq. (free-emergy-estimator) with ln Z_0 = L^d ln 2.
+ *
+ * Parity of the pieces not printed in the paper is pinned by tests/test_oracle_*.py:
+ * Philox by the published known-answer vectors, orc_exp against libm and a
+ * 60-digit reference, the sweep by brute-force Boltzmann distributions at L = 4, the
+ * Q_i / free-energy path by the exact finite-lattice partition function.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
+ * 1, 2, 3", SC'11).  Ten rounds; each round multiplies counter words 0 and 2 by the
+ * two round multipliers (full 64-bit products), and the key is bumped by the two Weyl
+ * constants between rounds.
+ * ---------------------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ x1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ x3 ^ k1;
+        uint32_t n3 = lo0;
+        x0 = n0; x1 = n1; x2 = n2; x3 = n3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Random-number streams: the tag sits in the top 4 bits of counter word 2. */
+enum { STREAM_INIT = 0, STREAM_SWEEP = 1, STREAM_RESAMPLE = 2, STREAM_POISSON = 3 };
+
+static uint32_t philox_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                            uint32_t c3, int lane)
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[lane];
+}
+
+/* ------------------------------------------------------------------------------------
+ * Deterministic exp (Cody & Waite argument reduction, then the Taylor series of e^r
+ * to degree 13 in Horner form).  x = k ln2 + r with k = rint(x / ln2), |r| <= ln2/2;
+ * ln2 is split as LN2_HI (32 significant bits, so k * LN2_HI is exact) plus LN2_LO.
+ * e^r = sum_{n<=13} r^n / n!; the truncation error r^14/14! < 5e-18 is below half an
+ * ulp.  Each multiply and add is a separate IEEE binary64 operation (the file is built
+ * with -ffp-contract=off), so the result is a fixed function of x.
+ * ---------------------------------------------------------------------------------- */
+#define ORC_LN2_HI 0x1.62e42feep-1
+#define ORC_LN2_LO 0x1.a39ef35793c76p-33
+#define ORC_INV_LN2 0x1.71547652b82fep+0
+
+double orc_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.5) return HUGE_VAL;
+    if (x < -745.5) return 0.0;
+    double k = rint(x * ORC_INV_LN2);
+    double r = (x - k * ORC_LN2_HI) - k * ORC_LN2_LO;
+    /* 1/n! for n = 13 .. 1; n! is an exact double for n <= 18, so each coefficient is
+       the correctly rounded quotient. */
+    double p = 1.0 / 6227020800.0;          /* 1/13! */
+    p = p * r + 1.0 / 479001600.0;          /* 1/12! */
+    p = p * r + 1.0 / 39916800.0;           /* 1/11! */
+    p = p * r + 1.0 / 3628800.0;            /* 1/10! */
+    p = p * r + 1.0 / 362880.0;             /* 1/9!  */
+    p = p * r + 1.0 / 40320.0;              /* 1/8!  */
+    p = p * r + 1.0 / 5040.0;               /* 1/7!  */
+    p = p * r + 1.0 / 720.0;                /* 1/6!  */
+    p = p * r + 1.0 / 120.0;                /* 1/5!  */
+    p = p * r + 1.0 / 24.0;                 /* 1/4!  */
+    p = p * r + 1.0 / 6.0;                  /* 1/3!  */
+    p = p * r + 0.5;                        /* 1/2!  */
+    p = p * r + 1.0;                        /* 1/1!  */
+    p = p * r + 1.0;                        /* 1/0!  */
+    return ldexp(p, (int)k);
+}
+
+/* Metropolis threshold floor(exp(-y) * 2^32) for y >= 0; 2^32 means "always". */
+uint64_t orc_metropolis_threshold(double y)
+{
+    double p = orc_exp(-y);
+    return (uint64_t)floor(p * 4294967296.0);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Lattice helpers.  E = -sum over the 2N nearest-neighbour bonds of s_i s_j
+ * (Eq. hamiltonian with J = 1), M = sum of spins.  The energy level is
+ * k = (E + 2N) / 4 in [0, N] (E = 2 n_anti - 2N and n_anti is even on the torus).
+ * ---------------------------------------------------------------------------------- */
+static inline int site(int L, int r, int c)
+{
+    r = (r + L) % L;
+    c = (c + L) % L;
+    return r * L + c;
+}
+
+void orc_energy_mag(int L, const int8_t *s, int32_t *E_out, int32_t *M_out)
+{
+    int E = 0, M = 0;
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c < L; ++c) {
+            int si = s[site(L, r, c)];
+            E -= si * s[site(L, r, c + 1)];
+            E -= si * s[site(L, r + 1, c)];
+            M += si;
+        }
+    *E_out = E;
+    *M_out = M;
+}
+
+/* FNV-1a 64 of the canonical packed bytes of one replica: for each row, ceil(L/32)
+   little-endian uint32 words, bit b of word w set iff the spin at column 32w + b is +1. */
+uint64_t orc_hash(int L, const int8_t *s)
+{
+    uint64_t h = 0xcbf29ce484222325ull;
+    int words = (L + 31) / 32;
+    for (int r = 0; r < L; ++r)
+        for (int w = 0; w < words; ++w) {
+            uint32_t v = 0;
+            for (int b = 0; b < 32; ++b) {
+                int c = 32 * w + b;
+                if (c < L && s[r * L + c] > 0) v |= (1u << b);
+            }
+            for (int byte = 0; byte < 4; ++byte) {
+                h ^= (uint64_t)((v >> (8 * byte)) & 0xffu);
+                h *= 0x100000001b3ull;
+            }
+        }
+    return h;
+}
+
+/* Canonical packed form (same bytes as hashed) <-> int8 spins. */
+void orc_pack(int L, const int8_t *s, uint32_t *out)
+{
+    int words = (L + 31) / 32;
+    for (int r = 0; r < L; ++r)
+        for (int w = 0; w < words; ++w) {
+            uint32_t v = 0;
+            for (int b = 0; b < 32; ++b) {
+                int c = 32 * w + b;
+                if (c < L && s[r * L + c] > 0) v |= (1u << b);
+            }
+            out[r * words + w] = v;
+        }
+}
+
+void orc_unpack(int L, const uint32_t *in, int8_t *s)
+{
+    int words = (L + 31) / 32;
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c < L; ++c)
+            s[r * L + c] = ((in[r * words + c / 32] >> (c % 32)) & 1u) ? 1 : -1;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Step 1 (Sec. II): simple sampling at beta_0 = 0.  Site n = r L + c of replica j takes
+ * bit (n mod 32) of the 32-bit word number n / 32 of the INIT stream: word w is lane
+ * (w mod 4) of Philox(ctr = (w / 4, j, INIT << 28, 0)); a set bit is s = +1.
+ * ---------------------------------------------------------------------------------- */
+void orc_init_replica(int L, uint64_t seed, uint32_t j, int8_t *s)
+{
+    int N = L * L;
+    for (int n = 0; n < N; ++n) {
+        uint32_t w = (uint32_t)n >> 5;
+        uint32_t x = philox_word(seed, w >> 2, j, (uint32_t)STREAM_INIT << 28, 0, (int)(w & 3));
+        s[n] = ((x >> (n & 31)) & 1u) ? 1 : -1;
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Step 3 (Sec. II): theta rounds of single-spin Metropolis at inverse temperature beta,
+ * in checkerboard order (the paper's GPU variant): within sweep t, first every site with
+ * (r + c) even (colour 0), then every site with (r + c) odd (colour 1).  Sites of one
+ * colour do not interact, so visiting them one after another is the same as updating
+ * them together.  Acceptance is min(1, exp(-beta dE)) with dE = 4a - 8, a = number of
+ * aligned neighbours: a <= 2 always flips; a = 3 flips iff x < floor(e^{-4 beta} 2^32);
+ * a = 4 flips iff x < floor(e^{-8 beta} 2^32).
+ * Random word x for site (r, c) of colour q in sweep t of step i, replica slot j:
+ * with p = c / 2 (index of the site among the L/2 colour-q sites of row r),
+ * x = lane (p mod 4) of Philox(ctr = (r * 16 + p / 4, j, (SWEEP << 28) | (2t + q), i)).
+ * ---------------------------------------------------------------------------------- */
+void orc_sweep_replica(int L, uint64_t seed, uint32_t step, uint32_t slot, double beta,
+                       int theta, int8_t *s)
+{
+    uint64_t T4 = orc_metropolis_threshold(4.0 * beta);
+    uint64_t T8 = orc_metropolis_threshold(8.0 * beta);
+    for (int t = 0; t < theta; ++t)
+        for (int q = 0; q < 2; ++q)
+            for (int r = 0; r < L; ++r)
+                for (int c = 0; c < L; ++c) {
+                    if (((r + c) & 1) != q) continue;
+                    int si = s[site(L, r, c)];
+                    int a = (s[site(L, r - 1, c)] == si) + (s[site(L, r + 1, c)] == si) +
+                            (s[site(L, r, c - 1)] == si) + (s[site(L, r, c + 1)] == si);
+                    int p = c / 2;
+                    uint32_t x = philox_word(seed, (uint32_t)(r * 16 + p / 4), slot,
+                                             ((uint32_t)STREAM_SWEEP << 28) | (uint32_t)(2 * t + q),
+                                             step, p % 4);
+                    int flip;
+                    if (a <= 2) flip = 1;
+                    else if (a == 3) flip = (uint64_t)x < T4;
+                    else flip = (uint64_t)x < T8;
+                    if (flip) s[site(L, r, c)] = (int8_t)(-si);
+                }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Step 2 (Sec. II): reweighting and resampling from beta_prev to beta_new given the
+ * energy levels of the R_prev current replicas (energies BEFORE resampling, as the
+ * paper stresses after Eq. boltzmann-weight).
+ *   h_k          histogram of levels, E_k = 4k - 2N
+ *   E_ref        energy of the lowest occupied level; w_k = exp(-dbeta (E_k - E_ref))
+ *   S            sum over occupied k in ascending order of h_k w_k
+ *   ln Q_i       = -dbeta E_ref + ln(S / R_prev)          (Eq. Q, shifted by E_ref)
+ *   tau_hat_k    = R w_k / S = (R / R_prev) exp(-dbeta E_k) / Q_i   (Eq. taus)
+ * Nearest-integer copies (Eq. resampling-factors): with u = x 2^-32 and x word 0 of
+ * Philox(ctr = (j, 0, RESAMPLE << 28, i)), r_j = floor(tau) if u > frac(tau), else
+ * floor(tau) + 1; equivalently r_j = floor(tau) + [x <= floor(frac(tau) 2^32)].
+ * Poisson copies: r_j ~ Poisson(tau_hat) by sequential inversion (see orc_poisson).
+ * Children of parent j fill the next r_j slots in parent order (tree order).
+ * ---------------------------------------------------------------------------------- */
+#define ORC_POISSON_CHUNK 32.0
+#define ORC_POISSON_KMAX 1000
+
+/* Poisson(lambda) by inversion of the cumulative distribution (sequential search,
+   Devroye 1986, Ch. X.3): u uniform in [0,1) with 53 bits, p_0 = e^{-mu},
+   p_k = p_{k-1} mu / k, return the first k with u < F_k.  For lambda >= 32 the draw is
+   the sum of m = ceil(lambda / 32) independent Poisson(lambda / m) draws; chunk c uses
+   Philox(ctr = (j, c, POISSON << 28, i)), u = (x0 >> 5) 2^-27 + (x1 >> 6) 2^-53. */
+int64_t orc_poisson(double lambda, uint64_t seed, uint32_t j, uint32_t step)
+{
+    if (!(lambda > 0.0)) return 0;
+    int64_t m = 1;
+    if (lambda >= ORC_POISSON_CHUNK) m = (int64_t)ceil(lambda / ORC_POISSON_CHUNK);
+    double mu = lambda / (double)m;
+    int64_t total = 0;
+    for (int64_t chunk = 0; chunk < m; ++chunk) {
+        uint32_t ctr[4] = {j, (uint32_t)chunk, (uint32_t)STREAM_POISSON << 28, step};
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t out[4];
+        orc_philox4x32_10(ctr, key, out);
+        double u = ((double)(out[0] >> 5) * 67108864.0 + (double)(out[1] >> 6)) *
+                   (1.0 / 9007199254740992.0);
+        double p = orc_exp(-mu);
+        double F = p;
+        int64_t k = 0;
+        while (u >= F && k < ORC_POISSON_KMAX) {
+            k = k + 1;
+            p = (p * mu) / (double)k;
+            F = F + p;
+        }
+        total += k;
+    }
+    return total;
+}
+
+typedef struct {
+    double lnQ;        /* ln Q_i of this step */
+    double S;          /* sum_k h_k w_k */
+    int32_t kmin;      /* lowest occupied level */
+    int32_t pad;
+    int64_t R_new;     /* new population size */
+} orc_resample_info;
+
+/* Status codes shared in meaning (not in code) with the library: 0 ok, 3 capacity,
+   6 numeric (empty population). */
+int orc_resample_levels(int L, int64_t R_target, int64_t R_prev, const int32_t *level,
+                        double beta_prev, double beta_new, uint32_t step, uint64_t seed,
+                        int kind, int64_t capacity, int32_t *counts_out,
+                        orc_resample_info *info)
+{
+    int N = L * L;
+    int64_t *h = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    double *w = (double *)calloc((size_t)N + 1, sizeof(double));
+    double *tau = (double *)calloc((size_t)N + 1, sizeof(double));
+    int64_t *fl = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    uint64_t *thr = (uint64_t *)calloc((size_t)N + 1, sizeof(uint64_t));
+    for (int64_t j = 0; j < R_prev; ++j) h[level[j]] += 1;
+    int kmin = 0;
+    while (kmin <= N && h[kmin] == 0) ++kmin;
+    double dbeta = beta_new - beta_prev;
+    int Eref = 4 * kmin - 2 * N;
+    for (int k = 0; k <= N; ++k) {
+        if (h[k] == 0) continue;
+        int Ek = 4 * k - 2 * N;
+        w[k] = orc_exp(-(dbeta * (double)(Ek - Eref)));
+    }
+    double S = 0.0;
+    for (int k = 0; k <= N; ++k)
+        if (h[k] != 0) S = S + (double)h[k] * w[k];
+    double lnQ = -(dbeta * (double)Eref) + log(S / (double)R_prev);
+    for (int k = 0; k <= N; ++k) {
+        if (h[k] == 0) continue;
+        tau[k] = ((double)R_target * w[k]) / S;
+        double f = floor(tau[k]);
+        fl[k] = (int64_t)f;
+        thr[k] = (uint64_t)floor((tau[k] - f) * 4294967296.0);
+    }
+    int64_t R_new = 0;
+    for (int64_t j = 0; j < R_prev; ++j) {
+        int k = level[j];
+        int64_t r;
+        if (kind == 0) {
+            uint32_t x = philox_word(seed, (uint32_t)j, 0, (uint32_t)STREAM_RESAMPLE << 28, step, 0);
+            r = fl[k] + (((uint64_t)x <= thr[k]) ? 1 : 0);
+        } else {
+            r = orc_poisson(tau[k], seed, (uint32_t)j, step);
+        }
+        counts_out[j] = (int32_t)r;
+        R_new += r;
+    }
+    info->lnQ = lnQ;
+    info->S = S;
+    info->kmin = kmin;
+    info->R_new = R_new;
+    free(h); free(w); free(tau); free(fl); free(thr);
+    if (R_new > capacity) return 3;
+    if (R_new == 0) return 6;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * The population: a full PA run held on the host.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+    int L, N, kind;
+    int64_t R_target, capacity, R;
+    uint64_t seed;
+    uint32_t step;          /* index i of the current temperature beta_i */
+    double beta, dbeta, lnQ, sum_lnQ;
+    int theta_last;
+    int8_t *s;              /* capacity * N */
+    int8_t *s_next;
+    int32_t *E, *M, *fam, *E_next, *M_next, *fam_next;
+    int32_t *counts;        /* copy numbers of the last resampling, R_prev entries */
+    int64_t R_prev;
+    int status;
+} orc_pa;
+
+void orc_pa_destroy(orc_pa *p);
+
+orc_pa *orc_pa_create(int L, int64_t R, int64_t capacity, uint64_t seed, int kind)
+{
+    if (L < 4 || (L % 2) != 0 || L > 128 || R < 1 || capacity < R) return NULL;
+    orc_pa *p = (orc_pa *)calloc(1, sizeof(orc_pa));
+    p->L = L; p->N = L * L; p->kind = kind;
+    p->R_target = R; p->capacity = capacity; p->seed = seed;
+    size_t cap = (size_t)capacity;
+    p->s = (int8_t *)malloc(cap * (size_t)p->N);
+    p->s_next = (int8_t *)malloc(cap * (size_t)p->N);
+    p->E = (int32_t *)malloc(cap * 4); p->M = (int32_t *)malloc(cap * 4);
+    p->fam = (int32_t *)malloc(cap * 4);
+    p->E_next = (int32_t *)malloc(cap * 4); p->M_next = (int32_t *)malloc(cap * 4);
+    p->fam_next = (int32_t *)malloc(cap * 4);
+    p->counts = (int32_t *)malloc(cap * 4);
+    if (!p->s || !p->s_next || !p->E || !p->M || !p->fam || !p->E_next || !p->M_next ||
+        !p->fam_next || !p->counts) {
+        orc_pa_destroy(p);
+        return NULL;
+    }
+    return p;
+}
+
+void orc_pa_destroy(orc_pa *p)
+{
+    if (!p) return;
+    free(p->s); free(p->s_next); free(p->E); free(p->M); free(p->fam);
+    free(p->E_next); free(p->M_next); free(p->fam_next); free(p->counts);
+    free(p);
+}
+
+static void measure_all(orc_pa *p)
+{
+    for (int64_t j = 0; j < p->R; ++j)
+        orc_energy_mag(p->L, p->s + (size_t)j * p->N, &p->E[j], &p->M[j]);
+}
+
+/* Step 1: R_0 = R replicas by simple sampling at beta_0 = 0, family id = own index. */
+void orc_pa_init(orc_pa *p)
+{
+    p->R = p->R_target;
+    p->R_prev = 0;
+    p->step = 0;
+    p->beta = 0.0; p->dbeta = 0.0; p->lnQ = 0.0; p->sum_lnQ = 0.0;
+    p->theta_last = 0;
+    p->status = 0;
+    for (int64_t j = 0; j < p->R; ++j) {
+        orc_init_replica(p->L, p->seed, (uint32_t)j, p->s + (size_t)j * p->N);
+        p->fam[j] = (int32_t)j;
+    }
+    measure_all(p);
+}
+
+/* Step 2: resample from the current beta to beta_new; step index advances by one. */
+int orc_pa_resample(orc_pa *p, double beta_new)
+{
+    if (p->status) return p->status;
+    int N = p->N;
+    int32_t *level = (int32_t *)malloc((size_t)p->R * 4);
+    for (int64_t j = 0; j < p->R; ++j) level[j] = (p->E[j] + 2 * N) / 4;
+    orc_resample_info info;
+    uint32_t step = p->step + 1;
+    int st = orc_resample_levels(p->L, p->R_target, p->R, level, p->beta, beta_new, step,
+                                 p->seed, p->kind, p->capacity, p->counts, &info);
+    free(level);
+    if (st) { p->status = st; return st; }
+    int64_t slot = 0;
+    for (int64_t j = 0; j < p->R; ++j)
+        for (int32_t c = 0; c < p->counts[j]; ++c) {
+            memcpy(p->s_next + (size_t)slot * N, p->s + (size_t)j * N, (size_t)N);
+            p->E_next[slot] = p->E[j];
+            p->M_next[slot] = p->M[j];
+            p->fam_next[slot] = p->fam[j];
+            ++slot;
+        }
+    int8_t *ts = p->s; p->s = p->s_next; p->s_next = ts;
+    int32_t *t;
+    t = p->E; p->E = p->E_next; p->E_next = t;
+    t = p->M; p->M = p->M_next; p->M_next = t;
+    t = p->fam; p->fam = p->fam_next; p->fam_next = t;
+    p->R_prev = p->R;
+    p->R = info.R_new;
+    p->dbeta = beta_new - p->beta;
+    p->beta = beta_new;
+    p->step = step;
+    p->lnQ = info.lnQ;
+    p->sum_lnQ = p->sum_lnQ + info.lnQ;
+    return 0;
+}
+
+/* Step 3 then the measurement of step 4: theta sweeps of every replica at the current
+   beta, then energies and magnetisations. */
+void orc_pa_sweep(orc_pa *p, int theta)
+{
+    for (int64_t j = 0; j < p->R; ++j)
+        orc_sweep_replica(p->L, p->seed, p->step, (uint32_t)j, p->beta, theta,
+                          p->s + (size_t)j * p->N);
+    p->theta_last = theta;
+    measure_all(p);
+}
+
+/* Step 4: population averages (Sec. III) and the free energy (Sec. VII), all from exact
+   integer sums; formula order fixed.
+   out[0] beta, [1] dbeta, [2] R_i, [3] e, [4] C, [5] m, [6] m2, [7] chi, [8] lnQ,
+   [9] -beta F, [10] families f, [11] rho_t, [12] step, [13] theta.
+   isums[0] sum E, [1] sum E^2, [2] sum |M|, [3] sum M^2, [4] f, [5] sum size^2. */
+void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
+{
+    int64_t sE = 0, sE2 = 0, sAM = 0, sM2 = 0;
+    for (int64_t j = 0; j < p->R; ++j) {
+        int64_t e = p->E[j], m = p->M[j];
+        sE += e; sE2 += e * e;
+        sAM += (m < 0 ? -m : m);
+        sM2 += m * m;
+    }
+    /* families (Sec. V): sizes of runs of equal ids; ids stay sorted in tree order */
+    int64_t f = 0, s2 = 0, run = 0;
+    for (int64_t j = 0; j < p->R; ++j) {
+        if (j == 0 || p->fam[j] != p->fam[j - 1]) {
+            if (run) s2 += run * run;
+            run = 0;
+            ++f;
+        }
+        ++run;
+    }
+    if (run) s2 += run * run;
+    double Rd = (double)p->R, Nd = (double)p->N, b = p->beta;
+    double meanE = (double)sE / Rd;
+    double meanE2 = (double)sE2 / Rd;
+    double e = meanE / Nd;
+    double C = ((b * b) * (meanE2 - meanE * meanE)) / Nd;
+    double m = ((double)sAM / Rd) / Nd;
+    double m2 = ((double)sM2 / Rd) / (Nd * Nd);
+    double chi = (b * Nd) * (m2 - m * m);
+    double rho_t = (double)s2 / Rd;
+    double mbF = Nd * 0.6931471805599453094 + p->sum_lnQ;
+    out[0] = p->beta; out[1] = p->dbeta; out[2] = Rd; out[3] = e; out[4] = C;
+    out[5] = m; out[6] = m2; out[7] = chi; out[8] = p->lnQ; out[9] = mbF;
+    out[10] = (double)f; out[11] = rho_t; out[12] = (double)p->step;
+    out[13] = (double)p->theta_last;
+    if (isums) {
+        isums[0] = sE; isums[1] = sE2; isums[2] = sAM; isums[3] = sM2; isums[4] = f;
+        isums[5] = s2;
+    }
+}
+
+/* Accessors used by the tests. */
+int64_t orc_pa_R(const orc_pa *p) { return p->R; }
+int64_t orc_pa_R_prev(const orc_pa *p) { return p->R_prev; }
+int orc_pa_status(const orc_pa *p) { return p->status; }
+double orc_pa_sum_lnQ(const orc_pa *p) { return p->sum_lnQ; }
+
+void orc_pa_histogram(const orc_pa *p, int32_t *h)
+{
+    memset(h, 0, sizeof(int32_t) * (size_t)(p->N + 1));
+    for (int64_t j = 0; j < p->R; ++j) h[(p->E[j] + 2 * p->N) / 4] += 1;
+}
+
+void orc_pa_hashes(const orc_pa *p, uint64_t *out)
+{
+    for (int64_t j = 0; j < p->R; ++j) out[j] = orc_hash(p->L, p->s + (size_t)j * p->N);
+}
+
+void orc_pa_get(const orc_pa *p, int32_t *E, int32_t *M, int32_t *fam)
+{
+    for (int64_t j = 0; j < p->R; ++j) {
+        if (E) E[j] = p->E[j];
+        if (M) M[j] = p->M[j];
+        if (fam) fam[j] = p->fam[j];
+    }
+}
+
+void orc_pa_counts(const orc_pa *p, int32_t *out)
+{
+    for (int64_t j = 0; j < p->R_prev; ++j) out[j] = p->counts[j];
+}
+
+void orc_pa_spins(const orc_pa *p, int64_t first, int64_t count, int8_t *out)
+{
+    memcpy(out, p->s + (size_t)first * p->N, (size_t)count * p->N);
+}
+
+/* Replace the population (for stepwise replay from an externally produced state). */
+int orc_pa_set(orc_pa *p, int64_t R, const int8_t *spins, const int32_t *fam,
+               uint32_t step, double beta, double sum_lnQ)
+{
+    if (R < 1 || R > p->capacity) return 1;
+    p->R = R;
+    memcpy(p->s, spins, (size_t)R * p->N);
+    for (int64_t j = 0; j < R; ++j) p->fam[j] = fam[j];
+    p->step = step;
+    p->beta = beta;
+    p->sum_lnQ = sum_lnQ;
+    p->status = 0;
+    measure_all(p);
+    return 0;
+}

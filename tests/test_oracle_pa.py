@@ -1,0 +1,193 @@
+"""Pins of the oracle's population-annealing loop (Sec. II) against exact results.
+
+Statistical checks use fixed seeds and tolerances of several standard errors; the
+standard errors are taken from the family statistics (rho_t, Eq. rhot), which bound the
+loss of independent replicas through resampling.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+LN2 = math.log(2.0)
+
+
+def _levels_energy(L, E):
+    return (np.asarray(E) + 2 * L * L) // 4
+
+
+def test_beta0_population_closed_forms():
+    """At beta = 0 (simple sampling): <E> = 0, Var(E) = 2N (the paper's sigma_0^2 = z L^d/2
+    with z = 4), <M^2> = N, -beta F_0 = N ln 2 (Sec. VII)."""
+    L, R = 8, 60000
+    N = L * L
+    pa = oracle.PA(L, R, seed=17)
+    pa.init()
+    o = pa.observables()
+    E, M, fam = pa.state()
+    assert np.array_equal(fam, np.arange(R))
+    assert o["minus_betaF"] == N * LN2
+    assert abs(E.mean()) < 5 * math.sqrt(2 * N / R)
+    assert E.var() == pytest.approx(2 * N, rel=5 * math.sqrt(2.0 / R))
+    assert (M.astype(np.float64) ** 2).mean() == pytest.approx(N, rel=5 * math.sqrt(2.0 / R))
+    assert o["families"] == R and o["rho_t"] == 1.0
+
+
+def test_first_lnQ_estimates_exact_partition_ratio():
+    """Q_1 estimates Z(beta_1)/Z(0) (Eq. Q and the telescoping product of Sec. VII)."""
+    L, R, b1 = 4, 200000, 0.2
+    pa = oracle.PA(L, R, seed=5)
+    pa.init()
+    E, _, _ = pa.state()
+    st, counts, lnQ, S, kmin, R_new = oracle.resample_levels(L, R, _levels_energy(L, E), 0.0, b1,
+                                                             1, 5, oracle.NEAREST, oracle.default_capacity(R))
+    assert st == 0
+    exact = oracle.kaufman_lnZ(L, b1) - 16 * LN2
+    w = np.exp(-b1 * E.astype(float))
+    sigma = w.std() / math.sqrt(R) / w.mean()
+    assert abs(lnQ - exact) < 5 * sigma
+    # same quantity computed directly from the energies
+    assert lnQ == pytest.approx(math.log(w.mean()), rel=1e-12, abs=1e-13)
+
+
+def test_thermodynamic_integration_limit():
+    """For small steps ln Q -> -dbeta <E> (Sec. VII, thermodynamic-integration limit)."""
+    L, R = 8, 20000
+    pa = oracle.PA(L, R, seed=8)
+    pa.init()
+    pa.resample(0.3)
+    pa.sweep(10)
+    E, _, _ = pa.state()
+    for db in (1e-4, 1e-5):
+        _, _, lnQ, _, _, _ = oracle.resample_levels(L, R, _levels_energy(L, E), 0.3, 0.3 + db, 2, 8,
+                                                    oracle.NEAREST, oracle.default_capacity(R))
+        mean = E.astype(float).mean()
+        var = E.astype(float).var()
+        assert lnQ == pytest.approx(-db * mean + 0.5 * db * db * var, rel=1e-5, abs=1e-14)
+
+
+def test_nearest_integer_counts_bounds_and_mean():
+    """Eq. (resampling-factors): r_j in {floor tau, floor tau + 1}; <r_j> = tau_hat_j."""
+    L, R = 8, 50000
+    pa = oracle.PA(L, R, seed=9)
+    pa.init()
+    E, _, _ = pa.state()
+    db = 0.05
+    st, counts, lnQ, S, kmin, R_new = oracle.resample_levels(L, R, _levels_energy(L, E), 0.0, db, 1, 9,
+                                                             oracle.NEAREST, oracle.default_capacity(R))
+    w = np.exp(-db * E.astype(float))
+    tau = R * w / w.sum()
+    fl = np.floor(tau)
+    assert np.all((counts == fl) | (counts == fl + 1))
+    assert R_new == counts.sum()
+    assert fl.sum() <= R_new <= fl.sum() + R
+    # mean of the fractional part decision per energy
+    frac = tau - fl
+    extra = counts - fl
+    assert abs(extra.sum() - frac.sum()) < 5 * math.sqrt(np.sum(frac * (1 - frac)))
+
+
+@pytest.mark.parametrize("lam", [0.3, 1.0, 2.5, 70.0])
+def test_poisson_sampler_pmf(lam):
+    n = 30000
+    draws = np.array([oracle.poisson(lam, 77, j, 3) for j in range(n)])
+    assert draws.mean() == pytest.approx(lam, abs=5 * math.sqrt(lam / n))
+    assert draws.var() == pytest.approx(lam, rel=6 * math.sqrt(2.0 / n) + 5 * math.sqrt(1 / (lam * n)))
+    ks = np.arange(0, int(lam + 10 * math.sqrt(lam) + 10))
+    logp = -lam + ks * math.log(lam) - np.array([math.lgamma(k + 1) for k in ks])
+    p = np.exp(logp)
+    obs = np.bincount(draws, minlength=len(ks))[: len(ks)]
+    mask = p * n > 5
+    chi2 = np.sum((obs[mask] - n * p[mask]) ** 2 / (n * p[mask]))
+    dof = mask.sum() - 1
+    assert chi2 < dof + 6 * math.sqrt(2 * dof)
+
+
+def test_poisson_counts_in_resampling_mean():
+    L, R = 8, 40000
+    pa = oracle.PA(L, R, seed=10, kind=oracle.POISSON)
+    pa.init()
+    E, _, _ = pa.state()
+    db = 0.03
+    st, counts, *_ = oracle.resample_levels(L, R, _levels_energy(L, E), 0.0, db, 1, 10,
+                                            oracle.POISSON, 10 * R)
+    w = np.exp(-db * E.astype(float))
+    tau = R * w / w.sum()
+    assert st == 0
+    assert abs(counts.sum() - R) < 5 * math.sqrt(R)
+    assert abs((counts - tau).sum()) < 5 * math.sqrt(tau.sum())
+
+
+def test_tree_order_and_copies():
+    """Children of one parent sit next to each other in parent order (Sec. V): family
+    ids stay sorted, each child is a bit copy of its parent."""
+    L, R = 8, 3000
+    pa = oracle.PA(L, R, seed=12)
+    pa.init()
+    for i, beta in enumerate([0.1, 0.2, 0.3, 0.4], start=1):
+        spins_before = pa.spins()
+        _, _, fam_before = pa.state()
+        assert pa.resample(beta) == 0
+        counts = pa.counts()
+        E, M, fam = pa.state()
+        assert np.all(np.diff(fam) >= 0)
+        parents = np.repeat(np.arange(len(counts)), counts)
+        assert np.array_equal(pa.spins(), spins_before[parents])
+        assert np.array_equal(fam, fam_before[parents])
+        h = pa.histogram()
+        assert h.sum() == pa.R
+        pa.sweep(3)
+
+
+def test_capacity_overflow_is_reported():
+    L, R = 4, 500
+    pa = oracle.PA(L, R, seed=1, kind=oracle.POISSON, capacity=R)
+    pa.init()
+    sts = [pa.resample(b) for b in (0.5, 1.0, 1.5, 2.0)]
+    assert 3 in sts  # Poisson population exceeds a capacity of exactly R at some step
+
+
+@pytest.mark.slow
+def test_full_anneal_L4_matches_enumeration():
+    """A whole anneal at L=4 reproduces the exact ln Z (Sec. VII estimator), <E> and C
+    within a few standard errors."""
+    L, R, theta = 4, 20000, 5
+    N = L * L
+    g, _, _ = oracle.bruteforce(L)
+    Ek = (4 * np.arange(N + 1) - 2 * N).astype(float)
+    pa = oracle.PA(L, R, seed=31)
+    pa.init()
+    for i in range(1, 21):
+        beta = i / 20.0
+        assert pa.resample(beta) == 0
+        pa.sweep(theta)
+        o = pa.observables()
+        w = g * np.exp(-beta * (Ek - Ek.min()))
+        Z = w.sum()
+        mE = (w * Ek).sum() / Z
+        varE = (w * Ek * Ek).sum() / Z - mE ** 2
+        lnZ = math.log(Z) - beta * Ek.min()
+        reff = o["R"] / o["rho_t"]
+        se_e = math.sqrt(varE / reff) / N
+        assert abs(o["e"] - mE / N) < 6 * se_e + 1e-12, (beta, o["e"], mE / N)
+        assert abs(o["minus_betaF"] - lnZ) < 0.02, (beta, o["minus_betaF"], lnZ)
+        C = beta ** 2 * varE / N
+        assert abs(o["C"] - C) < 0.1 * C + 0.02
+
+
+@pytest.mark.slow
+def test_anneal_L8_against_kaufman():
+    L, R, theta = 8, 5000, 10
+    N = L * L
+    pa = oracle.PA(L, R, seed=1)
+    pa.init()
+    for i in range(1, 51):
+        beta = i / 50.0
+        assert pa.resample(beta) == 0
+        pa.sweep(theta)
+    o = pa.observables()
+    e_ex, c_ex, lnZ = oracle.kaufman_thermo(L, 1.0)
+    assert abs(o["e"] - e_ex / N) < 0.01
+    assert abs(o["minus_betaF"] - lnZ) / N < 2e-3
