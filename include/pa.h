@@ -1,0 +1,176 @@
+/*
+ * pa.h -- C ABI of the GB300 (sm_103a) population-annealing library for the 2D Ising
+ * ferromagnet (J = 1, L x L periodic lattice), after Weigel, Barash, Shchur and Janke,
+ * "Understanding population annealing Monte Carlo simulations", arXiv:2102.06611.
+ *
+ * The entry points follow the method's step list (Sec. II):
+ *   pa_init        step 1  simple sampling of R replicas at beta_0 = 0, then measurement
+ *   pa_resample    step 2  reweighting by exp(-(beta_i - beta_{i-1}) E_j), Eq. (Q) for
+ *                          Q_i, Eq. (taus) for the rescaled copy means, Eq.
+ *                          (resampling-factors) or Poisson copy numbers, replica copying
+ *   pa_anneal_step step 3  theta Metropolis sweeps of every replica, then measurement
+ *   pa_observables step 4  population averages (Sec. III) and the free-energy estimator
+ *                          Eq. (free-emergy-estimator) with ln Z_0 = L^2 ln 2 (Sec. VII)
+ *
+ * Memory: the library never allocates device memory.  The caller allocates every device
+ * buffer (sizes from pa_query_sizes) and keeps it alive until pa_destroy.  The context
+ * object itself is host memory owned by the library.
+ *
+ * Streams: every call is asynchronous on the stream given to pa_init, except the calls
+ * documented as synchronising (they copy results to host memory).
+ *
+ * Errors: every call returns a pa_status.  Kernels never trap: a device-side failure
+ * (population above capacity, extinct population) sets a sticky error word that the next
+ * synchronising call returns; after any error the context is only valid for
+ * pa_last_error and pa_destroy.
+ *
+ * Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key = seed and counters
+ * keyed by (stream tag, step, sweep, replica slot, site), so every result is a fixed
+ * function of (config, schedule) and does not depend on the launch configuration.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pa_ctx pa_ctx;
+
+typedef enum {
+    PA_OK = 0,
+    PA_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment, or unsupported L */
+    PA_ERR_STATE = 2,       /* call out of order (e.g. resample to a lower beta) */
+    PA_ERR_CAPACITY = 3,    /* resampled population larger than the buffer capacity */
+    PA_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    PA_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    PA_ERR_NUMERIC = 6      /* empty population or non-finite weights */
+} pa_status;
+
+typedef enum {
+    PA_RESAMPLE_NEAREST = 0, /* Eq. (resampling-factors): floor(tau) or floor(tau) + 1 */
+    PA_RESAMPLE_POISSON = 1  /* r_j ~ Poisson(tau_hat_j), fluctuating population size */
+} pa_resample_kind;
+
+/* Run configuration.  L must be one of 4, 8, 12, 16, 24, 32, 48, 64, 128.
+   1 <= R <= capacity <= 2^31 - 1.  beta_0 is always 0 (simple sampling, Sec. II). */
+typedef struct {
+    int L;
+    int resample;                /* pa_resample_kind */
+    long long R;                 /* target population size R (Eq. taus) */
+    long long capacity;          /* replicas each buffer can hold (>= R) */
+    unsigned long long seed;     /* Philox key */
+} pa_config;
+
+/* Byte sizes of the caller-owned device buffers for a configuration.
+   spin_bytes: one spin buffer (capacity * bytes_per_replica), 256-byte aligned start.
+   int_bytes:  one per-replica int32 array (capacity * 4).
+   work_bytes: the workspace. */
+typedef struct {
+    size_t spin_bytes;
+    size_t int_bytes;
+    size_t work_bytes;
+    size_t bytes_per_replica;
+} pa_sizes;
+
+/* Caller-owned device buffers, each 256-byte aligned.  spins/level/mag/fam come in two
+   copies (current population and resampling target). */
+typedef struct {
+    void *spins[2];
+    void *level[2];   /* int32 energy level k = (E + 2N) / 4 per replica */
+    void *mag[2];     /* int32 magnetisation M per replica */
+    void *fam[2];     /* int32 family id (index of the beta_0 ancestor, Sec. V) */
+    void *work;       /* workspace of pa_sizes.work_bytes */
+} pa_buffers;
+
+/* One record of step 4.  All floating-point fields are computed in binary64 in a fixed
+   order from exact integer sums over the population.  Written by pa_observables and
+   pa_record. */
+typedef struct {
+    long long step;        /* temperature index i (0 after pa_init) */
+    long long R;           /* population size R_i */
+    double beta;           /* beta_i */
+    double dbeta;          /* beta_i - beta_{i-1} */
+    double e;              /* energy per spin <E>/N                  (Sec. III) */
+    double C;              /* specific heat per spin beta^2 Var(E)/N (Sec. III) */
+    double m;              /* <|M|>/N                                (Sec. III) */
+    double m2;             /* <M^2>/N^2 */
+    double chi;            /* beta N (<M^2>/N^2 - m^2)               (Sec. III) */
+    double lnQ;            /* ln Q_i of the last resampling          (Eq. Q) */
+    double minus_betaF;    /* N ln 2 + sum_k ln Q_k                  (Sec. VII) */
+    double rho_t;          /* R_i sum_k n_k^2, mean-square family size (Eq. rhot) */
+    long long families;    /* number f of surviving families         (Sec. V) */
+    long long sum_E;       /* exact integer sums the fields above are formed from */
+    long long sum_E2;
+    long long sum_absM;
+    long long sum_M2;
+    long long sum_size2;   /* sum over families of (family size)^2 */
+    int theta;             /* sweeps of the last pa_anneal_step */
+    int status;            /* sticky device error word (pa_status) */
+} pa_obs;
+
+/* Buffer sizes for cfg.  Returns PA_ERR_INVALID_ARG for an unsupported configuration. */
+pa_status pa_query_sizes(const pa_config *cfg, pa_sizes *out);
+
+/* Step 1 (Sec. II): create a context on `stream` (a cudaStream_t, NULL = legacy default
+   stream) over the caller's buffers, fill R replicas by simple sampling at beta_0 = 0
+   (site n of replica j is bit n mod 32 of word n/32 of Philox stream INIT), set family
+   id j, and measure energies, magnetisations and the level histogram.  Asynchronous. */
+pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_ctx **out);
+
+/* Step 2 (Sec. II, Eqs. Q, taus, resampling-factors): move from the current beta to
+   beta_new >= beta.  Uses the energies measured before resampling; builds the level
+   table in binary64 (w_k = exp(-dbeta (E_k - E_ref)), S = sum_k h_k w_k in ascending k,
+   tau_hat_k = R w_k / S), draws copy numbers, prefix-sums them on the device and copies
+   children to consecutive slots in parent order (tree order).  Advances the step index.
+   Asynchronous; a capacity overflow surfaces at the next synchronising call. */
+pa_status pa_resample(pa_ctx *ctx, double beta_new);
+
+/* Step 3 (Sec. II) and the measurement of step 4: theta >= 0 checkerboard Metropolis
+   sweeps of every replica at the current beta (acceptance min(1, exp(-beta dE)) with
+   integer thresholds floor(exp(-4 beta) 2^32), floor(exp(-8 beta) 2^32)), then
+   energies, magnetisations and the level histogram.  Asynchronous. */
+pa_status pa_anneal_step(pa_ctx *ctx, int theta);
+
+/* Step 4: form a pa_obs record on the device and write it to `device_dst` (a device
+   pointer to sizeof(pa_obs) bytes, 8-byte aligned).  Asynchronous. */
+pa_status pa_record(pa_ctx *ctx, void *device_dst);
+
+/* Step 4: form the record and copy it to host memory.  Synchronises the stream and
+   returns the sticky device error, if any. */
+pa_status pa_observables(pa_ctx *ctx, pa_obs *host_out);
+
+/* Synchronise the stream; returns the sticky device error, if any. */
+pa_status pa_sync(pa_ctx *ctx);
+
+/* Current population size R_i (synchronising). */
+pa_status pa_population(pa_ctx *ctx, long long *R_out);
+
+/* Testing and replay accessors (all synchronising, host destinations).
+   pa_histogram: N + 1 int32 level counts h_k of the current population.
+   pa_replicas:  level, magnetisation and family id of replicas [0, R_i) (any may be NULL).
+   pa_copy_counts: the R_{i-1} copy numbers r_j of the last resampling; host_out must hold
+                 `capacity` entries, *count_out receives R_{i-1}.
+   pa_hashes:    FNV-1a 64 of each replica's canonical packed bytes (rows of ceil(L/32)
+                 little-endian uint32 words, bit c mod 32 of word c/32 set iff spin at
+                 column c is +1).
+   pa_export_spins: canonical packed words of replicas [first, first + count). */
+pa_status pa_histogram(pa_ctx *ctx, int *host_out);
+pa_status pa_replicas(pa_ctx *ctx, int *level, int *mag, int *fam);
+pa_status pa_copy_counts(pa_ctx *ctx, int *host_out, long long *count_out);
+pa_status pa_hashes(pa_ctx *ctx, unsigned long long *host_out);
+pa_status pa_export_spins(pa_ctx *ctx, long long first, long long count, unsigned int *host_out);
+
+/* Message for the last failing call on ctx (static storage owned by the context). */
+const char *pa_last_error(const pa_ctx *ctx);
+
+/* Release the host context.  Does not touch the caller's device buffers. */
+void pa_destroy(pa_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H */

@@ -80,6 +80,9 @@ def lib():
                 "orc_init_replica": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, i8p]),
                 "orc_sweep_replica": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                              ctypes.c_uint32, ctypes.c_double, ctypes.c_int, i8p]),
+                "orc_sweep_replica_t0": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                                ctypes.c_uint32, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_int, i8p]),
                 "orc_poisson": (ctypes.c_int64, [ctypes.c_double, ctypes.c_uint64,
                                                  ctypes.c_uint32, ctypes.c_uint32]),
                 "orc_resample_levels": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
@@ -172,10 +175,11 @@ def init_replica(L: int, seed: int, j: int) -> np.ndarray:
 
 
 def sweep_replica(L: int, seed: int, step: int, slot: int, beta: float, theta: int,
-                  s: np.ndarray) -> np.ndarray:
+                  s: np.ndarray, t0: int = 0) -> np.ndarray:
+    """theta sweeps numbered t0 .. t0 + theta - 1 within temperature step `step`."""
     out = np.array(s, dtype=np.int8, copy=True).reshape(L * L)
-    lib().orc_sweep_replica(L, seed, step, slot, float(beta), int(theta),
-                            _ptr(out, ctypes.c_int8))
+    lib().orc_sweep_replica_t0(L, seed, step, slot, float(beta), int(t0), int(theta),
+                               _ptr(out, ctypes.c_int8))
     return out
 
 

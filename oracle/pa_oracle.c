@@ -218,12 +218,12 @@ void orc_init_replica(int L, uint64_t seed, uint32_t j, int8_t *s)
  * with p = c / 2 (index of the site among the L/2 colour-q sites of row r),
  * x = lane (p mod 4) of Philox(ctr = (r * 16 + p / 4, j, (SWEEP << 28) | (2t + q), i)).
  * ---------------------------------------------------------------------------------- */
-void orc_sweep_replica(int L, uint64_t seed, uint32_t step, uint32_t slot, double beta,
-                       int theta, int8_t *s)
+void orc_sweep_replica_t0(int L, uint64_t seed, uint32_t step, uint32_t slot, double beta,
+                          int t0, int theta, int8_t *s)
 {
     uint64_t T4 = orc_metropolis_threshold(4.0 * beta);
     uint64_t T8 = orc_metropolis_threshold(8.0 * beta);
-    for (int t = 0; t < theta; ++t)
+    for (int t = t0; t < t0 + theta; ++t)
         for (int q = 0; q < 2; ++q)
             for (int r = 0; r < L; ++r)
                 for (int c = 0; c < L; ++c) {
@@ -241,6 +241,14 @@ void orc_sweep_replica(int L, uint64_t seed, uint32_t step, uint32_t slot, doubl
                     else flip = (uint64_t)x < T8;
                     if (flip) s[site(L, r, c)] = (int8_t)(-si);
                 }
+}
+
+/* Sweeps are numbered from 0 within a temperature step; a run of theta sweeps that starts
+   after t0 earlier sweeps of the same step uses sweep numbers t0 .. t0 + theta - 1. */
+void orc_sweep_replica(int L, uint64_t seed, uint32_t step, uint32_t slot, double beta,
+                       int theta, int8_t *s)
+{
+    orc_sweep_replica_t0(L, seed, step, slot, beta, 0, theta, s);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -368,6 +376,7 @@ typedef struct {
     uint32_t step;          /* index i of the current temperature beta_i */
     double beta, dbeta, lnQ, sum_lnQ;
     int theta_last;
+    int t_done;             /* sweeps already done at the current step */
     int8_t *s;              /* capacity * N */
     int8_t *s_next;
     int32_t *E, *M, *fam, *E_next, *M_next, *fam_next;
@@ -422,6 +431,7 @@ void orc_pa_init(orc_pa *p)
     p->step = 0;
     p->beta = 0.0; p->dbeta = 0.0; p->lnQ = 0.0; p->sum_lnQ = 0.0;
     p->theta_last = 0;
+    p->t_done = 0;
     p->status = 0;
     for (int64_t j = 0; j < p->R; ++j) {
         orc_init_replica(p->L, p->seed, (uint32_t)j, p->s + (size_t)j * p->N);
@@ -462,6 +472,7 @@ int orc_pa_resample(orc_pa *p, double beta_new)
     p->dbeta = beta_new - p->beta;
     p->beta = beta_new;
     p->step = step;
+    p->t_done = 0;
     p->lnQ = info.lnQ;
     p->sum_lnQ = p->sum_lnQ + info.lnQ;
     return 0;
@@ -472,8 +483,9 @@ int orc_pa_resample(orc_pa *p, double beta_new)
 void orc_pa_sweep(orc_pa *p, int theta)
 {
     for (int64_t j = 0; j < p->R; ++j)
-        orc_sweep_replica(p->L, p->seed, p->step, (uint32_t)j, p->beta, theta,
-                          p->s + (size_t)j * p->N);
+        orc_sweep_replica_t0(p->L, p->seed, p->step, (uint32_t)j, p->beta, p->t_done, theta,
+                             p->s + (size_t)j * p->N);
+    p->t_done += theta;
     p->theta_last = theta;
     measure_all(p);
 }
@@ -570,6 +582,7 @@ int orc_pa_set(orc_pa *p, int64_t R, const int8_t *spins, const int32_t *fam,
     p->step = step;
     p->beta = beta;
     p->sum_lnQ = sum_lnQ;
+    p->t_done = 0;
     p->status = 0;
     measure_all(p);
     return 0;

@@ -1,0 +1,106 @@
+"""ctypes declarations of the C ABI in ``include/pa.h`` (argument marshalling only).
+
+Loading fails loudly if the CUDA library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+PA_OK, PA_ERR_INVALID_ARG, PA_ERR_STATE, PA_ERR_CAPACITY, PA_ERR_CUDA, PA_ERR_TIMEOUT, PA_ERR_NUMERIC = range(7)
+STATUS_NAMES = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_STATE", 3: "PA_ERR_CAPACITY",
+                4: "PA_ERR_CUDA", 5: "PA_ERR_TIMEOUT", 6: "PA_ERR_NUMERIC"}
+PA_RESAMPLE_NEAREST, PA_RESAMPLE_POISSON = 0, 1
+
+
+class PAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pa_config(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("resample", ctypes.c_int), ("R", ctypes.c_longlong),
+                ("capacity", ctypes.c_longlong), ("seed", ctypes.c_ulonglong)]
+
+
+class pa_sizes(ctypes.Structure):
+    _fields_ = [("spin_bytes", ctypes.c_size_t), ("int_bytes", ctypes.c_size_t),
+                ("work_bytes", ctypes.c_size_t), ("bytes_per_replica", ctypes.c_size_t)]
+
+
+class pa_buffers(ctypes.Structure):
+    _fields_ = [("spins", ctypes.c_void_p * 2), ("level", ctypes.c_void_p * 2),
+                ("mag", ctypes.c_void_p * 2), ("fam", ctypes.c_void_p * 2), ("work", ctypes.c_void_p)]
+
+
+class pa_obs(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("R", ctypes.c_longlong), ("beta", ctypes.c_double),
+                ("dbeta", ctypes.c_double), ("e", ctypes.c_double), ("C", ctypes.c_double),
+                ("m", ctypes.c_double), ("m2", ctypes.c_double), ("chi", ctypes.c_double),
+                ("lnQ", ctypes.c_double), ("minus_betaF", ctypes.c_double), ("rho_t", ctypes.c_double),
+                ("families", ctypes.c_longlong), ("sum_E", ctypes.c_longlong), ("sum_E2", ctypes.c_longlong),
+                ("sum_absM", ctypes.c_longlong), ("sum_M2", ctypes.c_longlong),
+                ("sum_size2", ctypes.c_longlong), ("theta", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+# name -> (restype, argtypes): every entry point declared in include/pa.h
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+SIGNATURES = {
+    "pa_query_sizes": (ctypes.c_int, [_P(pa_config), _P(pa_sizes)]),
+    "pa_init": (ctypes.c_int, [_P(pa_config), _P(pa_buffers), _vp, _P(_vp)]),
+    "pa_resample": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "pa_anneal_step": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "pa_record": (ctypes.c_int, [_vp, _vp]),
+    "pa_observables": (ctypes.c_int, [_vp, _P(pa_obs)]),
+    "pa_sync": (ctypes.c_int, [_vp]),
+    "pa_population": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
+    "pa_histogram": (ctypes.c_int, [_vp, _vp]),
+    "pa_replicas": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "pa_copy_counts": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_longlong)]),
+    "pa_hashes": (ctypes.c_int, [_vp, _vp]),
+    "pa_export_spins": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_longlong, _vp]),
+    "pa_last_error": (ctypes.c_char_p, [_vp]),
+    "pa_destroy": (None, [_vp]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load the library (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise ImportError(f"CUDA library {path} missing; build it with paper_2102_06611_gb300.build")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def load_without_build() -> ctypes.CDLL:
+    """Load an already built library (used by the symbol-export test)."""
+    L = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L

@@ -1,0 +1,414 @@
+// pa_api.cu -- the C ABI (include/pa.h): argument checks, the host-side context, and the
+// launch sequence of each step of population annealing (arXiv:2102.06611, Sec. II).
+// The library allocates no device memory; all device state lives in caller buffers.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pa_common.cuh"
+#include "pa_kernels.h"
+
+struct pa_ctx {
+    pa_config cfg;
+    int N;
+    int device;
+    int num_sms;
+    cudaStream_t stream;
+    pa_buffers buf;
+    pa::Workspace ws;
+    pa::DevState *st;
+    int cur;               // index of the buffers holding the current population
+    long long step;        // temperature index i
+    double beta, dbeta;
+    int theta_last;
+    int sweeps_in_step;    // sweeps already done at this temperature
+    int failed;            // sticky host-side status
+    char err[256];
+};
+
+namespace {
+
+bool supported_L(int L)
+{
+    switch (L) {
+        case 4: case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 128: return true;
+        default: return false;
+    }
+}
+
+pa_status fail(pa_ctx *c, pa_status s, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+        if (s != PA_ERR_INVALID_ARG && s != PA_ERR_STATE) c->failed = s;
+    }
+    return s;
+}
+
+pa_status cuda_fail(pa_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, PA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <typename T>
+T *at(const pa_ctx *c, size_t off)
+{
+    return reinterpret_cast<T *>(static_cast<char *>(c->buf.work) + off);
+}
+
+int *cur_level(pa_ctx *c) { return static_cast<int *>(c->buf.level[c->cur]); }
+int *cur_mag(pa_ctx *c) { return static_cast<int *>(c->buf.mag[c->cur]); }
+int *cur_fam(pa_ctx *c) { return static_cast<int *>(c->buf.fam[c->cur]); }
+
+// Make the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+pa_status check_live(pa_ctx *c)
+{
+    if (!c) return PA_ERR_INVALID_ARG;
+    if (c->failed) return (pa_status)c->failed;
+    return PA_OK;
+}
+
+// Synchronise and fold the device's sticky error word into the context.
+pa_status sync_and_check(pa_ctx *c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    int dev_err = 0;
+    e = cudaMemcpy(&dev_err, &c->st->error, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read error word");
+    if (dev_err) {
+        const char *what = dev_err == PA_ERR_CAPACITY ? "population exceeds buffer capacity"
+                           : dev_err == PA_ERR_NUMERIC ? "empty population or non-finite weights"
+                                                       : "device error";
+        return fail(c, (pa_status)dev_err, "%s", what);
+    }
+    return PA_OK;
+}
+
+long long read_R(pa_ctx *c, bool prev, pa_status *st)
+{
+    long long R = 0;
+    *st = sync_and_check(c);
+    if (*st != PA_OK) return 0;
+    cudaError_t e = cudaMemcpy(&R, prev ? &c->st->R_prev : &c->st->R_cur, sizeof(R), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) *st = cuda_fail(c, e, "read population size");
+    return R;
+}
+
+bool aligned256(const void *p) { return p && ((reinterpret_cast<uintptr_t>(p) & 255u) == 0); }
+
+}  // namespace
+
+extern "C" {
+
+pa_status pa_query_sizes(const pa_config *cfg, pa_sizes *out)
+{
+    if (!cfg || !out) return PA_ERR_INVALID_ARG;
+    if (!supported_L(cfg->L) || cfg->R < 1 || cfg->capacity < cfg->R || cfg->capacity > 2147483647LL)
+        return PA_ERR_INVALID_ARG;
+    if (cfg->resample != PA_RESAMPLE_NEAREST && cfg->resample != PA_RESAMPLE_POISSON) return PA_ERR_INVALID_ARG;
+    const pa::Workspace ws = pa::plan_workspace(cfg->L, cfg->capacity);
+    out->bytes_per_replica = (size_t)pa::bytes_per_replica(cfg->L);
+    out->spin_bytes = out->bytes_per_replica * (size_t)cfg->capacity;
+    out->int_bytes = (size_t)cfg->capacity * 4;
+    out->work_bytes = ws.total;
+    return PA_OK;
+}
+
+pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_ctx **out)
+{
+    if (!out) return PA_ERR_INVALID_ARG;
+    *out = nullptr;
+    pa_sizes sz;
+    if (!cfg || !buf || pa_query_sizes(cfg, &sz) != PA_OK) return PA_ERR_INVALID_ARG;
+    for (int b = 0; b < 2; ++b)
+        if (!aligned256(buf->spins[b]) || !aligned256(buf->level[b]) || !aligned256(buf->mag[b]) ||
+            !aligned256(buf->fam[b]))
+            return PA_ERR_INVALID_ARG;
+    if (!aligned256(buf->work)) return PA_ERR_INVALID_ARG;
+
+    pa_ctx *c = new (std::nothrow) pa_ctx();
+    if (!c) return PA_ERR_INVALID_ARG;
+    c->cfg = *cfg;
+    c->N = cfg->L * cfg->L;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->buf = *buf;
+    c->ws = pa::plan_workspace(cfg->L, cfg->capacity);
+    c->st = at<pa::DevState>(c, c->ws.state);
+    c->cur = 0;
+    c->step = 0;
+    c->beta = 0.0;
+    c->dbeta = 0.0;
+    c->theta_last = 0;
+    c->sweeps_in_step = 0;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return PA_ERR_CUDA;
+    }
+    e = pa::launch_setup(c->st, cfg->R, at<int>(c, c->ws.hist), c->N, c->stream);
+    if (e == cudaSuccess) {
+        pa::SweepArgs a{};
+        a.spins = buf->spins[0];
+        a.level = cur_level(c);
+        a.mag = cur_mag(c);
+        a.fam = cur_fam(c);
+        a.hist = at<int>(c, c->ws.hist);
+        a.st = c->st;
+        a.R_init = cfg->R;
+        a.R_bound = cfg->R;
+        a.k0 = (unsigned int)(cfg->seed & 0xffffffffu);
+        a.k1 = (unsigned int)(cfg->seed >> 32);
+        a.step = 0;
+        a.t0 = 0;
+        a.theta = 0;
+        e = pa::launch_sweep(cfg->L, true, a, c->num_sms, c->stream);
+    }
+    if (e != cudaSuccess) {
+        delete c;
+        return PA_ERR_CUDA;
+    }
+    *out = c;
+    return PA_OK;
+}
+
+pa_status pa_resample(pa_ctx *c, double beta_new)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!std::isfinite(beta_new) || beta_new < c->beta)
+        return fail(c, PA_ERR_STATE, "beta_new %.17g must be finite and >= current beta %.17g", beta_new, c->beta);
+    DeviceGuard g(c->device);
+    const int nxt = c->cur ^ 1;
+    pa::ResampleArgs a{};
+    a.L = c->cfg.L;
+    a.kind = c->cfg.resample;
+    a.R_target = c->cfg.R;
+    a.capacity = c->cfg.capacity;
+    a.beta_prev = c->beta;
+    a.beta_new = beta_new;
+    a.step = (unsigned int)(c->step + 1);
+    a.k0 = (unsigned int)(c->cfg.seed & 0xffffffffu);
+    a.k1 = (unsigned int)(c->cfg.seed >> 32);
+    a.st = c->st;
+    a.hist = at<int>(c, c->ws.hist);
+    a.fl = at<int>(c, c->ws.fl);
+    a.thr = at<unsigned int>(c, c->ws.thr);
+    a.tau = at<double>(c, c->ws.tau);
+    a.w = at<double>(c, c->ws.w);
+    a.counts = at<int>(c, c->ws.counts);
+    a.blocksum = at<long long>(c, c->ws.blocksum);
+    a.nblk = c->ws.nblk;
+    a.spins_src = c->buf.spins[c->cur];
+    a.spins_dst = c->buf.spins[nxt];
+    a.level_src = static_cast<const int *>(c->buf.level[c->cur]);
+    a.mag_src = static_cast<const int *>(c->buf.mag[c->cur]);
+    a.fam_src = static_cast<const int *>(c->buf.fam[c->cur]);
+    a.level_dst = static_cast<int *>(c->buf.level[nxt]);
+    a.mag_dst = static_cast<int *>(c->buf.mag[nxt]);
+    a.fam_dst = static_cast<int *>(c->buf.fam[nxt]);
+    cudaError_t e = pa::launch_resample(a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "resample launch");
+    c->cur = nxt;
+    c->step += 1;
+    c->dbeta = beta_new - c->beta;
+    c->beta = beta_new;
+    c->sweeps_in_step = 0;
+    return PA_OK;
+}
+
+pa_status pa_anneal_step(pa_ctx *c, int theta)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (theta < 0 || (long long)c->sweeps_in_step + theta > (1 << 27))
+        return fail(c, PA_ERR_INVALID_ARG, "theta %d out of range", theta);
+    DeviceGuard g(c->device);
+    cudaError_t e = pa::launch_zero_measure(c->st, at<int>(c, c->ws.hist), c->N, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "zero measurement");
+    pa::SweepArgs a{};
+    a.spins = c->buf.spins[c->cur];
+    a.level = cur_level(c);
+    a.mag = cur_mag(c);
+    a.fam = cur_fam(c);
+    a.hist = at<int>(c, c->ws.hist);
+    a.st = c->st;
+    a.R_init = 0;
+    a.R_bound = c->cfg.capacity;
+    a.k0 = (unsigned int)(c->cfg.seed & 0xffffffffu);
+    a.k1 = (unsigned int)(c->cfg.seed >> 32);
+    a.step = (unsigned int)c->step;
+    a.t0 = c->sweeps_in_step;
+    a.theta = theta;
+    e = pa::launch_sweep(c->cfg.L, false, a, c->num_sms, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
+    c->sweeps_in_step += theta;
+    c->theta_last = theta;
+    return PA_OK;
+}
+
+pa_status pa_record(pa_ctx *c, void *device_dst)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!device_dst || (reinterpret_cast<uintptr_t>(device_dst) & 7u))
+        return fail(c, PA_ERR_INVALID_ARG, "record destination must be an 8-byte aligned device pointer");
+    DeviceGuard g(c->device);
+    pa::ObsArgs a{};
+    a.L = c->cfg.L;
+    a.step = c->step;
+    a.beta = c->beta;
+    a.dbeta = c->dbeta;
+    a.theta = c->theta_last;
+    a.st = c->st;
+    a.hist = at<int>(c, c->ws.hist);
+    a.fam = cur_fam(c);
+    a.fampart = at<long long>(c, c->ws.fampart);
+    a.dst = static_cast<pa_obs *>(device_dst);
+    cudaError_t e = pa::launch_observables(a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "observables launch");
+    return PA_OK;
+}
+
+pa_status pa_observables(pa_ctx *c, pa_obs *host_out)
+{
+    if (!host_out) return PA_ERR_INVALID_ARG;
+    pa_status s = pa_record(c, at<void>(c, c->ws.obs));
+    if (s != PA_OK) return s;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaMemcpyAsync(host_out, at<void>(c, c->ws.obs), sizeof(pa_obs), cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "observables copy");
+    return sync_and_check(c);
+}
+
+pa_status pa_sync(pa_ctx *c)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    DeviceGuard g(c->device);
+    return sync_and_check(c);
+}
+
+pa_status pa_population(pa_ctx *c, long long *R_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!R_out) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    *R_out = read_R(c, false, &s);
+    return s;
+}
+
+pa_status pa_histogram(pa_ctx *c, int *host_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!host_out) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if ((s = sync_and_check(c)) != PA_OK) return s;
+    cudaError_t e = cudaMemcpy(host_out, at<int>(c, c->ws.hist), sizeof(int) * (size_t)(c->N + 1),
+                               cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PA_OK : cuda_fail(c, e, "histogram copy");
+}
+
+pa_status pa_replicas(pa_ctx *c, int *level, int *mag, int *fam)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    DeviceGuard g(c->device);
+    const long long R = read_R(c, false, &s);
+    if (s != PA_OK) return s;
+    const size_t bytes = sizeof(int) * (size_t)R;
+    cudaError_t e = cudaSuccess;
+    if (level && e == cudaSuccess) e = cudaMemcpy(level, cur_level(c), bytes, cudaMemcpyDeviceToHost);
+    if (mag && e == cudaSuccess) e = cudaMemcpy(mag, cur_mag(c), bytes, cudaMemcpyDeviceToHost);
+    if (fam && e == cudaSuccess) e = cudaMemcpy(fam, cur_fam(c), bytes, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PA_OK : cuda_fail(c, e, "replica copy");
+}
+
+pa_status pa_copy_counts(pa_ctx *c, int *host_out, long long *count_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!host_out || !count_out) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    const long long Rp = read_R(c, true, &s);
+    if (s != PA_OK) return s;
+    *count_out = Rp;
+    cudaError_t e = cudaMemcpy(host_out, at<int>(c, c->ws.counts), sizeof(int) * (size_t)Rp,
+                               cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PA_OK : cuda_fail(c, e, "copy-count copy");
+}
+
+pa_status pa_hashes(pa_ctx *c, unsigned long long *host_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!host_out) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    unsigned long long *dev = at<unsigned long long>(c, c->ws.hashes);
+    cudaError_t e = pa::launch_hashes(c->cfg.L, c->buf.spins[c->cur], c->cfg.capacity, c->st, dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hash launch");
+    const long long R = read_R(c, false, &s);
+    if (s != PA_OK) return s;
+    e = cudaMemcpy(host_out, dev, sizeof(unsigned long long) * (size_t)R, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PA_OK : cuda_fail(c, e, "hash copy");
+}
+
+pa_status pa_export_spins(pa_ctx *c, long long first, long long count, unsigned int *host_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!host_out || first < 0 || count < 0) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    const long long R = read_R(c, false, &s);
+    if (s != PA_OK) return s;
+    if (first + count > R) return fail(c, PA_ERR_INVALID_ARG, "replicas [%lld, %lld) beyond R = %lld", first,
+                                       first + count, R);
+    const size_t words = (size_t)c->cfg.L * ((c->cfg.L + 31) / 32);
+    unsigned int *stage = at<unsigned int>(c, c->ws.stage);
+    for (long long done = 0; done < count; done += pa::kStageReplicas) {
+        const long long n = count - done < pa::kStageReplicas ? count - done : pa::kStageReplicas;
+        cudaError_t e = pa::launch_export(c->cfg.L, c->buf.spins[c->cur], first + done, n, stage, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_out + (size_t)done * words, stage, sizeof(unsigned int) * words * (size_t)n,
+                                cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "spin export");
+    }
+    return PA_OK;
+}
+
+const char *pa_last_error(const pa_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err;
+}
+
+void pa_destroy(pa_ctx *c)
+{
+    delete c;
+}
+
+}  // extern "C"

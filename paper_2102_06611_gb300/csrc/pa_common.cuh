@@ -1,0 +1,152 @@
+// pa_common.cuh -- device-side building blocks shared by the library's translation units:
+// lattice geometry of the packed layout, Philox4x32-10, the deterministic binary64 exp,
+// and the device state block kept in the caller's workspace.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pa.h"
+
+namespace pa {
+
+// ------------------------------------------------------------------------------------
+// Packed spin layout.  Row r of a replica is stored as two half-rows: half 0 holds the
+// spins at even columns 2j (bit j), half 1 those at odd columns 2j + 1 (bit j); bit set
+// = spin +1.  A half-row of H = L/2 bits is one uint32 (L <= 64) or one uint64 (L = 128).
+// Rows follow each other; a replica is L * 2 half-row words, contiguous.
+//
+// In the checkerboard update the sites of colour q = (r + c) mod 2 in row r are exactly
+// half (r + q) mod 2 of that row, so one colour of one row is one whole word.
+//
+// A replica is handled by G lanes of a warp; lane g holds rows g*RPL .. g*RPL + RPL - 1.
+// ------------------------------------------------------------------------------------
+template <int L_>
+struct Geo {
+    static constexpr int L = L_;
+    static constexpr int N = L * L;
+    static constexpr int H = L / 2;                      // sites per half-row
+    static constexpr bool WIDE = (H > 32);
+    using W = typename std::conditional<WIDE, unsigned long long, unsigned int>::type;
+    static constexpr int RPL = (L == 12 || L == 24 || L == 48) ? 3 : (L == 128 ? 4 : 2);
+    static constexpr int G = L / RPL;                    // lanes per replica (power of 2)
+    static constexpr int RPW = 32 / G;                   // replicas per warp
+    static constexpr int WORD_BYTES = WIDE ? 8 : 4;
+    static constexpr int BYTES = L * 2 * WORD_BYTES;     // bytes per replica
+    static constexpr int LANE_WORDS = 2 * RPL;           // half-row words held per lane
+    static_assert(L % RPL == 0, "rows per lane must divide L");
+    static_assert((G & (G - 1)) == 0 && G <= 32 && G >= 2, "lanes per replica");
+};
+
+__host__ __device__ constexpr int bytes_per_replica(int L) { return L * 2 * (L / 2 > 32 ? 8 : 4); }
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// multiplies; the key is advanced by the Weyl constants between rounds.
+// ------------------------------------------------------------------------------------
+constexpr unsigned int kPhiloxM0 = 0xD2511F53u;
+constexpr unsigned int kPhiloxM1 = 0xCD9E8D57u;
+constexpr unsigned int kPhiloxW0 = 0x9E3779B9u;
+constexpr unsigned int kPhiloxW1 = 0xBB67AE85u;
+
+enum : unsigned int { kStreamInit = 0u, kStreamSweep = 1u, kStreamResample = 2u, kStreamPoisson = 3u };
+
+__device__ __forceinline__ void mulhilo(unsigned int a, unsigned int b, unsigned int &hi, unsigned int &lo)
+{
+    unsigned long long p = (unsigned long long)a * (unsigned long long)b;
+    hi = (unsigned int)(p >> 32);
+    lo = (unsigned int)p;
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, unsigned int k0, unsigned int k1)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        unsigned int hi0, lo0, hi1, lo1;
+        mulhilo(kPhiloxM0, c.x, hi0, lo0);
+        mulhilo(kPhiloxM1, c.z, hi1, lo1);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------------------------
+// Deterministic binary64 exp: Cody-Waite reduction x = k ln2 + r (ln2 = LN2_HI + LN2_LO,
+// LN2_HI has 32 significant bits so k * LN2_HI is exact), then sum_{n<=13} r^n/n! in
+// Horner form.  Every operation is an explicitly rounded binary64 intrinsic (no FMA
+// contraction), so the value is a fixed function of x on every device.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double det_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.5) return __longlong_as_double(0x7ff0000000000000ll);
+    if (x < -745.5) return 0.0;
+    const double kLn2Hi = 0x1.62e42feep-1;
+    const double kLn2Lo = 0x1.a39ef35793c76p-33;
+    const double kInvLn2 = 0x1.71547652b82fep+0;
+    double k = rint(__dmul_rn(x, kInvLn2));
+    double r = __dadd_rn(__dadd_rn(x, -__dmul_rn(k, kLn2Hi)), -__dmul_rn(k, kLn2Lo));
+    double p = 1.0 / 6227020800.0;
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 479001600.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 39916800.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 3628800.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 362880.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 40320.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 5040.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 720.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 120.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 24.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 6.0);
+    p = __dadd_rn(__dmul_rn(p, r), 0.5);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0);
+    return ldexp(p, (int)k);
+}
+
+// floor(exp(-y) 2^32) as a 64-bit integer in [0, 2^32].
+__device__ __forceinline__ unsigned long long metropolis_threshold(double y)
+{
+    double p = det_exp(-y);
+    return (unsigned long long)floor(__dmul_rn(p, 4294967296.0));
+}
+
+// ------------------------------------------------------------------------------------
+// Device state block (first bytes of the workspace).
+// ------------------------------------------------------------------------------------
+struct DevState {
+    long long R_cur;          // current population size R_i
+    long long R_prev;         // population size before the last resampling R_{i-1}
+    double lnQ;               // ln Q_i of the last resampling
+    double sum_lnQ;           // running sum_k ln Q_k
+    double S;                 // sum_k h_k w_k of the last resampling
+    int kmin;                 // lowest occupied level of the last resampling
+    int error;                // sticky pa_status bits (first error wins)
+    // Metropolis acceptance at the current beta: accept iff x <= tm1 (and nz != 0)
+    unsigned int tm1_4, tm1_8;
+    unsigned int nz_4, nz_8;
+    // exact integer sums of the current population (filled by measurement)
+    unsigned long long sum_absM;
+    unsigned long long sum_M2;
+    long long fam_count;
+    long long fam_size2;
+    int theta;
+    int pad;
+};
+
+__device__ __forceinline__ void set_error(DevState *st, int code)
+{
+    atomicCAS(&st->error, 0, code);
+}
+
+// Warp-level reductions over aligned groups of G lanes.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace pa

@@ -1,0 +1,102 @@
+// pa_kernels.h -- argument blocks and launchers of the library's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/pa.h"
+
+namespace pa {
+
+struct DevState;
+
+// Workspace layout (byte offsets, all 256-byte aligned), computed by plan_workspace().
+struct Workspace {
+    size_t state;       // DevState
+    size_t hist;        // int32[N + 1]   level histogram of the current population
+    size_t fl;          // int32[N + 1]   floor(tau_hat_k)
+    size_t thr;         // uint32[N + 1]  floor(frac(tau_hat_k) 2^32)
+    size_t tau;         // double[N + 1]  tau_hat_k
+    size_t w;           // double[N + 1]  w_k
+    size_t counts;      // int32[capacity] copy numbers r_j of the last resampling
+    size_t blocksum;    // int64[nblk]    per-block sums of r_j, then exclusive offsets
+    size_t fampart;     // int64[2 * kFamBlocks] family partial sums
+    size_t obs;         // pa_obs          record slot used by pa_observables
+    size_t hashes;      // uint64[capacity]
+    size_t stage;       // uint32[kStageReplicas * L * ceil(L/32)] export staging
+    size_t total;
+    long long nblk;     // blocks of the copy-count / copy kernels
+};
+
+constexpr int kCountThreads = 256;
+constexpr int kCountItems = 4;                              // parents per thread
+constexpr int kCountBlockItems = kCountThreads * kCountItems; // parents per block
+constexpr int kFamBlocks = 512;
+constexpr long long kStageReplicas = 4096;
+
+Workspace plan_workspace(int L, long long capacity);
+
+struct SweepArgs {
+    void *spins;            // current spin buffer (updated in place)
+    int *level;
+    int *mag;
+    int *fam;               // written only by the init kernel
+    int *hist;
+    DevState *st;
+    long long R_init;       // population size for the init kernel
+    long long R_bound;      // host-side upper bound on R (grid sizing only)
+    unsigned int k0, k1;    // Philox key (seed)
+    unsigned int step;      // temperature index i
+    int t0;                 // sweeps already done at this step (sweep numbering offset)
+    int theta;
+};
+
+cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s);
+
+struct ResampleArgs {
+    int L;
+    int kind;
+    long long R_target;
+    long long capacity;
+    double beta_prev, beta_new;
+    unsigned int step;
+    unsigned int k0, k1;
+    DevState *st;
+    const int *hist;
+    int *fl;
+    unsigned int *thr;
+    double *tau;
+    double *w;
+    int *counts;
+    long long *blocksum;
+    long long nblk;
+    const void *spins_src;
+    void *spins_dst;
+    const int *level_src, *mag_src, *fam_src;
+    int *level_dst, *mag_dst, *fam_dst;
+};
+
+cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s);
+cudaError_t launch_thresholds(DevState *st, double beta, cudaStream_t s);
+cudaError_t launch_zero_measure(DevState *st, int *hist, int N, cudaStream_t s);
+cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, cudaStream_t s);
+
+struct ObsArgs {
+    int L;
+    long long step;
+    double beta, dbeta;
+    int theta;
+    DevState *st;
+    const int *hist;
+    const int *fam;
+    long long *fampart;
+    pa_obs *dst;
+};
+
+cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s);
+
+cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
+                          unsigned long long *out, cudaStream_t s);
+cudaError_t launch_export(int L, const void *spins, long long first, long long count,
+                          unsigned int *out, cudaStream_t s);
+
+}  // namespace pa

@@ -1,0 +1,555 @@
+// pa_resample.cu -- step 2 (reweighting, resampling, replica copying) and step 4
+// (observables, families, free energy) of population annealing (arXiv:2102.06611, Sec. II),
+// plus the hash / export kernels used to check the population against an independent CPU
+// implementation.
+//
+// Step 2 on the device, for the energies measured before resampling:
+//   k_table   one block: level histogram h_k -> E_ref (lowest occupied level),
+//             w_k = exp(-dbeta (E_k - E_ref)), S = sum over occupied k in ascending order
+//             of h_k w_k (one thread, fixed order), ln Q_i = -dbeta E_ref + ln(S / R_{i-1})
+//             (Eq. Q), tau_hat_k = R w_k / S (Eq. taus), floor(tau_hat_k) and the integer
+//             threshold floor(frac(tau_hat_k) 2^32).  All binary64 arithmetic uses explicitly
+//             rounded intrinsics; this file is also built with -fmad=false.
+//   k_counts  one thread per parent: nearest-integer copies (Eq. resampling-factors) from one
+//             Philox word, or Poisson copies; per-block sums.
+//   k_scan    one block: exclusive prefix sum of the block sums, R_i, capacity check.
+//   k_copy    per block: exclusive scan of its parents' copy numbers, then each warp copies
+//             a parent's packed spins (16-byte vectors) to its r_j consecutive child slots
+//             with the level, magnetisation and family id (tree order).
+#include <climits>
+
+#include "pa_common.cuh"
+#include "pa_kernels.h"
+
+namespace pa {
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Workspace plan_workspace(int L, long long capacity)
+{
+    Workspace w{};
+    const size_t nlev = (size_t)L * L + 1;
+    const long long nblk = (capacity + kCountBlockItems - 1) / kCountBlockItems;
+    const size_t words = (size_t)L * ((L + 31) / 32);
+    size_t off = 0;
+    w.state = off;    off = align256(off + sizeof(DevState));
+    w.hist = off;     off = align256(off + nlev * 4);
+    w.fl = off;       off = align256(off + nlev * 4);
+    w.thr = off;      off = align256(off + nlev * 4);
+    w.tau = off;      off = align256(off + nlev * 8);
+    w.w = off;        off = align256(off + nlev * 8);
+    w.counts = off;   off = align256(off + (size_t)capacity * 4);
+    w.blocksum = off; off = align256(off + (size_t)nblk * 8);
+    w.fampart = off;  off = align256(off + (size_t)kFamBlocks * 2 * 8);
+    w.obs = off;      off = align256(off + sizeof(pa_obs));
+    w.hashes = off;   off = align256(off + (size_t)capacity * 8);
+    w.stage = off;    off = align256(off + (size_t)kStageReplicas * words * 4);
+    w.total = off;
+    w.nblk = nblk;
+    return w;
+}
+
+// ------------------------------------------------------------------------------ helpers
+template <typename T, int THREADS>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *total)
+{
+    __shared__ T warp_tot[THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T t = lane < THREADS / 32 ? warp_tot[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < THREADS / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const T before = wid > 0 ? warp_tot[wid - 1] : T(0);
+    *total = warp_tot[THREADS / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <typename T, int THREADS>
+__device__ __forceinline__ T block_sum(T v)
+{
+    __shared__ T part[THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[wid] = v;
+    __syncthreads();
+    T t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < THREADS / 32; ++i) t += part[i];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+__device__ __forceinline__ void set_thresholds(DevState *st, double beta)
+{
+    const unsigned long long t4 = metropolis_threshold(__dmul_rn(4.0, beta));
+    const unsigned long long t8 = metropolis_threshold(__dmul_rn(8.0, beta));
+    st->tm1_4 = t4 ? (unsigned int)(t4 - 1ull) : 0u;
+    st->nz_4 = t4 ? 1u : 0u;
+    st->tm1_8 = t8 ? (unsigned int)(t8 - 1ull) : 0u;
+    st->nz_8 = t8 ? 1u : 0u;
+}
+
+// ------------------------------------------------------------------------------ setup
+__global__ void k_setup(DevState *st, long long R, int *hist, int nlev)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        DevState z{};
+        *st = z;
+        st->R_cur = R;
+        st->R_prev = 0;
+        set_thresholds(st, 0.0);
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlev; k += gridDim.x * blockDim.x) hist[k] = 0;
+}
+
+__global__ void k_zero_measure(DevState *st, int *hist, int nlev)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->sum_absM = 0;
+        st->sum_M2 = 0;
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlev; k += gridDim.x * blockDim.x) hist[k] = 0;
+}
+
+__global__ void k_thresholds(DevState *st, double beta) { set_thresholds(st, beta); }
+
+cudaError_t launch_zero_measure(DevState *st, int *hist, int N, cudaStream_t s)
+{
+    const int nlev = N + 1;
+    k_zero_measure<<<(nlev + 1023) / 1024, 1024, 0, s>>>(st, hist, nlev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thresholds(DevState *st, double beta, cudaStream_t s)
+{
+    k_thresholds<<<1, 1, 0, s>>>(st, beta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, cudaStream_t s)
+{
+    const int nlev = N + 1;
+    k_setup<<<(nlev + 1023) / 1024, 1024, 0, s>>>(st, R, hist, nlev);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ k_table
+constexpr int kTableThreads = 1024;
+
+__global__ void __launch_bounds__(kTableThreads) k_table(ResampleArgs a)
+{
+    extern __shared__ double sh_prod[];  // compacted h_k w_k, ascending k
+    __shared__ int sh_kmin;
+    __shared__ double sh_S;
+    DevState *st = a.st;
+    if (st->error) return;
+    const int N = a.L * a.L;
+    const int nlev = N + 1;
+    const int tid = threadIdx.x;
+
+    // lowest occupied level
+    int kmin_local = INT_MAX;
+    for (int k = tid; k < nlev; k += kTableThreads)
+        if (a.hist[k] > 0) kmin_local = min(kmin_local, k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kmin_local = min(kmin_local, __shfl_xor_sync(0xffffffffu, kmin_local, o));
+    if (tid == 0) sh_kmin = INT_MAX;
+    __syncthreads();
+    if ((tid & 31) == 0) atomicMin(&sh_kmin, kmin_local);
+    __syncthreads();
+    const int kmin = sh_kmin;
+    if (kmin == INT_MAX) {
+        if (tid == 0) set_error(st, PA_ERR_NUMERIC);
+        return;
+    }
+    const double dbeta = __dsub_rn(a.beta_new, a.beta_prev);
+    const int Eref = 4 * kmin - 2 * N;
+
+    // each thread owns a contiguous chunk of levels; compact the occupied ones in order
+    const int chunk = (nlev + kTableThreads - 1) / kTableThreads;
+    const int k_lo = min(tid * chunk, nlev), k_hi = min(k_lo + chunk, nlev);
+    int occ = 0;
+    for (int k = k_lo; k < k_hi; ++k) occ += a.hist[k] > 0;
+    int nocc;
+    int pos = block_exclusive_scan<int, kTableThreads>(occ, &nocc);
+    for (int k = k_lo; k < k_hi; ++k) {
+        const int h = a.hist[k];
+        if (h > 0) {
+            const int Ek = 4 * k - 2 * N;
+            const double wk = det_exp(-__dmul_rn(dbeta, (double)(Ek - Eref)));
+            a.w[k] = wk;
+            sh_prod[pos++] = __dmul_rn((double)h, wk);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double S = 0.0;
+        for (int i = 0; i < nocc; ++i) S = __dadd_rn(S, sh_prod[i]);
+        sh_S = S;
+    }
+    __syncthreads();
+    const double S = sh_S;
+    const double Rt = (double)a.R_target;
+    for (int k = k_lo; k < k_hi; ++k) {
+        if (a.hist[k] > 0) {
+            const double tau = __ddiv_rn(__dmul_rn(Rt, a.w[k]), S);
+            const double f = floor(tau);
+            a.tau[k] = tau;
+            a.fl[k] = (int)f;
+            a.thr[k] = (unsigned int)floor(__dmul_rn(__dsub_rn(tau, f), 4294967296.0));
+        }
+    }
+    if (tid == 0) {
+        const long long Rp = st->R_cur;
+        const double lnQ = __dadd_rn(-__dmul_rn(dbeta, (double)Eref), log(__ddiv_rn(S, (double)Rp)));
+        st->lnQ = lnQ;
+        st->sum_lnQ = __dadd_rn(st->sum_lnQ, lnQ);
+        st->S = S;
+        st->kmin = kmin;
+        st->R_prev = Rp;
+        set_thresholds(st, a.beta_new);
+        if (!(S > 0.0) || !isfinite(S)) set_error(st, PA_ERR_NUMERIC);
+    }
+}
+
+// ------------------------------------------------------------------------------ counts
+// Poisson(lambda) by sequential inversion (Devroye 1986, Ch. X.3); lambda >= 32 is split
+// into m = ceil(lambda / 32) independent draws of mean lambda / m.  Chunk c of parent j
+// uses Philox(ctr = (j, c, POISSON << 28, i)); u = ((x0 >> 5) 2^26 + (x1 >> 6)) 2^-53.
+__device__ long long poisson_draw(double lambda, unsigned int j, unsigned int step, unsigned int k0,
+                                  unsigned int k1)
+{
+    if (!(lambda > 0.0)) return 0;
+    long long m = 1;
+    if (lambda >= 32.0) m = (long long)ceil(__ddiv_rn(lambda, 32.0));
+    const double mu = __ddiv_rn(lambda, (double)m);
+    const double p0 = det_exp(-mu);
+    long long total = 0;
+    for (long long c = 0; c < m; ++c) {
+        const uint4 x = philox(make_uint4(j, (unsigned int)c, kStreamPoisson << 28, step), k0, k1);
+        const double u = __dmul_rn(__dadd_rn(__dmul_rn((double)(x.x >> 5), 67108864.0), (double)(x.y >> 6)),
+                                   1.0 / 9007199254740992.0);
+        double p = p0, F = p0;
+        long long k = 0;
+        while (u >= F && k < 1000) {
+            k = k + 1;
+            p = __ddiv_rn(__dmul_rn(p, mu), (double)k);
+            F = __dadd_rn(F, p);
+        }
+        total += k;
+    }
+    return total;
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_counts(ResampleArgs a)
+{
+    DevState *st = a.st;
+    if (st->error) return;
+    const long long Rp = st->R_prev;
+    const long long base = (long long)blockIdx.x * kCountBlockItems;
+    long long sum = 0;
+#pragma unroll
+    for (int it = 0; it < kCountItems; ++it) {
+        const long long j = base + it * kCountThreads + threadIdx.x;
+        if (j < Rp) {
+            const int k = a.level_src[j];
+            long long r;
+            if (a.kind == PA_RESAMPLE_NEAREST) {
+                const uint4 x = philox(make_uint4((unsigned int)j, 0u, kStreamResample << 28, a.step), a.k0, a.k1);
+                r = (long long)a.fl[k] + (x.x <= a.thr[k] ? 1 : 0);
+            } else {
+                r = poisson_draw(a.tau[k], (unsigned int)j, a.step, a.k0, a.k1);
+            }
+            if (r > INT_MAX) r = INT_MAX;  // the capacity check rejects this population
+            a.counts[j] = (int)r;
+            sum += r;
+        }
+    }
+    const long long t = block_sum<long long, kCountThreads>(sum);
+    if (threadIdx.x == 0) a.blocksum[blockIdx.x] = t;
+}
+
+// ------------------------------------------------------------------------------ scan
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(ResampleArgs a)
+{
+    DevState *st = a.st;
+    if (st->error) return;
+    const long long Rp = st->R_prev;
+    const long long nb = (Rp + kCountBlockItems - 1) / kCountBlockItems;
+    long long carry = 0;
+    for (long long start = 0; start < nb; start += kScanThreads) {
+        const long long b = start + threadIdx.x;
+        const long long v = b < nb ? a.blocksum[b] : 0;
+        long long tot;
+        const long long ex = block_exclusive_scan<long long, kScanThreads>(v, &tot);
+        if (b < nb) a.blocksum[b] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        if (carry > a.capacity) set_error(st, PA_ERR_CAPACITY);
+        else if (carry == 0) set_error(st, PA_ERR_NUMERIC);
+        else st->R_cur = carry;
+    }
+}
+
+// ------------------------------------------------------------------------------ copy
+__global__ void __launch_bounds__(kCountThreads) k_copy(ResampleArgs a, int chunks16)
+{
+    __shared__ int sh_cnt[kCountBlockItems];
+    __shared__ long long sh_off[kCountBlockItems];
+    DevState *st = a.st;
+    if (st->error) return;
+    const long long Rp = st->R_prev;
+    const long long base = (long long)blockIdx.x * kCountBlockItems;
+    if (base >= Rp) return;
+    // thread t scans parents base + 4t .. base + 4t + 3
+    int c[kCountItems];
+    long long local = 0;
+#pragma unroll
+    for (int it = 0; it < kCountItems; ++it) {
+        const long long j = base + threadIdx.x * kCountItems + it;
+        c[it] = j < Rp ? a.counts[j] : 0;
+        local += c[it];
+    }
+    long long tot;
+    long long off = block_exclusive_scan<long long, kCountThreads>(local, &tot) + a.blocksum[blockIdx.x];
+#pragma unroll
+    for (int it = 0; it < kCountItems; ++it) {
+        sh_cnt[threadIdx.x * kCountItems + it] = c[it];
+        sh_off[threadIdx.x * kCountItems + it] = off;
+        off += c[it];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.spins_src);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.spins_dst);
+    const int nloc = (int)min((long long)kCountBlockItems, Rp - base);
+    for (int p = wid; p < nloc; p += kCountThreads / 32) {
+        const int cnt = sh_cnt[p];
+        if (cnt == 0) continue;
+        const long long j = base + p;
+        const long long o = sh_off[p];
+        for (int ch = lane; ch < chunks16; ch += 32) {
+            const uint4 v = src[(size_t)j * chunks16 + ch];
+            for (int k = 0; k < cnt; ++k) dst[(size_t)(o + k) * chunks16 + ch] = v;
+        }
+        const int lv = a.level_src[j], mg = a.mag_src[j], fm = a.fam_src[j];
+        for (int k = lane; k < cnt; k += 32) {
+            a.level_dst[o + k] = lv;
+            a.mag_dst[o + k] = mg;
+            a.fam_dst[o + k] = fm;
+        }
+    }
+}
+
+cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
+{
+    const int nlev = a.L * a.L + 1;
+    const size_t smem = (size_t)nlev * sizeof(double);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    k_table<<<1, kTableThreads, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned int nblk = (unsigned int)a.nblk;
+    k_counts<<<nblk, kCountThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scan<<<1, kScanThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int chunks16 = bytes_per_replica(a.L) / 16;
+    k_copy<<<nblk, kCountThreads, 0, s>>>(a, chunks16);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ step 4
+__global__ void __launch_bounds__(256) k_families(const DevState *st, const int *fam, long long *part)
+{
+    const long long R = st->R_cur;
+    long long cnt = 0, s2 = 0;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < R;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int f = fam[j];
+        if (j > 0 && fam[j - 1] == f) continue;
+        // run start: gallop, then bisect, for the first index with a different id
+        long long lo = j, stepw = 1;
+        while (lo + stepw < R && fam[lo + stepw] == f) {
+            lo += stepw;
+            stepw <<= 1;
+        }
+        long long hi = min(lo + stepw, R);
+        while (hi - lo > 1) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (fam[mid] == f) lo = mid;
+            else hi = mid;
+        }
+        const long long len = hi - j;
+        cnt += 1;
+        s2 += len * len;
+    }
+    const long long c = block_sum<long long, 256>(cnt);
+    const long long t = block_sum<long long, 256>(s2);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = c;
+        part[2 * blockIdx.x + 1] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_obs(ObsArgs a)
+{
+    const DevState *st = a.st;
+    const int N = a.L * a.L;
+    long long sE = 0, sE2 = 0;
+    for (int k = threadIdx.x; k <= N; k += 1024) {
+        const long long h = a.hist[k];
+        const long long E = 4LL * k - 2LL * N;
+        sE += h * E;
+        sE2 += h * E * E;
+    }
+    long long fc = 0, f2 = 0;
+    for (int b = threadIdx.x; b < kFamBlocks; b += 1024) {
+        fc += a.fampart[2 * b];
+        f2 += a.fampart[2 * b + 1];
+    }
+    sE = block_sum<long long, 1024>(sE);
+    sE2 = block_sum<long long, 1024>(sE2);
+    fc = block_sum<long long, 1024>(fc);
+    f2 = block_sum<long long, 1024>(f2);
+    if (threadIdx.x != 0) return;
+    const long long R = st->R_cur;
+    const double Rd = (double)R, Nd = (double)N, b = a.beta;
+    const double meanE = __ddiv_rn((double)sE, Rd);
+    const double meanE2 = __ddiv_rn((double)sE2, Rd);
+    pa_obs o;
+    o.step = a.step;
+    o.R = R;
+    o.beta = a.beta;
+    o.dbeta = a.dbeta;
+    o.e = __ddiv_rn(meanE, Nd);
+    o.C = __ddiv_rn(__dmul_rn(__dmul_rn(b, b), __dsub_rn(meanE2, __dmul_rn(meanE, meanE))), Nd);
+    o.m = __ddiv_rn(__ddiv_rn((double)st->sum_absM, Rd), Nd);
+    o.m2 = __ddiv_rn(__ddiv_rn((double)st->sum_M2, Rd), __dmul_rn(Nd, Nd));
+    o.chi = __dmul_rn(__dmul_rn(b, Nd), __dsub_rn(o.m2, __dmul_rn(o.m, o.m)));
+    o.lnQ = st->lnQ;
+    o.minus_betaF = __dadd_rn(__dmul_rn(Nd, 0.6931471805599453094), st->sum_lnQ);
+    o.rho_t = __ddiv_rn((double)f2, Rd);
+    o.families = fc;
+    o.sum_E = sE;
+    o.sum_E2 = sE2;
+    o.sum_absM = (long long)st->sum_absM;
+    o.sum_M2 = (long long)st->sum_M2;
+    o.sum_size2 = f2;
+    o.theta = a.theta;
+    o.status = st->error;
+    *a.dst = o;
+}
+
+cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s)
+{
+    k_families<<<kFamBlocks, 256, 0, s>>>(a.st, a.fam, a.fampart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_obs<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ hashes
+// Canonical packed row: 32 columns per word, bit b of word w = spin at column 32w + b.
+// The even-column half supplies the even bits, the odd-column half the odd bits.
+__device__ __forceinline__ unsigned int spread16(unsigned int x)
+{
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+template <typename W>
+__device__ __forceinline__ unsigned int canonical_word(W E, W O, int w)
+{
+    const unsigned int e = (unsigned int)(E >> (16 * w)) & 0xFFFFu;
+    const unsigned int o = (unsigned int)(O >> (16 * w)) & 0xFFFFu;
+    return spread16(e) | (spread16(o) << 1);
+}
+
+template <typename W>
+__global__ void k_hashes(int L, const W *spins, long long R_host, const DevState *st, unsigned long long *out)
+{
+    const long long R = st ? st->R_cur : R_host;
+    const int nw = (L + 31) / 32;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < R;
+         j += (long long)gridDim.x * blockDim.x) {
+        const W *rep = spins + (size_t)j * 2 * L;
+        unsigned long long h = 0xcbf29ce484222325ull;
+        for (int r = 0; r < L; ++r) {
+            const W E = rep[2 * r], O = rep[2 * r + 1];
+            for (int w = 0; w < nw; ++w) {
+                const unsigned int v = canonical_word<W>(E, O, w);
+                for (int byte = 0; byte < 4; ++byte) {
+                    h ^= (unsigned long long)((v >> (8 * byte)) & 0xFFu);
+                    h *= 0x100000001b3ull;
+                }
+            }
+        }
+        out[j] = h;
+    }
+}
+
+template <typename W>
+__global__ void k_export(int L, const W *spins, long long first, long long count, unsigned int *out)
+{
+    const int nw = (L + 31) / 32;
+    const long long total = count * L;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long jj = t / L;
+        const int r = (int)(t % L);
+        const W *rep = spins + (size_t)(first + jj) * 2 * L;
+        const W E = rep[2 * r], O = rep[2 * r + 1];
+        for (int w = 0; w < nw; ++w) out[(size_t)t * nw + w] = canonical_word<W>(E, O, w);
+    }
+}
+
+cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
+                          unsigned long long *out, cudaStream_t s)
+{
+    const unsigned int blocks = (unsigned int)min((R + 255) / 256 + 1, 4096LL);
+    if (L / 2 > 32) k_hashes<unsigned long long><<<blocks, 256, 0, s>>>(L, (const unsigned long long *)spins, R, st, out);
+    else k_hashes<unsigned int><<<blocks, 256, 0, s>>>(L, (const unsigned int *)spins, R, st, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(int L, const void *spins, long long first, long long count, unsigned int *out,
+                          cudaStream_t s)
+{
+    const unsigned int blocks = (unsigned int)min((count * L + 255) / 256 + 1, 4096LL);
+    if (L / 2 > 32) k_export<unsigned long long><<<blocks, 256, 0, s>>>(L, (const unsigned long long *)spins, first, count, out);
+    else k_export<unsigned int><<<blocks, 256, 0, s>>>(L, (const unsigned int *)spins, first, count, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pa
