@@ -1,0 +1,321 @@
+"""Throughput of the population-annealing hot path on GB300 (arXiv:2102.06611, Sec. II).
+
+Workload (default): 2D Ising, L = 64 periodic, R = 10^6 replicas (512 B each, packed,
+double-buffered), 301 temperatures beta = i / 300, theta = 10 checkerboard Metropolis
+sweeps per temperature, nearest-integer resampling, seed 7 (seed 7 + rank on rank > 0).
+One bench step = one temperature step of the method: resampling (table, copy numbers,
+prefix sum, tree-ordered copy), theta sweeps with the fused measurement, and the step-4
+record (families, observables) written on the device.
+
+Metric: Metropolis spin-flip attempts per ns, attempts = N * R_i * theta summed over the
+timed steps, R_i read back from the device records after the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L_DEFAULT, R_DEFAULT, THETA, N_TEMPS, SEED = 64, 1_000_000, 10, 301, 7
+METRIC = "Metropolis flips/ns on 1 GB300"
+UNIT = "attempts/ns"
+KERNELS_PER_STEP = 8  # k_table, k_counts, k_scan, k_copy, k_zero_measure, k_sweep, k_families, k_obs
+
+# Integer roofline of the sweep kernel (derivation in the design doc): the algorithm needs one
+# Philox4x32-10 call per 4 attempts, i.e. 20 32x32->64-bit multiplies (mul.wide) per 4
+# attempts.  A 32-bit integer multiply-add issues at 64 per clock per SM; the widening
+# multiply writes two registers and issues at half that rate, 32 per clock per SM.
+# Peak attempts/ns = SMs * MULWIDE_PER_SM_CLK * f_SM / (20 / 4).
+SMS = 152
+MULWIDE_PER_SM_CLK = 32.0
+MULWIDE_PER_ATTEMPT = 20.0 / 4.0
+# DRAM bytes per attempt of k_sweep<64> from one ncu capture (profiles/k_sweep_L64_R262144_full.md);
+# set to None whenever the kernel changes until it is captured again.
+SWEEP64_DRAM_BYTES_PER_ATTEMPT = 210.2e6 / (262144 * 4096 * 10)
+
+
+def _parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--L", type=int, default=L_DEFAULT)
+    p.add_argument("--R", type=int, default=R_DEFAULT)
+    p.add_argument("--theta", type=int, default=THETA)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ oracle timing
+def oracle_rate(L: int, R_sample: int, steps: int, theta: int, seed: int):
+    """The CPU oracle as it stands on one host core: attempts / ns over `steps` temperature
+    steps of a population of R_sample replicas (the per-attempt cost does not depend on R)."""
+    import oracle
+    pa = oracle.PA(L, R_sample, seed)
+    pa.init()
+    attempts = 0
+    t0 = time.perf_counter()
+    for i in range(1, steps + 1):
+        pa.resample(i / (N_TEMPS - 1))
+        pa.sweep(theta)
+        attempts += L * L * pa.R * theta
+        pa.observables()
+    dt = time.perf_counter() - t0
+    return attempts / (dt * 1e9), attempts, dt
+
+
+def cpu_baseline(L: int, theta: int) -> dict:
+    R_sample, steps = 1000, 10
+    v, att, dt = oracle_rate(L, R_sample, steps, theta, SEED)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"L={L}, R={R_sample}, {steps} temperature steps beta=i/300, theta={theta}: "
+                      f"{att:.3g} attempts in {dt:.1f} s (single-threaded C oracle)"}
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2102_06611_gb300 import OBS_BYTES, PopulationAnnealing, pa_obs
+
+    L, R, theta = args.L, args.R, args.theta
+    N = L * L
+    K, W = args.steps, args.warmup
+    assert W + K <= N_TEMPS - 1, "schedule has 300 steps"
+    stream = torch.cuda.current_stream(dev)
+    pa = PopulationAnnealing(L, R, SEED + rank, device=dev, stream=stream)
+    records = torch.zeros((K, (OBS_BYTES + 7) // 8), dtype=torch.int64, device=dev)
+
+    def beta(i):
+        return i / (N_TEMPS - 1)
+
+    for i in range(1, W + 1):
+        pa.resample(beta(i))
+        pa.anneal_step(theta)
+        pa.record(records[0])
+    torch.cuda.synchronize()
+
+    sw_start = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sw_end = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    t_start.record(stream)
+    for s in range(K):
+        i = W + 1 + s
+        pa.resample(beta(i))
+        sw_start[s].record(stream)
+        pa.anneal_step(theta)
+        sw_end[s].record(stream)
+        pa.record(records[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    sweep_ms = sum(a.elapsed_time(b) for a, b in zip(sw_start, sw_end))
+
+    recs = records.cpu().numpy()
+    import ctypes
+    Rs = []
+    for s in range(K):
+        o = pa_obs.from_buffer_copy(recs[s].tobytes()[: ctypes.sizeof(pa_obs)])
+        assert o.status == 0, f"device error {o.status}"
+        Rs.append(o.R)
+    attempts = float(N) * float(sum(Rs)) * theta
+
+    # end to end through the public API with host results: each step reads its record
+    # (pa_obs, D2H) and synchronises
+    pa2 = pa
+    e2e_steps = min(K, N_TEMPS - 1 - (W + K))
+    e2e = None
+    if e2e_steps >= 3:
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_att = 0.0
+        ev0.record(stream)
+        for s in range(e2e_steps):
+            i = W + K + 1 + s
+            pa2.resample(beta(i))
+            pa2.anneal_step(theta)
+            o = pa2.observables()
+            e2e_att += float(N) * o["R"] * theta
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = ev0.elapsed_time(ev1)
+        e2e = {"value": e2e_att / (e2e_ms * 1e6), "unit": UNIT, "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": ctypes.sizeof(pa_obs), "steps": e2e_steps,
+               "note": "public API per step: pa_resample(beta) + pa_anneal_step(theta) + pa_observables "
+                       "(host record, synchronising); beta passes by value, no input tensor is copied"}
+
+    if world > 1:
+        t = torch.tensor([ms, sweep_ms, attempts], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:2], op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum[2:], op=dist.ReduceOp.SUM)
+        ms, sweep_ms, attempts = float(tmax[0]), float(tmax[1]), float(tsum[2])
+
+    if rank == 0:
+        value = attempts / (ms * 1e6)
+        sweep_rate = (attempts / world) / (sweep_ms * 1e6)
+        f_mhz = clk["sm_mhz"] or 2070.0
+        peak = SMS * MULWIDE_PER_SM_CLK * f_mhz * 1e6 / MULWIDE_PER_ATTEMPT / 1e9  # attempts/ns
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": K,
+            "warmup": W,
+            "ms_per_step": ms / K,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u32",
+            "data": "synthetic (simple sampling at beta=0, Philox4x32-10 seed 7+rank)",
+            "config": {"workload": f"2D Ising PA L={L} R={R} theta={theta} beta=i/300 nearest-integer",
+                       "L": L, "R": R, "theta": theta, "temperatures": N_TEMPS, "resampling": "nearest",
+                       "parallelism": f"independent runs x{world}" if world > 1 else "single run",
+                       "l2": "inputs larger than L2 (2 x %.0f MB spin buffers)" % (R * L * 2 * 4 / 1e6)},
+            "roofline": {"bound": "alu", "kernel": f"k_sweep<{L}>", "achieved": sweep_rate, "peak": peak,
+                         "unit": UNIT, "frac": sweep_rate / peak,
+                         "traffic": (SWEEP64_DRAM_BYTES_PER_ATTEMPT * attempts / world / K
+                                     if (L == 64 and SWEEP64_DRAM_BYTES_PER_ATTEMPT) else None),
+                         "traffic_unit": "DRAM bytes per launch (ncu, scaled from R=262144 by attempts)",
+                         "peak_basis": "152 SM x 32 mul.wide/clk/SM x median SM clock / 5 mul.wide per "
+                                       "attempt (one Philox4x32-10 call per 4 attempts)"},
+            "sweep_share": sweep_ms / ms,
+            "clocks": clk,
+            "gpu_launches": KERNELS_PER_STEP * K,
+            "wall_s": wall,
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(L, theta)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The CPU oracle as it stands, timed on the host: the reference arm of this build."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    L, theta = args.L, args.theta
+    R_sample = 120
+    W, K = args.warmup, args.steps
+    import oracle
+    pa = oracle.PA(L, R_sample, SEED)
+    pa.init()
+    for i in range(1, W + 1):
+        pa.resample(i / (N_TEMPS - 1))
+        pa.sweep(theta)
+    att = 0
+    t0 = time.perf_counter()
+    for s in range(K):
+        pa.resample((W + 1 + s) / (N_TEMPS - 1))
+        pa.sweep(theta)
+        pa.observables()
+        att += L * L * pa.R * theta
+    dt = time.perf_counter() - t0
+    v = att / (dt * 1e9)
+    sample = f"L={L}, R={R_sample} per step (bounded sample of the R={args.R} population), theta={theta}"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
+        "warmup": W, "ms_per_step": dt * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i8", "data": "synthetic",
+        "config": {"workload": f"2D Ising PA L={L} R={args.R} theta={theta} beta=i/300 nearest-integer",
+                   "L": L, "R": args.R, "theta": theta},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = _parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
