@@ -46,7 +46,8 @@ typedef enum {
     PA_ERR_CAPACITY = 3,    /* resampled population larger than the buffer capacity */
     PA_ERR_CUDA = 4,        /* a CUDA runtime call failed */
     PA_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-    PA_ERR_NUMERIC = 6      /* empty population or non-finite weights */
+    PA_ERR_NUMERIC = 6,     /* empty population or non-finite weights */
+    PA_ERR_TOO_LARGE = 7    /* size above the fixed maximum of pa_copy_numbers_static */
 } pa_status;
 
 typedef enum {
@@ -162,6 +163,28 @@ pa_status pa_replicas(pa_ctx *ctx, int *level, int *mag, int *fam);
 pa_status pa_copy_counts(pa_ctx *ctx, int *host_out, long long *count_out);
 pa_status pa_hashes(pa_ctx *ctx, unsigned long long *host_out);
 pa_status pa_export_spins(pa_ctx *ctx, long long first, long long count, unsigned int *host_out);
+
+/* Copy numbers of one resampling step WITHOUT a workspace (the paper has no counterpart: this
+   is a deployment variant of the level-table / copy-number / prefix-sum kernels of
+   pa_resample, not a step of the method).
+   For callers that cannot provide the workspace pa_resample needs -- code that may only touch
+   the arrays it is handed (e.g. a plugin inside another program's memory pool), or a process
+   that fixes its device memory at start-up and forbids any later cudaMalloc.  The caller
+   passes the energy levels of the R_prev parents (device int32[R_prev], level k = (E + 2N)/4)
+   and receives their copy numbers r_j in counts_dev (device int32[R_prev]), exactly as
+   pa_resample would draw them for the same (seed, step i, beta_prev -> beta_new, R_target,
+   kind); *lnQ_out gets ln Q_i and *R_new_out the new population size.  The scratch (histogram,
+   level tables, block sums) is one fixed array of 493,056 bytes in the library image, present
+   on every GPU that loads the library until the process exits.  Limits: L one of the supported
+   sizes (so at most 16385 levels) and 1 <= R_prev <= 4,194,304; a larger R_prev returns
+   PA_ERR_TOO_LARGE.  Allocates nothing.  The first call on a device also looks up the array's
+   device address (once per device); make that first call before any stream capture.  All calls
+   share the array and each clears what it needs first; calls that overlap on the GPU (e.g. on
+   two streams) race.  Synchronises `stream`. */
+pa_status pa_copy_numbers_static(int L, long long R_target, long long R_prev, const int *level_dev,
+                                 double beta_prev, double beta_new, unsigned int step,
+                                 unsigned long long seed, int kind, int *counts_dev,
+                                 double *lnQ_out, long long *R_new_out, void *stream);
 
 /* Message for the last failing call on ctx (static storage owned by the context). */
 const char *pa_last_error(const pa_ctx *ctx);

@@ -13,9 +13,10 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-PA_OK, PA_ERR_INVALID_ARG, PA_ERR_STATE, PA_ERR_CAPACITY, PA_ERR_CUDA, PA_ERR_TIMEOUT, PA_ERR_NUMERIC = range(7)
+(PA_OK, PA_ERR_INVALID_ARG, PA_ERR_STATE, PA_ERR_CAPACITY, PA_ERR_CUDA, PA_ERR_TIMEOUT, PA_ERR_NUMERIC,
+ PA_ERR_TOO_LARGE) = range(8)
 STATUS_NAMES = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_STATE", 3: "PA_ERR_CAPACITY",
-                4: "PA_ERR_CUDA", 5: "PA_ERR_TIMEOUT", 6: "PA_ERR_NUMERIC"}
+                4: "PA_ERR_CUDA", 5: "PA_ERR_TIMEOUT", 6: "PA_ERR_NUMERIC", 7: "PA_ERR_TOO_LARGE"}
 PA_RESAMPLE_NEAREST, PA_RESAMPLE_POISSON = 0, 1
 
 
@@ -70,6 +71,10 @@ SIGNATURES = {
     "pa_copy_counts": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_longlong)]),
     "pa_hashes": (ctypes.c_int, [_vp, _vp]),
     "pa_export_spins": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_longlong, _vp]),
+    "pa_copy_numbers_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong, _vp,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_uint,
+                                              ctypes.c_ulonglong, ctypes.c_int, _vp, _P(ctypes.c_double),
+                                              _P(ctypes.c_longlong), _vp]),
     "pa_last_error": (ctypes.c_char_p, [_vp]),
     "pa_destroy": (None, [_vp]),
 }

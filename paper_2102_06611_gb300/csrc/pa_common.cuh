@@ -6,7 +6,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/pa.h"
+#include "pa.h"
 
 namespace pa {
 

@@ -3,7 +3,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/pa.h"
+#include "pa.h"
 
 namespace pa {
 
@@ -76,6 +76,7 @@ struct ResampleArgs {
 };
 
 cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s);
+cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s);
 cudaError_t launch_thresholds(DevState *st, double beta, cudaStream_t s);
 cudaError_t launch_zero_measure(DevState *st, int *hist, int N, cudaStream_t s);
 cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, cudaStream_t s);

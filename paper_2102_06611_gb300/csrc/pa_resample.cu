@@ -384,6 +384,28 @@ cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Level table, copy numbers and their total, without the replica copy (used by the
+// no-workspace entry point, whose scratch is a static device array).
+cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s)
+{
+    const int nlev = a.L * a.L + 1;
+    const size_t smem = (size_t)nlev * sizeof(double);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    k_table<<<1, kTableThreads, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_counts<<<(unsigned int)a.nblk, kCountThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scan<<<1, kScanThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------ step 4
 __global__ void __launch_bounds__(256) k_families(const DevState *st, const int *fam, long long *part)
 {
