@@ -32,17 +32,19 @@ METRIC = "Metropolis flips/ns on 1 GB300"
 UNIT = "attempts/ns"
 KERNELS_PER_STEP = 8  # k_table, k_counts, k_scan, k_copy, k_zero_measure, k_sweep, k_families, k_obs
 
-# Integer roofline of the sweep kernel (derivation in the design doc): the algorithm needs one
-# Philox4x32-10 call per 4 attempts, i.e. 20 32x32->64-bit multiplies (mul.wide) per 4
-# attempts.  A 32-bit integer multiply-add issues at 64 per clock per SM; the widening
-# multiply writes two registers and issues at half that rate, 32 per clock per SM.
-# Peak attempts/ns = SMs * MULWIDE_PER_SM_CLK * f_SM / (20 / 4).
+# Integer roofline of the sweep kernel (derivation in the design doc).  Peak: 152 SMs x 4
+# partitions x 32 lanes issue 128 32-bit integer operations per clock per SM.  Algorithmic
+# 32-bit integer operations per attempt of the bit-plane Metropolis step, per 32-site word:
+# 2 Philox4x32-10 calls for 8 bit planes (each call 20 widening multiplies counted as 2 ops
+# and 20 three-input XORs: 60 ops), 8 planes x 5 ops of bit-serial comparison, 15 ops of
+# neighbour classes and update; plus one 62-op low-bits draw for the 2^-8 of sites whose top
+# 8 bits tie with the threshold.
 SMS = 152
-MULWIDE_PER_SM_CLK = 32.0
-MULWIDE_PER_ATTEMPT = 20.0 / 4.0
-# DRAM bytes per attempt of k_sweep<64> from one ncu capture (profiles/k_sweep_L64_R262144_full.md);
-# set to None whenever the kernel changes until it is captured again.
-SWEEP64_DRAM_BYTES_PER_ATTEMPT = 210.2e6 / (262144 * 4096 * 10)
+INT_OPS_PER_SM_CLK = 128.0
+OPS_PER_ATTEMPT = (2 * 60 + 8 * 5 + 15) / 32 + 62 / 256
+# DRAM bytes per attempt of k_sweep<64> from one ncu capture; None until the current kernel
+# has been captured.
+SWEEP64_DRAM_BYTES_PER_ATTEMPT = None
 
 
 def _parse_args():
@@ -234,7 +236,8 @@ def run_ours(args):
         value = attempts / (ms * 1e6)
         sweep_rate = (attempts / world) / (sweep_ms * 1e6)
         f_mhz = clk["sm_mhz"] or 2070.0
-        peak = SMS * MULWIDE_PER_SM_CLK * f_mhz * 1e6 / MULWIDE_PER_ATTEMPT / 1e9  # attempts/ns
+        peak_tops = SMS * INT_OPS_PER_SM_CLK * f_mhz * 1e6 / 1e12           # int32 Tops/s
+        achieved_tops = sweep_rate * 1e9 * OPS_PER_ATTEMPT / 1e12
         line = {
             "metric": METRIC,
             "value": value,
@@ -252,13 +255,16 @@ def run_ours(args):
                        "L": L, "R": R, "theta": theta, "temperatures": N_TEMPS, "resampling": "nearest",
                        "parallelism": f"independent runs x{world}" if world > 1 else "single run",
                        "l2": "inputs larger than L2 (2 x %.0f MB spin buffers)" % (R * L * 2 * 4 / 1e6)},
-            "roofline": {"bound": "alu", "kernel": f"k_sweep<{L}>", "achieved": sweep_rate, "peak": peak,
-                         "unit": UNIT, "frac": sweep_rate / peak,
+            "roofline": {"bound": "alu", "kernel": f"k_sweep<{L}>", "achieved": achieved_tops,
+                         "peak": peak_tops, "unit": "Tops/s (int32)", "frac": achieved_tops / peak_tops,
                          "traffic": (SWEEP64_DRAM_BYTES_PER_ATTEMPT * attempts / world / K
                                      if (L == 64 and SWEEP64_DRAM_BYTES_PER_ATTEMPT) else None),
                          "traffic_unit": "DRAM bytes per launch (ncu, scaled from R=262144 by attempts)",
-                         "peak_basis": "152 SM x 32 mul.wide/clk/SM x median SM clock / 5 mul.wide per "
-                                       "attempt (one Philox4x32-10 call per 4 attempts)"},
+                         "achieved_attempts_per_ns": sweep_rate,
+                         "peak_attempts_per_ns": peak_tops * 1e3 / OPS_PER_ATTEMPT,
+                         "ops_per_attempt": OPS_PER_ATTEMPT,
+                         "peak_basis": "152 SM x 128 int32 ops/clk/SM x median SM clock (sampled); "
+                                       "algorithmic ops per attempt of the bit-plane Metropolis step"},
             "sweep_share": sweep_ms / ms,
             "clocks": clk,
             "gpu_launches": KERNELS_PER_STEP * K,

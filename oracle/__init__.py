@@ -32,7 +32,7 @@ _SOURCES = ["pa_oracle.c", "exact_ising.c"]
 _lock = threading.Lock()
 _lib = None
 
-STREAM_INIT, STREAM_SWEEP, STREAM_RESAMPLE, STREAM_POISSON = 0, 1, 2, 3
+STREAM_INIT, STREAM_SWEEP, STREAM_RESAMPLE, STREAM_POISSON, STREAM_REFINE = 0, 1, 2, 3, 4
 NEAREST, POISSON = 0, 1
 
 
@@ -83,6 +83,9 @@ def lib():
                 "orc_sweep_replica_t0": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                                 ctypes.c_uint32, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_int, i8p]),
+                "orc_sweep_uniform": (ctypes.c_uint32, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                                        ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                                        ctypes.c_int]),
                 "orc_poisson": (ctypes.c_int64, [ctypes.c_double, ctypes.c_uint64,
                                                  ctypes.c_uint32, ctypes.c_uint32]),
                 "orc_resample_levels": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
@@ -181,6 +184,11 @@ def sweep_replica(L: int, seed: int, step: int, slot: int, beta: float, theta: i
     lib().orc_sweep_replica_t0(L, seed, step, slot, float(beta), int(t0), int(theta),
                                _ptr(out, ctypes.c_int8))
     return out
+
+
+def sweep_uniform(L: int, seed: int, step: int, slot: int, tag: int, r: int, p: int) -> int:
+    """The 32-bit uniform of colour-site p of row r in sweep-colour `tag` = 2t + q."""
+    return int(lib().orc_sweep_uniform(L, seed, step, slot, tag, r, p))
 
 
 def poisson(lam: float, seed: int, j: int, step: int) -> int:

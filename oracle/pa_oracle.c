@@ -213,11 +213,38 @@ void orc_init_replica(int L, uint64_t seed, uint32_t j, int8_t *s)
  * colour do not interact, so visiting them one after another is the same as updating
  * them together.  Acceptance is min(1, exp(-beta dE)) with dE = 4a - 8, a = number of
  * aligned neighbours: a <= 2 always flips; a = 3 flips iff x < floor(e^{-4 beta} 2^32);
- * a = 4 flips iff x < floor(e^{-8 beta} 2^32).
- * Random word x for site (r, c) of colour q in sweep t of step i, replica slot j:
- * with p = c / 2 (index of the site among the L/2 colour-q sites of row r),
- * x = lane (p mod 4) of Philox(ctr = (r * 16 + p / 4, j, (SWEEP << 28) | (2t + q), i)).
+ * a = 4 flips iff x < floor(e^{-8 beta} 2^32), x a uniform 32-bit integer.
+ *
+ * The uniform x of site (r, c) of colour q in sweep t of step i, replica slot j, is built
+ * from two independent parts (every bit is an independent uniform bit, so x is uniform on
+ * [0, 2^32)).  Let p = c / 2 (index of the site among the L/2 colour-q sites of row r),
+ * h = p / 32, b = p mod 32, nh = ceil(L / 64) (32-bit chunks per half-row), tag =
+ * (2t + q):
+ *   top 8 bits:   bit (31 - k) of x, k = 0..7, is bit b of word (k mod 4) of
+ *                 Philox(ctr = (2 (nh r + h) + k / 4, j, (SWEEP << 28) | tag, i));
+ *   low 24 bits:  the low 24 bits of word 0 of
+ *                 Philox(ctr = (64 r + p, j, (REFINE << 28) | tag, i)).
  * ---------------------------------------------------------------------------------- */
+enum { STREAM_REFINE = 4 };
+
+uint32_t orc_sweep_uniform(int L, uint64_t seed, uint32_t step, uint32_t slot, int tag, int r, int p)
+{
+    int nh = (L + 63) / 64;
+    int h = p / 32, b = p % 32;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t planes[8];
+    for (int call = 0; call < 2; ++call) {
+        uint32_t ctr[4] = {(uint32_t)(2 * (nh * r + h) + call), slot,
+                           ((uint32_t)STREAM_SWEEP << 28) | (uint32_t)tag, step};
+        orc_philox4x32_10(ctr, key, planes + 4 * call);
+    }
+    uint32_t x = 0;
+    for (int k = 0; k < 8; ++k) x |= ((planes[k] >> b) & 1u) << (31 - k);
+    uint32_t low = philox_word(seed, (uint32_t)(64 * r + p), slot,
+                               ((uint32_t)STREAM_REFINE << 28) | (uint32_t)tag, step, 0);
+    return x | (low & 0xFFFFFFu);
+}
+
 void orc_sweep_replica_t0(int L, uint64_t seed, uint32_t step, uint32_t slot, double beta,
                           int t0, int theta, int8_t *s)
 {
@@ -231,10 +258,7 @@ void orc_sweep_replica_t0(int L, uint64_t seed, uint32_t step, uint32_t slot, do
                     int si = s[site(L, r, c)];
                     int a = (s[site(L, r - 1, c)] == si) + (s[site(L, r + 1, c)] == si) +
                             (s[site(L, r, c - 1)] == si) + (s[site(L, r, c + 1)] == si);
-                    int p = c / 2;
-                    uint32_t x = philox_word(seed, (uint32_t)(r * 16 + p / 4), slot,
-                                             ((uint32_t)STREAM_SWEEP << 28) | (uint32_t)(2 * t + q),
-                                             step, p % 4);
+                    uint32_t x = orc_sweep_uniform(L, seed, step, slot, 2 * t + q, r, c / 2);
                     int flip;
                     if (a <= 2) flip = 1;
                     else if (a == 3) flip = (uint64_t)x < T4;

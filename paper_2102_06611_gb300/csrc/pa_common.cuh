@@ -8,6 +8,18 @@
 
 #include "pa.h"
 
+// Rows of a replica held by one lane in the sweep kernel (tuning knobs; lanes per replica =
+// L / rows, a power of two <= 32).
+#ifndef PA_RPL_32
+#define PA_RPL_32 4
+#endif
+#ifndef PA_RPL_64
+#define PA_RPL_64 4
+#endif
+#ifndef PA_RPL_128
+#define PA_RPL_128 4
+#endif
+
 namespace pa {
 
 // ------------------------------------------------------------------------------------
@@ -28,7 +40,11 @@ struct Geo {
     static constexpr int H = L / 2;                      // sites per half-row
     static constexpr bool WIDE = (H > 32);
     using W = typename std::conditional<WIDE, unsigned long long, unsigned int>::type;
-    static constexpr int RPL = (L == 12 || L == 24 || L == 48) ? 3 : (L == 128 ? 4 : 2);
+    static constexpr int RPL = (L == 12 || L == 24 || L == 48) ? 3
+                               : L == 128                     ? PA_RPL_128
+                               : L == 64                      ? PA_RPL_64
+                               : L == 32                      ? PA_RPL_32
+                                                              : 2;
     static constexpr int G = L / RPL;                    // lanes per replica (power of 2)
     static constexpr int RPW = 32 / G;                   // replicas per warp
     static constexpr int WORD_BYTES = WIDE ? 8 : 4;
@@ -49,7 +65,13 @@ constexpr unsigned int kPhiloxM1 = 0xCD9E8D57u;
 constexpr unsigned int kPhiloxW0 = 0x9E3779B9u;
 constexpr unsigned int kPhiloxW1 = 0xBB67AE85u;
 
-enum : unsigned int { kStreamInit = 0u, kStreamSweep = 1u, kStreamResample = 2u, kStreamPoisson = 3u };
+enum : unsigned int {
+    kStreamInit = 0u,
+    kStreamSweep = 1u,
+    kStreamResample = 2u,
+    kStreamPoisson = 3u,
+    kStreamRefine = 4u
+};
 
 __device__ __forceinline__ void mulhilo(unsigned int a, unsigned int b, unsigned int &hi, unsigned int &lo)
 {
@@ -123,9 +145,9 @@ struct DevState {
     double S;                 // sum_k h_k w_k of the last resampling
     int kmin;                 // lowest occupied level of the last resampling
     int error;                // sticky pa_status bits (first error wins)
-    // Metropolis acceptance at the current beta: accept iff x <= tm1 (and nz != 0)
-    unsigned int tm1_4, tm1_8;
-    unsigned int nz_4, nz_8;
+    // Metropolis thresholds at the current beta, floor(e^{-4 beta} 2^32) and
+    // floor(e^{-8 beta} 2^32) in [0, 2^32]: a 32-bit uniform x is accepted iff x < T
+    unsigned long long T4, T8;
     // exact integer sums of the current population (filled by measurement)
     unsigned long long sum_absM;
     unsigned long long sum_M2;

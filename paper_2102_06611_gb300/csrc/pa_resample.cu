@@ -99,10 +99,8 @@ __device__ __forceinline__ void set_thresholds(DevState *st, double beta)
 {
     const unsigned long long t4 = metropolis_threshold(__dmul_rn(4.0, beta));
     const unsigned long long t8 = metropolis_threshold(__dmul_rn(8.0, beta));
-    st->tm1_4 = t4 ? (unsigned int)(t4 - 1ull) : 0u;
-    st->nz_4 = t4 ? 1u : 0u;
-    st->tm1_8 = t8 ? (unsigned int)(t8 - 1ull) : 0u;
-    st->nz_8 = t8 ? 1u : 0u;
+    st->T4 = t4;
+    st->T8 = t8;
 }
 
 // ------------------------------------------------------------------------------ setup

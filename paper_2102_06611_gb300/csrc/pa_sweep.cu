@@ -11,11 +11,18 @@
 //
 // Metropolis rule (Sec. IV, acceptance min[1, exp(-beta dE)], dE = 4a - 8 for a aligned
 // neighbours): a <= 2 flips; a = 3 flips iff x < floor(e^{-4 beta} 2^32); a = 4 flips iff
-// x < floor(e^{-8 beta} 2^32), with x a 32-bit Philox word.  Random word for the colour-q
-// site with index j (column 2j + ((r + q) & 1)) of row r in sweep t of step i, slot s:
-// lane (j & 3) of Philox(key = seed, ctr = (16 r + j / 4, s, SWEEP << 28 | (2t + q), i)).
+// x < floor(e^{-8 beta} 2^32), with x a uniform 32-bit integer per site drawn from Philox
+// (key = seed): its top 8 bits come from bit planes shared by the 32 sites of a word, its low
+// 24 bits from a per-site draw made only when the top bits tie with the threshold (see
+// half_sweep for the counters).
 #include "pa_common.cuh"
 #include "pa_kernels.h"
+
+// Minimum resident blocks of 256 threads per SM the sweep kernel is compiled for (caps its
+// registers at 65536 / (256 * n)).
+#ifndef PA_SWEEP_MIN_BLOCKS
+#define PA_SWEEP_MIN_BLOCKS 2
+#endif
 
 namespace pa {
 
@@ -43,17 +50,41 @@ __device__ __forceinline__ W rot_down(W x)
 __device__ __forceinline__ int popc(unsigned int x) { return __popc(x); }
 __device__ __forceinline__ int popc(unsigned long long x) { return __popcll(x); }
 
-// Philox4x32-10 with the first round's uniform half precomputed: u0 = hi(M1 c2) ^ c1 ^ k0,
-// u1 = lo(M1 c2), u2 = c3 ^ k1; only c0 varies between calls.
-__device__ __forceinline__ uint4 philox_c0(unsigned int c0, unsigned int u0, unsigned int u1,
-                                           unsigned int u2, const unsigned int *rk0,
+// Philox4x32-10 for calls that differ only in c0.  After round 1 the words 0 and 1 are
+// u0 = hi(M1 c2) ^ c1 ^ k0 and u1 = lo(M1 c2), the same for every call, so round 2's
+// product M0 * u0 = (v_hi, v_lo) is shared too; u2 = c3 ^ k1, u1k = u1 ^ k0'.
+struct PhiloxC0 {
+    unsigned int u0, u1, u2;
+    unsigned int v_hi, v_lo;
+    unsigned int u1k;  // u1 ^ (round-2 key word 0)
+};
+
+__device__ __forceinline__ PhiloxC0 philox_c0_setup(unsigned int c1, unsigned int c2, unsigned int c3,
+                                                    const unsigned int *rk0, const unsigned int *rk1)
+{
+    PhiloxC0 p;
+    unsigned int h1, l1;
+    mulhilo(kPhiloxM1, c2, h1, l1);
+    p.u0 = h1 ^ c1 ^ rk0[0];
+    p.u1 = l1;
+    p.u2 = c3 ^ rk1[0];
+    mulhilo(kPhiloxM0, p.u0, p.v_hi, p.v_lo);
+    p.u1k = p.u1 ^ rk0[1];
+    return p;
+}
+
+__device__ __forceinline__ uint4 philox_c0(unsigned int c0, const PhiloxC0 &p, const unsigned int *rk0,
                                            const unsigned int *rk1)
 {
     unsigned int hi0, lo0;
     mulhilo(kPhiloxM0, c0, hi0, lo0);
-    uint4 c = make_uint4(u0, u1, hi0 ^ u2, lo0);
+    // round 1: (u0, u1, hi0 ^ c3 ^ k1, lo0); round 2 with the shared M0 * u0
+    const unsigned int z2 = hi0 ^ p.u2, z3 = lo0;
+    unsigned int h1, l1;
+    mulhilo(kPhiloxM1, z2, h1, l1);
+    uint4 c = make_uint4(h1 ^ p.u1k, l1, p.v_hi ^ z3 ^ rk1[1], p.v_lo);
 #pragma unroll
-    for (int i = 1; i < 10; ++i) {
+    for (int i = 2; i < 10; ++i) {
         unsigned int h0, l0, h1, l1;
         mulhilo(kPhiloxM0, c.x, h0, l0);
         mulhilo(kPhiloxM1, c.z, h1, l1);
@@ -153,19 +184,55 @@ __device__ __forceinline__ void init_rows(unsigned int slot, int r0, unsigned in
     }
 }
 
+// Per-launch constants of the acceptance test.  T = floor(e^{-4 beta} 2^32) (class a = 3)
+// or floor(e^{-8 beta} 2^32) (class a = 4), T in [0, 2^32]: m[k] = all ones iff bit 31 - k of
+// T is set (top 8 bits as bit-plane masks), low = T mod 2^24, alw = all ones iff T = 2^32.
+template <typename W>
+struct Accept {
+    W m4[8], m8[8];
+    W alw4, alw8;
+    unsigned int low4, low8;
+};
+
+template <typename W>
+__device__ __forceinline__ Accept<W> make_accept(unsigned long long T4, unsigned long long T8)
+{
+    Accept<W> c;
+    const bool all4 = T4 >= (1ull << 32), all8 = T8 >= (1ull << 32);
+    const unsigned int t4 = all4 ? 0u : (unsigned int)T4, t8 = all8 ? 0u : (unsigned int)T8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        c.m4[k] = ((t4 >> (31 - k)) & 1u) ? ~W(0) : W(0);
+        c.m8[k] = ((t8 >> (31 - k)) & 1u) ? ~W(0) : W(0);
+    }
+    c.alw4 = all4 ? ~W(0) : W(0);
+    c.alw8 = all8 ? ~W(0) : W(0);
+    c.low4 = t4 & 0xFFFFFFu;
+    c.low8 = t8 & 0xFFFFFFu;
+    return c;
+}
+
 // One colour (compile-time Q) of one sweep over the rows a lane holds.
+//
+// Acceptance x < T is decided bit-serially over the 32 sites of a word at once: the top 8
+// bits of every site's uniform x are 8 bit planes (bit j of plane k is bit 31 - k of site j's
+// x), compared most significant first against the class threshold's bits; a site stays
+// undecided only while its bits equal the threshold's, which after 8 planes happens with
+// probability 2^-8, and only then is its low 24-bit part drawn.  Plane k of row r is word
+// k mod 4 of Philox(ctr = (2 (nh r + h) + k / 4, slot, SWEEP << 28 | tag, i)) for the 32-site
+// chunk h of the half-row (nh = chunks per half-row); the low part of site j is the low 24
+// bits of word 0 of Philox(ctr = (64 r + j, slot, REFINE << 28 | tag, i)), tag = 2t + Q.
 template <int L, int Q>
 __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L>::W *B, int r0,
                                            int lane, unsigned int slot, unsigned int tag,
                                            unsigned int step, const unsigned int *rk0,
-                                           const unsigned int *rk1, unsigned int tm1_4,
-                                           unsigned int tm1_8, typename Geo<L>::W nz4,
-                                           typename Geo<L>::W nz8)
+                                           const unsigned int *rk1, unsigned int k0, unsigned int k1,
+                                           const Accept<typename Geo<L>::W> &ac)
 {
     using Gm = Geo<L>;
     using W = typename Gm::W;
     constexpr int RPL = Gm::RPL, G = Gm::G, H = Gm::H;
-    constexpr int NGRP = (H + 3) / 4;
+    constexpr int NH = Gm::WIDE ? 2 : 1;  // 32-site chunks per half-row
     W *T = (Q == 0) ? A : B;          // words updated by this colour
     const W *O = (Q == 0) ? B : A;    // the other half of each row (read only here)
 
@@ -175,13 +242,10 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
     const W from_up = __shfl_sync(0xffffffffu, O[RPL - 1], gbase | ((q - 1) & (G - 1)));
     const W from_down = __shfl_sync(0xffffffffu, O[0], gbase | ((q + 1) & (G - 1)));
 
-    // first Philox round: the c2 = tag product and the slot / step words are uniform here
-    unsigned int h1, l1;
-    mulhilo(kPhiloxM1, tag, h1, l1);
-    const unsigned int u0 = h1 ^ slot ^ rk0[0];
-    const unsigned int u1 = l1;
-    const unsigned int u2 = step ^ rk1[0];
+    // the plane stream's calls differ only in c0 (rounds 1 and 2 partly shared)
+    const PhiloxC0 pc = philox_c0_setup(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
 
+    W lt[RPL], eq[RPL], a4[RPL], g3[RPL];
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
         const int r = r0 + i;
@@ -193,28 +257,74 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
         const bool even_half = ((r + Q) & 1) == 0;
         const W h_b = even_half ? rot_up<W, H>(O[i]) : rot_down<W, H>(O[i]);
         const W x1 = ~(s ^ up), x2 = ~(s ^ dn), x3 = ~(s ^ h_a), x4 = ~(s ^ h_b);
-        const W all4 = x1 & x2 & x3 & x4;
-        const W ge3 = (x1 & x2 & (x3 | x4)) | (x3 & x4 & (x1 | x2));
+        const W all4 = x1 & x2 & x3 & x4 & half_mask<W, H>();
+        const W ge3 = ((x1 & x2 & (x3 | x4)) | (x3 & x4 & (x1 | x2))) & half_mask<W, H>();
         const W eq3 = ge3 & ~all4;
-        W acc3 = 0, acc4 = 0;
+
+        // bit planes of the top 8 bits of every site's uniform
+        W plane[8];
+        if constexpr (NH == 1) {
+            const uint4 p0 = philox_c0((unsigned int)(2 * r), pc, rk0, rk1);
+            const uint4 p1 = philox_c0((unsigned int)(2 * r + 1), pc, rk0, rk1);
+            plane[0] = p0.x; plane[1] = p0.y; plane[2] = p0.z; plane[3] = p0.w;
+            plane[4] = p1.x; plane[5] = p1.y; plane[6] = p1.z; plane[7] = p1.w;
+        } else {
+            const uint4 a0 = philox_c0((unsigned int)(4 * r), pc, rk0, rk1);
+            const uint4 a1 = philox_c0((unsigned int)(4 * r + 1), pc, rk0, rk1);
+            const uint4 b0 = philox_c0((unsigned int)(4 * r + 2), pc, rk0, rk1);
+            const uint4 b1 = philox_c0((unsigned int)(4 * r + 3), pc, rk0, rk1);
+            const unsigned int lo[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const unsigned int hi[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int g = 0; g < NGRP; ++g) {
-            const uint4 x = philox_c0((unsigned int)(16 * r + g), u0, u1, u2, rk0, rk1);
-            const unsigned int xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int j = 4 * g + k;
-                if (j < H) {
-                    acc3 |= (W)(xs[k] <= tm1_4) << j;
-                    acc4 |= (W)(xs[k] <= tm1_8) << j;
-                }
-            }
+            for (int k = 0; k < 8; ++k) plane[k] = (W)lo[k] | ((W)hi[k] << 32);
         }
-        acc3 &= nz4;
-        acc4 &= nz8;
-        const W flip = (~ge3 | (eq3 & acc3) | (all4 & acc4)) & half_mask<W, H>();
-        T[i] = s ^ flip;
+        W l = (eq3 & ac.alw4) | (all4 & ac.alw8);   // decided: x < T
+        W e = (eq3 & ~ac.alw4) | (all4 & ~ac.alw8); // undecided: top bits equal so far
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const W tm = (eq3 & ac.m4[k]) | (all4 & ac.m8[k]);  // threshold bit of each site
+            l |= e & ~plane[k] & tm;
+            e &= ~(plane[k] ^ tm);
+        }
+        lt[i] = l;
+        eq[i] = e;
+        a4[i] = all4;
+        g3[i] = ge3;
     }
+
+    // rare: the low 24 bits decide the sites whose top 8 bits equal the threshold's; one
+    // loop over all rows of the lane keeps the warp's divergent iterations few
+    W pending = 0;
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) pending |= eq[i];
+    while (pending) {
+        int isel = 0;
+        W w = 0, a4s = 0;
+#pragma unroll
+        for (int i = RPL - 1; i >= 0; --i)
+            if (eq[i]) {
+                isel = i;
+                w = eq[i];
+                a4s = a4[i];
+            }
+        const int j = Gm::WIDE ? __ffsll((long long)w) - 1 : __ffs((int)w) - 1;
+        const uint4 xr = philox(make_uint4((unsigned int)(64 * (r0 + isel) + j), slot, (kStreamRefine << 28) | tag,
+                                           step), k0, k1);
+        const unsigned int thr = ((a4s >> j) & W(1)) ? ac.low8 : ac.low4;
+        const W bit = W(1) << j;
+        const W acc = ((xr.x & 0xFFFFFFu) < thr) ? bit : W(0);
+        pending = 0;
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+            if (i == isel) {
+                eq[i] &= ~bit;
+                lt[i] |= acc;
+            }
+            pending |= eq[i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) T[i] ^= (~g3[i] | lt[i]) & half_mask<W, H>();
 }
 
 // Energy level n_anti / 2 and number of up spins of the rows a lane holds (summed over the
@@ -248,7 +358,7 @@ __device__ __forceinline__ void measure_rows(const typename Geo<L>::W *A, const 
 
 // Fused kernel: (INIT) generate or (!INIT) load each replica, theta sweeps, measure.
 template <int L, bool INIT>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
+__global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_sweep(SweepArgs a)
 {
     using Gm = Geo<L>;
     using W = typename Gm::W;
@@ -272,9 +382,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
         rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
         rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
     }
-    const unsigned int tm1_4 = a.st->tm1_4, tm1_8 = a.st->tm1_8;
-    const W nz4 = a.st->nz_4 ? ~W(0) : W(0);
-    const W nz8 = a.st->nz_8 ? ~W(0) : W(0);
+    const Accept<W> ac = make_accept<W>(a.st->T4, a.st->T8);
 
     unsigned long long s_abs = 0, s_m2 = 0;
     W *spins = reinterpret_cast<W *>(a.spins);
@@ -295,11 +403,9 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
         }
 #pragma unroll 1
         for (int t = 0; t < a.theta; ++t) {
-            const unsigned int tag0 = (kStreamSweep << 28) | (unsigned int)(2 * (a.t0 + t));
-            half_sweep<L, 0>(A, B, r0, lane, (unsigned int)j, tag0, a.step, rk0, rk1, tm1_4,
-                             tm1_8, nz4, nz8);
-            half_sweep<L, 1>(A, B, r0, lane, (unsigned int)j, tag0 | 1u, a.step, rk0, rk1, tm1_4,
-                             tm1_8, nz4, nz8);
+            const unsigned int tag0 = (unsigned int)(2 * (a.t0 + t));
+            half_sweep<L, 0>(A, B, r0, lane, (unsigned int)j, tag0, a.step, rk0, rk1, a.k0, a.k1, ac);
+            half_sweep<L, 1>(A, B, r0, lane, (unsigned int)j, tag0 | 1u, a.step, rk0, rk1, a.k0, a.k1, ac);
         }
         int anti, ups;
         measure_rows<L>(A, B, r0, lane, anti, ups);

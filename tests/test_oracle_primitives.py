@@ -151,6 +151,34 @@ def test_init_is_uniform():
 
 
 # ---------------------------------------------------------------------------- sweep
+@pytest.mark.parametrize("L,r,p", [(8, 3, 2), (64, 63, 31), (128, 5, 40), (128, 127, 63)])
+def test_sweep_uniform_follows_its_definition(L, r, p):
+    """Top 8 bits from bit p mod 32 of eight Philox words (bit planes), low 24 bits from a
+    separate refinement draw, as documented in the oracle."""
+    seed, step, slot, tag = 0x1234_5678_9ABC, 17, 4242, 7
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    nh = (L + 63) // 64
+    h, b = p // 32, p % 32
+    planes = np.concatenate([oracle.philox4x32_10([2 * (nh * r + h) + c, slot, (1 << 28) | tag, step], key)
+                             for c in (0, 1)])
+    top = 0
+    for k in range(8):
+        top |= ((int(planes[k]) >> b) & 1) << (31 - k)
+    low = int(oracle.philox4x32_10([64 * r + p, slot, (4 << 28) | tag, step], key)[0]) & 0xFFFFFF
+    assert oracle.sweep_uniform(L, seed, step, slot, tag, r, p) == top | low
+
+
+def test_sweep_uniform_is_uniform():
+    xs = np.array([oracle.sweep_uniform(64, 3, 1, j, t, r, p) for j in range(4) for t in range(2)
+                   for r in range(64) for p in range(32)], dtype=np.uint64)
+    n = len(xs)
+    assert abs(xs.astype(float).mean() / 2 ** 32 - 0.5) < 5 * math.sqrt(1 / 12 / n)
+    for shift, bins in ((24, 256), (0, 256)):
+        counts = np.bincount(((xs >> shift) & 255).astype(np.int64), minlength=bins)
+        chi2 = np.sum((counts - n / bins) ** 2 / (n / bins))
+        assert chi2 < bins - 1 + 6 * math.sqrt(2 * (bins - 1))
+
+
 @pytest.mark.parametrize("L", [4, 8, 12])
 def test_sweep_beta_zero_inverts_every_spin(L):
     """At beta = 0 every proposal is accepted, so one checkerboard sweep maps s -> -s
