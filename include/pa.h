@@ -112,6 +112,23 @@ typedef struct {
     int status;            /* sticky device error word (pa_status) */
 } pa_obs;
 
+/* One temperature step of the schedule a context actually ran (see pa_schedule_log). */
+typedef struct {
+    long long step;        /* temperature index i */
+    double beta;           /* beta_i */
+    double dbeta;          /* beta_i - beta_{i-1} */
+    double alpha;          /* histogram overlap of the proposal that produced beta_i (NaN if none) */
+    int theta;             /* sweeps run at beta_i */
+    int source;            /* PA_SCHED_* */
+} pa_sched_entry;
+
+enum {
+    PA_SCHED_CALLER = 0,   /* beta_i passed by the caller */
+    PA_SCHED_BISECT = 1,   /* from pa_propose_schedule (overlap bisection) */
+    PA_SCHED_LEARNED = 2,  /* learned proposal accepted (overlap at or above the floor) */
+    PA_SCHED_FALLBACK = 3  /* learned proposal rejected, bisection used instead */
+};
+
 /* Buffer sizes for cfg.  Returns PA_ERR_INVALID_ARG for an unsupported configuration. */
 pa_status pa_query_sizes(const pa_config *cfg, pa_sizes *out);
 
@@ -142,6 +159,24 @@ pa_status pa_record(pa_ctx *ctx, void *device_dst);
 /* Step 4: form the record and copy it to host memory.  Synchronises the stream and
    returns the sticky device error, if any. */
 pa_status pa_observables(pa_ctx *ctx, pa_obs *host_out);
+
+/* Adaptive temperature step (the paper's self-adaptive steps, Sec. II; overlap guideline
+   alpha > 0.7, Sec. X).  From the energy-level histogram h_k of the current population
+   (measured at the current beta; measured first if a resampling came since), the overlap
+   alpha(dbeta) = sum_k min(h_k / R, h_k w_k / S) of the energy distribution with its
+   reweighting to beta + dbeta (w_k, S as in pa_resample) is evaluated in binary64 in a
+   fixed order, and *beta_next receives beta + the largest dbeta in (0, hi],
+   hi = min(dbeta_max, beta_final - beta), with alpha >= alpha_target (hi itself if it
+   qualifies, else 48 bisection steps on [0, hi]; beta_final exactly when the whole
+   remaining range qualifies).  *alpha_out receives alpha at that step.  Does not resample:
+   pass *beta_next to pa_resample.  Synchronising.  0 < alpha_target <= 1, dbeta_max > 0,
+   beta_final >= beta. */
+pa_status pa_propose_schedule(pa_ctx *ctx, double alpha_target, double dbeta_max, double beta_final,
+                              double *beta_next, double *alpha_out);
+
+/* Copy up to max_entries records of the schedule run so far (one per pa_resample, in order)
+   to host_out; *n_out receives the number of records available. */
+pa_status pa_schedule_log(pa_ctx *ctx, pa_sched_entry *host_out, long long max_entries, long long *n_out);
 
 /* Synchronise the stream; returns the sticky device error, if any. */
 pa_status pa_sync(pa_ctx *ctx);

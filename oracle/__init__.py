@@ -110,6 +110,11 @@ def lib():
                 "orc_pa_spins": (None, [vp, ctypes.c_int64, ctypes.c_int64, i8p]),
                 "orc_pa_set": (ctypes.c_int, [vp, ctypes.c_int64, i8p, i32p, ctypes.c_uint32,
                                               ctypes.c_double, ctypes.c_double]),
+                "orc_overlap": (ctypes.c_double, [ctypes.c_int, i64p, ctypes.c_double]),
+                "orc_bisect_next_beta": (ctypes.c_double, [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double,
+                                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]),
+                "orc_pa_propose_bisect": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                            ctypes.c_int, dp]),
                 "orc_bruteforce": (ctypes.c_int, [ctypes.c_int, i64p, i64p, i64p]),
                 "orc_transfer_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
                 "orc_kaufman_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
@@ -204,6 +209,24 @@ def resample_levels(L, R_target, levels, beta_prev, beta_new, step, seed, kind, 
                                    float(beta_prev), float(beta_new), step, seed, kind,
                                    capacity, _ptr(counts, ctypes.c_int32), ctypes.byref(info))
     return st, counts, info.lnQ, info.S, info.kmin, info.R_new
+
+
+# ----------------------------------------------------------------------------- schedule
+BISECT_ITERS = 48
+
+
+def overlap(N: int, hist, dbeta: float) -> float:
+    """Energy-histogram overlap alpha(dbeta) of a level histogram with its reweighting."""
+    h = np.ascontiguousarray(hist, dtype=np.int64)
+    return float(lib().orc_overlap(N, _ptr(h, ctypes.c_int64), float(dbeta)))
+
+
+def bisect_next_beta(N, hist, beta, beta_final, dbeta_max, alpha_target, iters=BISECT_ITERS):
+    h = np.ascontiguousarray(hist, dtype=np.int64)
+    a = ctypes.c_double()
+    b = lib().orc_bisect_next_beta(N, _ptr(h, ctypes.c_int64), float(beta), float(beta_final),
+                                   float(dbeta_max), float(alpha_target), int(iters), ctypes.byref(a))
+    return float(b), float(a.value)
 
 
 # ----------------------------------------------------------------------------- exact
@@ -308,6 +331,14 @@ class PA:
         out = np.zeros(count * self.N, np.int8)
         lib().orc_pa_spins(self._h, first, count, _ptr(out, ctypes.c_int8))
         return out.reshape(count, self.L, self.L)
+
+    def propose_bisect(self, beta_final: float, dbeta_max: float, alpha_target: float,
+                       iters: int = BISECT_ITERS):
+        """Next beta of the adaptive schedule from the current population's histogram."""
+        a = ctypes.c_double()
+        b = lib().orc_pa_propose_bisect(self._h, float(beta_final), float(dbeta_max), float(alpha_target),
+                                        int(iters), ctypes.byref(a))
+        return float(b), float(a.value)
 
     def set_population(self, spins: np.ndarray, fam: np.ndarray, step: int, beta: float,
                        sum_lnQ: float = 0.0):

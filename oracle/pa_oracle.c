@@ -559,6 +559,92 @@ void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
     }
 }
 
+/* ------------------------------------------------------------------------------------
+ * Adaptive temperature step (the paper names it, Sec. II and Sec. IX, and recommends a
+ * step that keeps the energy-histogram overlap above about 0.7, Sec. X; the procedure itself
+ * is not printed).  Reading: the overlap of the energy distribution at beta, estimated by
+ * the population histogram p_k = h_k / R, with the one reweighted to beta + dbeta,
+ * q_k = h_k w_k / S (w_k and S as in the resampling step), is
+ *     alpha(dbeta) = sum over occupied k, ascending, of min(p_k, q_k);
+ * the next step is the largest dbeta in (0, hi], hi = min(dbeta_max, beta_final - beta),
+ * with alpha(dbeta) >= alpha_target, found by `iters` bisection steps on [0, hi] after
+ * trying hi itself.
+ * ---------------------------------------------------------------------------------- */
+double orc_overlap(int N, const int64_t *h, double dbeta)
+{
+    int kmin = 0;
+    while (kmin <= N && h[kmin] == 0) ++kmin;
+    if (kmin > N) return 0.0;
+    int Eref = 4 * kmin - 2 * N;
+    int64_t R = 0;
+    for (int k = 0; k <= N; ++k) R += h[k];
+    double S = 0.0;
+    for (int k = 0; k <= N; ++k) {
+        if (h[k] == 0) continue;
+        double w = orc_exp(-(dbeta * (double)(4 * k - 2 * N - Eref)));
+        S = S + (double)h[k] * w;
+    }
+    double alpha = 0.0;
+    for (int k = 0; k <= N; ++k) {
+        if (h[k] == 0) continue;
+        double w = orc_exp(-(dbeta * (double)(4 * k - 2 * N - Eref)));
+        double pk = (double)h[k] / (double)R;
+        double qk = ((double)h[k] * w) / S;
+        alpha = alpha + (pk < qk ? pk : qk);
+    }
+    return alpha;
+}
+
+double orc_bisect_next_beta(int N, const int64_t *h, double beta, double beta_final, double dbeta_max,
+                            double alpha_target, int iters, double *alpha_out)
+{
+    double hi = beta_final - beta;
+    if (dbeta_max < hi) hi = dbeta_max;
+    if (!(hi > 0.0)) {
+        if (alpha_out) *alpha_out = 1.0;
+        return beta_final;
+    }
+    const double hi0 = hi;
+    double dbeta, alpha;
+    double a_hi = orc_overlap(N, h, hi);
+    if (a_hi >= alpha_target) {
+        dbeta = hi;
+        alpha = a_hi;
+    } else {
+        double lo = 0.0, a_lo = 1.0;
+        for (int it = 0; it < iters; ++it) {
+            double mid = 0.5 * (lo + hi);
+            double a_mid = orc_overlap(N, h, mid);
+            if (a_mid >= alpha_target) {
+                lo = mid;
+                a_lo = a_mid;
+            } else {
+                hi = mid;
+            }
+        }
+        if (lo > 0.0) {
+            dbeta = lo;
+            alpha = a_lo;
+        } else { /* no tried step reaches the target: take the smallest one tried */
+            dbeta = hi;
+            alpha = orc_overlap(N, h, hi);
+        }
+    }
+    if (alpha_out) *alpha_out = alpha;
+    if (dbeta == hi0 && hi0 == beta_final - beta) return beta_final;
+    return beta + dbeta;
+}
+
+double orc_pa_propose_bisect(const orc_pa *p, double beta_final, double dbeta_max, double alpha_target,
+                             int iters, double *alpha_out)
+{
+    int64_t *h = (int64_t *)calloc((size_t)p->N + 1, sizeof(int64_t));
+    for (int64_t j = 0; j < p->R; ++j) h[(p->E[j] + 2 * p->N) / 4] += 1;
+    double b = orc_bisect_next_beta(p->N, h, p->beta, beta_final, dbeta_max, alpha_target, iters, alpha_out);
+    free(h);
+    return b;
+}
+
 /* Accessors used by the tests. */
 int64_t orc_pa_R(const orc_pa *p) { return p->R; }
 int64_t orc_pa_R_prev(const orc_pa *p) { return p->R_prev; }

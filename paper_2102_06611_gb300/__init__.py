@@ -94,6 +94,20 @@ class PopulationAnnealing:
         _check(self.lib, self.ctx, self.lib.pa_observables(self.ctx, ctypes.byref(o)))
         return o.as_dict()
 
+    def propose_schedule(self, alpha_target: float = 0.8, dbeta_max: float = 0.1, beta_final: float = 1.0):
+        """Adaptive step: (beta_next, alpha) from overlap bisection on the current histogram."""
+        b, a = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib, self.ctx, self.lib.pa_propose_schedule(self.ctx, float(alpha_target), float(dbeta_max),
+                                                                float(beta_final), ctypes.byref(b), ctypes.byref(a)))
+        return b.value, a.value
+
+    def schedule_log(self) -> list[dict]:
+        n = ctypes.c_longlong()
+        _check(self.lib, self.ctx, self.lib.pa_schedule_log(self.ctx, None, 0, ctypes.byref(n)))
+        buf = (_lib.pa_sched_entry * max(1, n.value))()
+        _check(self.lib, self.ctx, self.lib.pa_schedule_log(self.ctx, buf, n.value, ctypes.byref(n)))
+        return [{f: getattr(buf[i], f) for f, _ in _lib.pa_sched_entry._fields_} for i in range(n.value)]
+
     def sync(self) -> None:
         _check(self.lib, self.ctx, self.lib.pa_sync(self.ctx))
 

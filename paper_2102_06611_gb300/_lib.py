@@ -54,6 +54,13 @@ class pa_obs(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class pa_sched_entry(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("beta", ctypes.c_double), ("dbeta", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("theta", ctypes.c_int), ("source", ctypes.c_int)]
+
+
+PA_SCHED_CALLER, PA_SCHED_BISECT, PA_SCHED_LEARNED, PA_SCHED_FALLBACK = 0, 1, 2, 3
+
 # name -> (restype, argtypes): every entry point declared in include/pa.h
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
@@ -64,6 +71,9 @@ SIGNATURES = {
     "pa_anneal_step": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pa_record": (ctypes.c_int, [_vp, _vp]),
     "pa_observables": (ctypes.c_int, [_vp, _P(pa_obs)]),
+    "pa_propose_schedule": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           _P(ctypes.c_double), _P(ctypes.c_double)]),
+    "pa_schedule_log": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, _P(ctypes.c_longlong)]),
     "pa_sync": (ctypes.c_int, [_vp]),
     "pa_population": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
     "pa_histogram": (ctypes.c_int, [_vp, _vp]),

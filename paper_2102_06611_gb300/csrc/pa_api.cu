@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "pa_common.cuh"
 #include "pa_kernels.h"
@@ -25,6 +26,11 @@ struct pa_ctx {
     double beta, dbeta;
     int theta_last;
     int sweeps_in_step;    // sweeps already done at this temperature
+    bool measured;         // histogram and per-replica levels describe the current population
+    std::vector<pa_sched_entry> log;  // one record per pa_resample
+    bool prop_valid;       // the last schedule proposal, matched against the next pa_resample
+    double prop_beta, prop_alpha;
+    int prop_source;
     int failed;            // sticky host-side status
     char err[256];
 };
@@ -160,6 +166,8 @@ pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_
     c->dbeta = 0.0;
     c->theta_last = 0;
     c->sweeps_in_step = 0;
+    c->measured = true;
+    c->prop_valid = false;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {
@@ -232,18 +240,26 @@ pa_status pa_resample(pa_ctx *c, double beta_new)
     c->cur = nxt;
     c->step += 1;
     c->dbeta = beta_new - c->beta;
+    pa_sched_entry rec{};
+    rec.step = c->step;
+    rec.beta = beta_new;
+    rec.dbeta = c->dbeta;
+    rec.theta = 0;
+    const bool proposed = c->prop_valid && beta_new == c->prop_beta;
+    rec.source = proposed ? c->prop_source : PA_SCHED_CALLER;
+    rec.alpha = proposed ? c->prop_alpha : std::nan("");
+    c->log.push_back(rec);
+    c->prop_valid = false;
     c->beta = beta_new;
     c->sweeps_in_step = 0;
+    c->measured = false;
     return PA_OK;
 }
 
-pa_status pa_anneal_step(pa_ctx *c, int theta)
+// theta sweeps at the current beta (theta = 0: measurement only), then energies, magnetisations
+// and the level histogram of the current population.
+static pa_status sweep_and_measure(pa_ctx *c, int theta)
 {
-    pa_status s = check_live(c);
-    if (s != PA_OK) return s;
-    if (theta < 0 || (long long)c->sweeps_in_step + theta > (1 << 27))
-        return fail(c, PA_ERR_INVALID_ARG, "theta %d out of range", theta);
-    DeviceGuard g(c->device);
     cudaError_t e = pa::launch_zero_measure(c->st, at<int>(c, c->ws.hist), c->N, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "zero measurement");
     pa::SweepArgs a{};
@@ -262,8 +278,70 @@ pa_status pa_anneal_step(pa_ctx *c, int theta)
     a.theta = theta;
     e = pa::launch_sweep(c->cfg.L, false, a, c->num_sms, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
+    c->measured = true;
+    return PA_OK;
+}
+
+pa_status pa_anneal_step(pa_ctx *c, int theta)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (theta < 0 || (long long)c->sweeps_in_step + theta > (1 << 27))
+        return fail(c, PA_ERR_INVALID_ARG, "theta %d out of range", theta);
+    DeviceGuard g(c->device);
+    if ((s = sweep_and_measure(c, theta)) != PA_OK) return s;
     c->sweeps_in_step += theta;
     c->theta_last = theta;
+    if (!c->log.empty() && c->log.back().step == c->step) c->log.back().theta += theta;
+    return PA_OK;
+}
+
+pa_status pa_propose_schedule(pa_ctx *c, double alpha_target, double dbeta_max, double beta_final,
+                              double *beta_next, double *alpha_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!beta_next || !alpha_out || !(alpha_target > 0.0 && alpha_target <= 1.0) || !(dbeta_max > 0.0) ||
+        !std::isfinite(dbeta_max) || !std::isfinite(beta_final))
+        return fail(c, PA_ERR_INVALID_ARG, "bad schedule parameters");
+    if (beta_final < c->beta)
+        return fail(c, PA_ERR_STATE, "beta_final %.17g below current beta %.17g", beta_final, c->beta);
+    DeviceGuard g(c->device);
+    if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
+    pa::BisectArgs a{};
+    a.L = c->cfg.L;
+    a.st = c->st;
+    a.hist = at<int>(c, c->ws.hist);
+    a.occ_k = at<int>(c, c->ws.occ_k);
+    a.occ_h = at<int>(c, c->ws.occ_h);
+    a.occ_w = at<double>(c, c->ws.occ_w);
+    a.occ_t = at<double>(c, c->ws.occ_t);
+    a.beta = c->beta;
+    a.beta_final = beta_final;
+    a.dbeta_max = dbeta_max;
+    a.alpha_target = alpha_target;
+    a.iters = pa::kBisectIters;
+    cudaError_t e = pa::launch_bisect(a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "bisection launch");
+    if ((s = sync_and_check(c)) != PA_OK) return s;
+    double out[2];
+    e = cudaMemcpy(out, &c->st->beta_next, sizeof(out), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "proposal copy");
+    *beta_next = out[0];
+    *alpha_out = out[1];
+    c->prop_valid = true;
+    c->prop_beta = out[0];
+    c->prop_alpha = out[1];
+    c->prop_source = PA_SCHED_BISECT;
+    return PA_OK;
+}
+
+pa_status pa_schedule_log(pa_ctx *c, pa_sched_entry *host_out, long long max_entries, long long *n_out)
+{
+    if (!c || !n_out || max_entries < 0 || (max_entries > 0 && !host_out)) return PA_ERR_INVALID_ARG;
+    const long long n = (long long)c->log.size();
+    *n_out = n;
+    for (long long i = 0; i < n && i < max_entries; ++i) host_out[i] = c->log[(size_t)i];
     return PA_OK;
 }
 
@@ -274,6 +352,7 @@ pa_status pa_record(pa_ctx *c, void *device_dst)
     if (!device_dst || (reinterpret_cast<uintptr_t>(device_dst) & 7u))
         return fail(c, PA_ERR_INVALID_ARG, "record destination must be an 8-byte aligned device pointer");
     DeviceGuard g(c->device);
+    if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
     pa::ObsArgs a{};
     a.L = c->cfg.L;
     a.step = c->step;

@@ -153,6 +153,9 @@ struct DevState {
     unsigned long long sum_M2;
     long long fam_count;
     long long fam_size2;
+    // result of the last schedule proposal
+    double beta_next;
+    double alpha_next;
     int theta;
     int pad;
 };

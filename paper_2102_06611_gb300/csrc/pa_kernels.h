@@ -23,6 +23,10 @@ struct Workspace {
     size_t obs;         // pa_obs          record slot used by pa_observables
     size_t hashes;      // uint64[capacity]
     size_t stage;       // uint32[kStageReplicas * L * ceil(L/32)] export staging
+    size_t occ_k;       // int32[N + 1]   occupied levels, ascending (schedule proposals)
+    size_t occ_h;       // int32[N + 1]   their counts
+    size_t occ_w;       // double[N + 1]  reweighting factors at a trial step
+    size_t occ_t;       // double[N + 1]  overlap terms at a trial step
     size_t total;
     long long nblk;     // blocks of the copy-count / copy kernels
 };
@@ -94,6 +98,21 @@ struct ObsArgs {
 };
 
 cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s);
+
+// Adaptive temperature step: bisection on dbeta for the histogram overlap (see k_bisect).
+struct BisectArgs {
+    int L;
+    DevState *st;
+    const int *hist;
+    int *occ_k, *occ_h;
+    double *occ_w, *occ_t;
+    double beta, beta_final, dbeta_max, alpha_target;
+    int iters;
+};
+
+constexpr int kBisectIters = 48;
+
+cudaError_t launch_bisect(const BisectArgs &a, cudaStream_t s);
 
 cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
                           unsigned long long *out, cudaStream_t s);

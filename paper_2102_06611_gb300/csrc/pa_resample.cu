@@ -44,6 +44,10 @@ Workspace plan_workspace(int L, long long capacity)
     w.obs = off;      off = align256(off + sizeof(pa_obs));
     w.hashes = off;   off = align256(off + (size_t)capacity * 8);
     w.stage = off;    off = align256(off + (size_t)kStageReplicas * words * 4);
+    w.occ_k = off;    off = align256(off + nlev * 4);
+    w.occ_h = off;    off = align256(off + nlev * 4);
+    w.occ_w = off;    off = align256(off + nlev * 8);
+    w.occ_t = off;    off = align256(off + nlev * 8);
     w.total = off;
     w.nblk = nblk;
     return w;
@@ -492,6 +496,131 @@ cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_obs<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ schedule
+// Adaptive temperature step.  alpha(dbeta) = sum over occupied levels k, ascending, of
+// min(p_k, q_k) with p_k = h_k / R (current energy distribution) and q_k = h_k w_k / S (its
+// reweighting to beta + dbeta; w_k, S as in k_table).  The step is the largest dbeta in
+// (0, hi], hi = min(dbeta_max, beta_final - beta), with alpha >= alpha_target: hi itself if
+// it qualifies, else `iters` bisection steps on [0, hi].  One block: the exps and the
+// per-level terms are computed in parallel, the two sums by one thread in ascending order.
+constexpr int kBisectThreads = 1024;
+
+__global__ void __launch_bounds__(kBisectThreads) k_bisect(BisectArgs a)
+{
+    __shared__ int sh_nocc, sh_kmin;
+    __shared__ long long sh_R;
+    __shared__ double sh_S, sh_alpha;
+    const int N = a.L * a.L, nlev = N + 1, tid = threadIdx.x;
+    DevState *st = a.st;
+
+    // compact the occupied levels in ascending order
+    const int chunk = (nlev + kBisectThreads - 1) / kBisectThreads;
+    const int k_lo = min(tid * chunk, nlev), k_hi = min(k_lo + chunk, nlev);
+    int occ = 0;
+    long long rsum = 0;
+    for (int k = k_lo; k < k_hi; ++k) {
+        occ += a.hist[k] > 0;
+        rsum += a.hist[k];
+    }
+    int nocc;
+    int pos = block_exclusive_scan<int, kBisectThreads>(occ, &nocc);
+    const long long R = block_sum<long long, kBisectThreads>(rsum);
+    for (int k = k_lo; k < k_hi; ++k) {
+        const int h = a.hist[k];
+        if (h > 0) {
+            a.occ_k[pos] = k;
+            a.occ_h[pos] = h;
+            ++pos;
+        }
+    }
+    if (tid == 0) {
+        sh_nocc = nocc;
+        sh_R = R;
+    }
+    __syncthreads();
+    if (tid == 0) sh_kmin = nocc > 0 ? a.occ_k[0] : 0;
+    __syncthreads();
+    nocc = sh_nocc;
+    const double Rd = (double)sh_R;
+    const int Eref = 4 * sh_kmin - 2 * N;
+
+    auto overlap = [&](double dbeta) -> double {
+        for (int i = tid; i < nocc; i += kBisectThreads) {
+            const int Ek = 4 * a.occ_k[i] - 2 * N;
+            a.occ_w[i] = det_exp(-__dmul_rn(dbeta, (double)(Ek - Eref)));
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double S = 0.0;
+            for (int i = 0; i < nocc; ++i) S = __dadd_rn(S, __dmul_rn((double)a.occ_h[i], a.occ_w[i]));
+            sh_S = S;
+        }
+        __syncthreads();
+        const double S = sh_S;
+        for (int i = tid; i < nocc; i += kBisectThreads) {
+            const double hk = (double)a.occ_h[i];
+            const double pk = __ddiv_rn(hk, Rd);
+            const double qk = __ddiv_rn(__dmul_rn(hk, a.occ_w[i]), S);
+            a.occ_t[i] = pk < qk ? pk : qk;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double alpha = 0.0;
+            for (int i = 0; i < nocc; ++i) alpha = __dadd_rn(alpha, a.occ_t[i]);
+            sh_alpha = alpha;
+        }
+        __syncthreads();
+        return sh_alpha;
+    };
+
+    double hi = __dsub_rn(a.beta_final, a.beta);
+    if (a.dbeta_max < hi) hi = a.dbeta_max;
+    double beta_next, alpha;
+    if (!(hi > 0.0) || nocc == 0) {
+        beta_next = a.beta_final;
+        alpha = 1.0;
+    } else {
+        const double hi0 = hi;
+        double dbeta;
+        const double a_hi = overlap(hi);
+        if (a_hi >= a.alpha_target) {
+            dbeta = hi;
+            alpha = a_hi;
+        } else {
+            double lo = 0.0, a_lo = 1.0;
+            for (int it = 0; it < a.iters; ++it) {
+                const double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+                const double a_mid = overlap(mid);
+                if (a_mid >= a.alpha_target) {
+                    lo = mid;
+                    a_lo = a_mid;
+                } else {
+                    hi = mid;
+                }
+            }
+            if (lo > 0.0) {
+                dbeta = lo;
+                alpha = a_lo;
+            } else {  // no tried step reaches the target: take the smallest one tried
+                dbeta = hi;
+                alpha = overlap(hi);
+            }
+        }
+        beta_next = (dbeta == hi0 && hi0 == __dsub_rn(a.beta_final, a.beta)) ? a.beta_final
+                                                                            : __dadd_rn(a.beta, dbeta);
+    }
+    if (tid == 0) {
+        st->beta_next = beta_next;
+        st->alpha_next = alpha;
+    }
+}
+
+cudaError_t launch_bisect(const BisectArgs &a, cudaStream_t s)
+{
+    k_bisect<<<1, kBisectThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
