@@ -174,6 +174,66 @@ pa_status pa_observables(pa_ctx *ctx, pa_obs *host_out);
 pa_status pa_propose_schedule(pa_ctx *ctx, double alpha_target, double dbeta_max, double beta_final,
                               double *beta_next, double *alpha_out);
 
+/* ---- Learned schedule.  The paper has no learned schedule: it names self-adaptive steps
+   (Sec. II), advises alpha > 0.7 and an adaptive number of sweeps (Sec. X).  This is a design
+   extension that only proposes; the overlap check below keeps every accepted step above a
+   floor, and the schedule used is logged for exact replay.
+   Network: 12 inputs -> 64 -> 64 -> 64 (tanh) -> 2 outputs, 9282 parameters in the flat
+   order W1[64x12], b1[64], W2[64x64], b2[64], W3[64x64], b3[64], W4[2x64], b4[2] (row-major,
+   W[out][in]), stored as bfloat16 bit patterns (uint16) for evaluation, float32 accumulation.
+   Inputs (float32, from binary64 statistics of the current population): beta, ln L, ln R_i,
+   <E>/N, ln(Var(E)/N + 1e-12), skewness and excess kurtosis of E, previous dbeta * L,
+   previous theta / theta0, previous overlap, ln(rho_t) / ln(R_i) (Eq. rhot), fraction of
+   parents given no copy at the last resampling.  Outputs (standardised): ln(dbeta L) and
+   ln(theta). */
+typedef struct {
+    const unsigned short *params_bf16; /* device, 9282 bfloat16 patterns */
+    const float *norm;                 /* device, 28 floats: x_mean[12], x_std[12], y_mean[2], y_std[2] */
+} pa_learned_model;
+
+typedef struct {
+    double beta_next;   /* the step to pass to pa_resample */
+    double alpha;       /* overlap at beta_next */
+    double dbeta_prop;  /* the network's step before the check */
+    int theta_next;     /* sweeps to run at beta_next (theta_prop if kept, theta0 on fallback) */
+    int theta_prop;     /* the network's sweep count, clamped to [1, theta_max] */
+    int source;         /* PA_SCHED_LEARNED or PA_SCHED_FALLBACK */
+    int pad;
+} pa_proposal;
+
+/* Number of network parameters (9282). */
+size_t pa_mlp_param_count(void);
+
+/* Batched forward pass: y[batch x 2] from x[batch x 12]; act (optional, batch x 192 floats)
+   receives the three hidden activations for pa_mlp_backward.  Asynchronous on `stream`. */
+pa_status pa_mlp_forward(const unsigned short *params_bf16, const float *x, int batch, float *y, float *act,
+                         void *stream);
+
+/* Gradient of L = 1/(2 batch) sum (y - t)^2 with respect to the 9282 parameters (evaluated
+   at their bfloat16 values) into grad (float32); delta is scratch of batch x 194 floats.
+   Batch sums run in sample order (deterministic).  Asynchronous. */
+pa_status pa_mlp_backward(const unsigned short *params_bf16, const float *x, const float *t, int batch,
+                          const float *act, const float *y, float *delta, float *grad, void *stream);
+
+/* One Adam step (Kingma & Ba) on float32 master parameters (step counts from 1), then the
+   bfloat16 copy is refreshed by round-to-nearest-even.  Asynchronous. */
+pa_status pa_mlp_adam(float *master, float *m, float *v, const float *grad, int step, float lr, float beta1,
+                      float beta2, float eps, unsigned short *params_bf16, void *stream);
+
+/* bfloat16 copy of float32 master parameters (round to nearest even).  Asynchronous. */
+pa_status pa_mlp_round(const float *master, unsigned short *params_bf16, void *stream);
+
+/* The 12 network inputs of the current population (measured first if needed) into
+   host_out; previous-step inputs come from the context's schedule (theta0 scales theta).
+   Synchronising. */
+pa_status pa_features(pa_ctx *ctx, int theta0, float *host_out);
+
+/* Learned step: features -> network -> (dbeta_prop, theta_prop) on the device; the step is
+   kept if the overlap at min(dbeta_prop, hi) reaches alpha_floor, otherwise the bisection of
+   pa_propose_schedule with alpha_target decides and theta0 sweeps are used.  Synchronising. */
+pa_status pa_propose_learned(pa_ctx *ctx, const pa_learned_model *model, double alpha_floor, double alpha_target,
+                             double dbeta_max, double beta_final, int theta0, int theta_max, pa_proposal *out);
+
 /* Copy up to max_entries records of the schedule run so far (one per pa_resample, in order)
    to host_out; *n_out receives the number of records available. */
 pa_status pa_schedule_log(pa_ctx *ctx, pa_sched_entry *host_out, long long max_entries, long long *n_out);

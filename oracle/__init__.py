@@ -115,6 +115,10 @@ def lib():
                                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]),
                 "orc_pa_propose_bisect": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                             ctypes.c_int, dp]),
+                "orc_accept_or_bisect": (ctypes.c_double, [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double,
+                                                           ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                           ctypes.c_double, ctypes.c_int, dp,
+                                                           ctypes.POINTER(ctypes.c_int)]),
                 "orc_bruteforce": (ctypes.c_int, [ctypes.c_int, i64p, i64p, i64p]),
                 "orc_transfer_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
                 "orc_kaufman_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
@@ -227,6 +231,19 @@ def bisect_next_beta(N, hist, beta, beta_final, dbeta_max, alpha_target, iters=B
     b = lib().orc_bisect_next_beta(N, _ptr(h, ctypes.c_int64), float(beta), float(beta_final),
                                    float(dbeta_max), float(alpha_target), int(iters), ctypes.byref(a))
     return float(b), float(a.value)
+
+
+def accept_or_bisect(N, hist, beta, beta_final, dbeta_max, dbeta_prop, alpha_floor, alpha_target,
+                     iters=BISECT_ITERS):
+    """Learned-schedule check: keep dbeta_prop if its overlap reaches alpha_floor, else bisect.
+    Returns (beta_next, alpha, source) with source 2 = kept, 3 = fallback."""
+    h = np.ascontiguousarray(hist, dtype=np.int64)
+    a = ctypes.c_double()
+    src = ctypes.c_int()
+    b = lib().orc_accept_or_bisect(N, _ptr(h, ctypes.c_int64), float(beta), float(beta_final), float(dbeta_max),
+                                   float(dbeta_prop), float(alpha_floor), float(alpha_target), int(iters),
+                                   ctypes.byref(a), ctypes.byref(src))
+    return float(b), float(a.value), int(src.value)
 
 
 # ----------------------------------------------------------------------------- exact

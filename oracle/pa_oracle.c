@@ -635,6 +635,33 @@ double orc_bisect_next_beta(int N, const int64_t *h, double beta, double beta_fi
     return beta + dbeta;
 }
 
+/* A proposed step (from the learned schedule) is kept if the overlap at that step reaches
+   alpha_floor (the proposal is first clipped to hi); otherwise the bisection above decides.
+   *source: 2 = proposal kept, 3 = bisection fallback. */
+double orc_accept_or_bisect(int N, const int64_t *h, double beta, double beta_final, double dbeta_max,
+                            double dbeta_prop, double alpha_floor, double alpha_target, int iters,
+                            double *alpha_out, int *source)
+{
+    double hi = beta_final - beta;
+    if (dbeta_max < hi) hi = dbeta_max;
+    if (!(hi > 0.0)) {
+        if (alpha_out) *alpha_out = 1.0;
+        *source = 2;
+        return beta_final;
+    }
+    double dp = dbeta_prop;
+    if (dp > hi) dp = hi;
+    double a_p = orc_overlap(N, h, dp);
+    if (a_p >= alpha_floor) {
+        if (alpha_out) *alpha_out = a_p;
+        *source = 2;
+        if (dp == hi && hi == beta_final - beta) return beta_final;
+        return beta + dp;
+    }
+    *source = 3;
+    return orc_bisect_next_beta(N, h, beta, beta_final, dbeta_max, alpha_target, iters, alpha_out);
+}
+
 double orc_pa_propose_bisect(const orc_pa *p, double beta_final, double dbeta_max, double alpha_target,
                              int iters, double *alpha_out)
 {

@@ -101,6 +101,21 @@ class PopulationAnnealing:
                                                                 float(beta_final), ctypes.byref(b), ctypes.byref(a)))
         return b.value, a.value
 
+    def features(self, theta0: int = 10) -> np.ndarray:
+        """The 12 learned-schedule inputs of the current population (float32)."""
+        out = np.zeros(12, np.float32)
+        _check(self.lib, self.ctx, self.lib.pa_features(self.ctx, int(theta0), out.ctypes.data))
+        return out
+
+    def propose_learned(self, model, alpha_floor: float = 0.7, alpha_target: float = 0.8, dbeta_max: float = 0.1,
+                        beta_final: float = 1.0, theta0: int = 10, theta_max: int = 40) -> dict:
+        """Learned step (network proposal checked against the overlap floor, bisection fallback)."""
+        out = _lib.pa_proposal()
+        _check(self.lib, self.ctx, self.lib.pa_propose_learned(
+            self.ctx, ctypes.byref(model.c_model()), float(alpha_floor), float(alpha_target), float(dbeta_max),
+            float(beta_final), int(theta0), int(theta_max), ctypes.byref(out)))
+        return out.as_dict()
+
     def schedule_log(self) -> list[dict]:
         n = ctypes.c_longlong()
         _check(self.lib, self.ctx, self.lib.pa_schedule_log(self.ctx, None, 0, ctypes.byref(n)))

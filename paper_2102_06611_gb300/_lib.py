@@ -61,6 +61,19 @@ class pa_sched_entry(ctypes.Structure):
 
 PA_SCHED_CALLER, PA_SCHED_BISECT, PA_SCHED_LEARNED, PA_SCHED_FALLBACK = 0, 1, 2, 3
 
+
+class pa_learned_model(ctypes.Structure):
+    _fields_ = [("params_bf16", ctypes.c_void_p), ("norm", ctypes.c_void_p)]
+
+
+class pa_proposal(ctypes.Structure):
+    _fields_ = [("beta_next", ctypes.c_double), ("alpha", ctypes.c_double), ("dbeta_prop", ctypes.c_double),
+                ("theta_next", ctypes.c_int), ("theta_prop", ctypes.c_int), ("source", ctypes.c_int),
+                ("pad", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+
 # name -> (restype, argtypes): every entry point declared in include/pa.h
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
@@ -74,6 +87,16 @@ SIGNATURES = {
     "pa_propose_schedule": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            _P(ctypes.c_double), _P(ctypes.c_double)]),
     "pa_schedule_log": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, _P(ctypes.c_longlong)]),
+    "pa_mlp_param_count": (ctypes.c_size_t, []),
+    "pa_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, _vp]),
+    "pa_mlp_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "pa_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, _vp, _vp]),
+    "pa_mlp_round": (ctypes.c_int, [_vp, _vp, _vp]),
+    "pa_features": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "pa_propose_learned": (ctypes.c_int, [_vp, _P(pa_learned_model), ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          _P(pa_proposal)]),
     "pa_sync": (ctypes.c_int, [_vp]),
     "pa_population": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
     "pa_histogram": (ctypes.c_int, [_vp, _vp]),

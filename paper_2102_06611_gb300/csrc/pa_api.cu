@@ -336,6 +336,96 @@ pa_status pa_propose_schedule(pa_ctx *c, double alpha_target, double dbeta_max, 
     return PA_OK;
 }
 
+// Features of the current population on the device (raw in feat[0..11], standardised in
+// feat[16..27]); the previous-step inputs come from the schedule log.
+static pa_status launch_feature_pass(pa_ctx *c, int theta0, const float *norm)
+{
+    pa_status s;
+    if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
+    cudaError_t e = pa::launch_families(c->st, cur_fam(c), at<long long>(c, c->ws.fampart), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "families launch");
+    pa::FeatureArgs a{};
+    a.L = c->cfg.L;
+    a.st = c->st;
+    a.hist = at<int>(c, c->ws.hist);
+    a.fampart = at<long long>(c, c->ws.fampart);
+    a.counts = at<int>(c, c->ws.counts);
+    a.beta = c->beta;
+    a.dbeta_prev = c->dbeta;
+    const bool have = !c->log.empty();
+    a.theta_ratio_prev = have ? (double)c->log.back().theta / (double)theta0 : 0.0;
+    a.alpha_prev = (have && std::isfinite(c->log.back().alpha)) ? c->log.back().alpha : 1.0;
+    a.norm = norm;
+    a.raw = at<float>(c, c->ws.feat);
+    a.x = at<float>(c, c->ws.feat) + 16;
+    e = pa::launch_features(a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "features launch");
+    return PA_OK;
+}
+
+pa_status pa_features(pa_ctx *c, int theta0, float *host_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!host_out || theta0 < 1) return fail(c, PA_ERR_INVALID_ARG, "bad feature arguments");
+    DeviceGuard g(c->device);
+    if ((s = launch_feature_pass(c, theta0, nullptr)) != PA_OK) return s;
+    if ((s = sync_and_check(c)) != PA_OK) return s;
+    cudaError_t e = cudaMemcpy(host_out, at<float>(c, c->ws.feat), 12 * sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PA_OK : cuda_fail(c, e, "feature copy");
+}
+
+pa_status pa_propose_learned(pa_ctx *c, const pa_learned_model *model, double alpha_floor, double alpha_target,
+                             double dbeta_max, double beta_final, int theta0, int theta_max, pa_proposal *out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!model || !model->params_bf16 || !model->norm || !out || theta0 < 1 || theta_max < 1 ||
+        !(alpha_floor > 0.0 && alpha_floor <= 1.0) || !(alpha_target > 0.0 && alpha_target <= 1.0) ||
+        !(dbeta_max > 0.0) || !std::isfinite(dbeta_max) || !std::isfinite(beta_final))
+        return fail(c, PA_ERR_INVALID_ARG, "bad learned-schedule arguments");
+    if (beta_final < c->beta)
+        return fail(c, PA_ERR_STATE, "beta_final %.17g below current beta %.17g", beta_final, c->beta);
+    DeviceGuard g(c->device);
+    if ((s = launch_feature_pass(c, theta0, model->norm)) != PA_OK) return s;
+    cudaError_t e = pa::launch_mlp_propose(model->params_bf16, model->norm, at<float>(c, c->ws.feat) + 16,
+                                           c->cfg.L, dbeta_max, theta_max, c->st, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "network launch");
+    pa::BisectArgs a{};
+    a.L = c->cfg.L;
+    a.st = c->st;
+    a.hist = at<int>(c, c->ws.hist);
+    a.occ_k = at<int>(c, c->ws.occ_k);
+    a.occ_h = at<int>(c, c->ws.occ_h);
+    a.occ_w = at<double>(c, c->ws.occ_w);
+    a.occ_t = at<double>(c, c->ws.occ_t);
+    a.beta = c->beta;
+    a.beta_final = beta_final;
+    a.dbeta_max = dbeta_max;
+    a.alpha_target = alpha_target;
+    a.iters = pa::kBisectIters;
+    a.use_prop = 1;
+    a.alpha_floor = alpha_floor;
+    e = pa::launch_bisect(a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "proposal check launch");
+    if ((s = sync_and_check(c)) != PA_OK) return s;
+    pa::DevState h;
+    e = cudaMemcpy(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "proposal copy");
+    out->beta_next = h.beta_next;
+    out->alpha = h.alpha_next;
+    out->dbeta_prop = h.dbeta_prop;
+    out->theta_prop = h.theta_prop;
+    out->source = h.source_next;
+    out->theta_next = h.source_next == PA_SCHED_LEARNED ? h.theta_prop : theta0;
+    out->pad = 0;
+    c->prop_valid = true;
+    c->prop_beta = h.beta_next;
+    c->prop_alpha = h.alpha_next;
+    c->prop_source = h.source_next;
+    return PA_OK;
+}
+
 pa_status pa_schedule_log(pa_ctx *c, pa_sched_entry *host_out, long long max_entries, long long *n_out)
 {
     if (!c || !n_out || max_entries < 0 || (max_entries > 0 && !host_out)) return PA_ERR_INVALID_ARG;

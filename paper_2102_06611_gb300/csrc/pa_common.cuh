@@ -156,6 +156,10 @@ struct DevState {
     // result of the last schedule proposal
     double beta_next;
     double alpha_next;
+    double dbeta_prop;        // learned proposal (before the overlap check)
+    int theta_prop;
+    int source_next;          // PA_SCHED_* of beta_next
+    float y_prop[2];          // raw network outputs of the proposal
     int theta;
     int pad;
 };

@@ -27,6 +27,7 @@ struct Workspace {
     size_t occ_h;       // int32[N + 1]   their counts
     size_t occ_w;       // double[N + 1]  reweighting factors at a trial step
     size_t occ_t;       // double[N + 1]  overlap terms at a trial step
+    size_t feat;        // float[32]      learned-schedule features (raw, standardised)
     size_t total;
     long long nblk;     // blocks of the copy-count / copy kernels
 };
@@ -108,11 +109,31 @@ struct BisectArgs {
     double *occ_w, *occ_t;
     double beta, beta_final, dbeta_max, alpha_target;
     int iters;
+    int use_prop;        // first try the step in st->dbeta_prop against alpha_floor
+    double alpha_floor;
 };
 
 constexpr int kBisectIters = 48;
 
 cudaError_t launch_bisect(const BisectArgs &a, cudaStream_t s);
+cudaError_t launch_families(const DevState *st, const int *fam, long long *fampart, cudaStream_t s);
+
+// Learned schedule (pa_mlp.cu).
+struct FeatureArgs {
+    int L;
+    const DevState *st;
+    const int *hist;
+    const long long *fampart;
+    const int *counts;
+    double beta, dbeta_prev, theta_ratio_prev, alpha_prev;
+    const float *norm;   // x_mean[12], x_std[12], y_mean[2], y_std[2] (may be null: raw only)
+    float *raw;          // 12 features
+    float *x;            // 12 standardised features
+};
+
+cudaError_t launch_features(const FeatureArgs &a, cudaStream_t s);
+cudaError_t launch_mlp_propose(const unsigned short *P, const float *norm, const float *x, int L, double dbeta_max,
+                               int theta_max, DevState *st, cudaStream_t s);
 
 cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
                           unsigned long long *out, cudaStream_t s);

@@ -48,6 +48,7 @@ Workspace plan_workspace(int L, long long capacity)
     w.occ_h = off;    off = align256(off + nlev * 4);
     w.occ_w = off;    off = align256(off + nlev * 8);
     w.occ_t = off;    off = align256(off + nlev * 8);
+    w.feat = off;     off = align256(off + 32 * 4);
     w.total = off;
     w.nblk = nblk;
     return w;
@@ -582,11 +583,29 @@ __global__ void __launch_bounds__(kBisectThreads) k_bisect(BisectArgs a)
     if (!(hi > 0.0) || nocc == 0) {
         beta_next = a.beta_final;
         alpha = 1.0;
+        if (tid == 0) st->source_next = a.use_prop ? PA_SCHED_LEARNED : PA_SCHED_BISECT;
     } else {
         const double hi0 = hi;
-        double dbeta;
-        const double a_hi = overlap(hi);
-        if (a_hi >= a.alpha_target) {
+        double dbeta = 0.0;
+        bool done = false;
+        int source = PA_SCHED_BISECT;
+        if (a.use_prop) {
+            // a proposed step is kept if its overlap reaches the floor
+            double dp = st->dbeta_prop;
+            if (dp > hi) dp = hi;
+            const double a_p = overlap(dp);
+            if (a_p >= a.alpha_floor) {
+                dbeta = dp;
+                alpha = a_p;
+                done = true;
+                source = PA_SCHED_LEARNED;
+            } else {
+                source = PA_SCHED_FALLBACK;
+            }
+        }
+        const double a_hi = done ? 0.0 : overlap(hi);
+        if (done) {
+        } else if (a_hi >= a.alpha_target) {
             dbeta = hi;
             alpha = a_hi;
         } else {
@@ -611,11 +630,18 @@ __global__ void __launch_bounds__(kBisectThreads) k_bisect(BisectArgs a)
         }
         beta_next = (dbeta == hi0 && hi0 == __dsub_rn(a.beta_final, a.beta)) ? a.beta_final
                                                                             : __dadd_rn(a.beta, dbeta);
+        if (tid == 0) st->source_next = source;
     }
     if (tid == 0) {
         st->beta_next = beta_next;
         st->alpha_next = alpha;
     }
+}
+
+cudaError_t launch_families(const DevState *st, const int *fam, long long *fampart, cudaStream_t s)
+{
+    k_families<<<kFamBlocks, 256, 0, s>>>(st, fam, fampart);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bisect(const BisectArgs &a, cudaStream_t s)
