@@ -184,8 +184,8 @@ pa_status pa_propose_schedule(pa_ctx *ctx, double alpha_target, double dbeta_max
    Inputs (float32, from binary64 statistics of the current population): beta, ln L, ln R_i,
    <E>/N, ln(Var(E)/N + 1e-12), skewness and excess kurtosis of E, previous dbeta * L,
    previous theta / theta0, previous overlap, ln(rho_t) / ln(R_i) (Eq. rhot), fraction of
-   parents given no copy at the last resampling.  Outputs (standardised): ln(dbeta L) and
-   ln(theta). */
+   parents given no copy at the last resampling.  Outputs (standardised): ln(dbeta sigma_E)
+   (sigma_E = the population's energy standard deviation) and ln(theta). */
 typedef struct {
     const unsigned short *params_bf16; /* device, 9282 bfloat16 patterns */
     const float *norm;                 /* device, 28 floats: x_mean[12], x_std[12], y_mean[2], y_std[2] */
@@ -233,6 +233,14 @@ pa_status pa_features(pa_ctx *ctx, int theta0, float *host_out);
    pa_propose_schedule with alpha_target decides and theta0 sweeps are used.  Synchronising. */
 pa_status pa_propose_learned(pa_ctx *ctx, const pa_learned_model *model, double alpha_floor, double alpha_target,
                              double dbeta_max, double beta_final, int theta0, int theta_max, pa_proposal *out);
+
+/* Decorrelation of the current temperature step (a design diagnostic for the sweep count; the
+   paper only asks for theta large enough to equilibrate, Sec. X): the Pearson correlation over
+   replicas of the energy level right after the step's resampling and after the sweeps run so
+   far at this step, from the exact integer sums of both levels, their squares and product
+   (accumulated by the sweep kernel; sums_out, optional, receives them in that order).
+   Synchronising. */
+pa_status pa_decorrelation(pa_ctx *ctx, double *corr_out, long long *sums_out);
 
 /* Copy up to max_entries records of the schedule run so far (one per pa_resample, in order)
    to host_out; *n_out receives the number of records available. */

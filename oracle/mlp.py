@@ -124,12 +124,27 @@ def features(L: int, hist, beta: float, dbeta_prev: float, theta_prev_over_theta
                      math.log(rho_t) / lnR if lnR > 0 else 0.0, frac0])
 
 
-def theta_label(mean_E, std_E, R: int, theta_max: int) -> int:
+THETA_CORR = 0.3
+
+
+def replica_correlation(E0, Et) -> float:
+    """Pearson correlation over replicas of the energies right after resampling and after t
+    sweeps (0 when either has no spread)."""
+    a = np.asarray(E0, dtype=np.float64)
+    b = np.asarray(Et, dtype=np.float64)
+    a = a - a.mean()
+    b = b - b.mean()
+    d = math.sqrt(float((a * a).sum()) * float((b * b).sum()))
+    return float((a * b).sum()) / d if d > 0 else 0.0
+
+
+def theta_label(E0, E_after, theta_max: int, threshold: float = THETA_CORR) -> int:
     """Sweeps needed at a temperature step (a design rule; the paper's adaptive theta is not
-    printed): the smallest t in 1..theta_max with |E(t) - E(t-1)| <= sigma_t(E) / sqrt(R),
-    where E(t) and sigma_t(E) are the population mean and standard deviation of the energy
-    after t sweeps (t = 0: right after resampling); theta_max if no t qualifies."""
-    for t in range(1, min(len(mean_E), theta_max + 1)):
-        if abs(mean_E[t] - mean_E[t - 1]) <= std_E[t] / math.sqrt(R):
+    printed, Sec. X): the smallest t in 1..theta_max at which the replicas' energies after t
+    sweeps have decorrelated from their values right after resampling,
+    corr_j(E_j(0), E_j(t)) <= threshold; theta_max if none does.  E_after[t-1] holds the
+    energies after t sweeps."""
+    for t in range(1, min(len(E_after), theta_max) + 1):
+        if replica_correlation(E0, E_after[t - 1]) <= threshold:
             return t
     return theta_max

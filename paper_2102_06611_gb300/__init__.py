@@ -107,6 +107,13 @@ class PopulationAnnealing:
         _check(self.lib, self.ctx, self.lib.pa_features(self.ctx, int(theta0), out.ctypes.data))
         return out
 
+    def decorrelation(self, with_sums: bool = False):
+        """Correlation over replicas of the energy level after this step's resampling and now."""
+        c = ctypes.c_double()
+        sums = np.zeros(5, np.int64)
+        _check(self.lib, self.ctx, self.lib.pa_decorrelation(self.ctx, ctypes.byref(c), sums.ctypes.data))
+        return (c.value, sums) if with_sums else c.value
+
     def propose_learned(self, model, alpha_floor: float = 0.7, alpha_target: float = 0.8, dbeta_max: float = 0.1,
                         beta_final: float = 1.0, theta0: int = 10, theta_max: int = 40) -> dict:
         """Learned step (network proposal checked against the overlap floor, bisection fallback)."""

@@ -94,6 +94,7 @@ SIGNATURES = {
                                    ctypes.c_float, ctypes.c_float, _vp, _vp]),
     "pa_mlp_round": (ctypes.c_int, [_vp, _vp, _vp]),
     "pa_features": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "pa_decorrelation": (ctypes.c_int, [_vp, _P(ctypes.c_double), _vp]),
     "pa_propose_learned": (ctypes.c_int, [_vp, _P(pa_learned_model), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                           _P(pa_proposal)]),

@@ -267,6 +267,7 @@ static pa_status sweep_and_measure(pa_ctx *c, int theta)
     a.level = cur_level(c);
     a.mag = cur_mag(c);
     a.fam = cur_fam(c);
+    a.level_snap = at<int>(c, c->ws.snap);
     a.hist = at<int>(c, c->ws.hist);
     a.st = c->st;
     a.R_init = 0;
@@ -336,6 +337,30 @@ pa_status pa_propose_schedule(pa_ctx *c, double alpha_target, double dbeta_max, 
     return PA_OK;
 }
 
+pa_status pa_decorrelation(pa_ctx *c, double *corr_out, long long *sums_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!corr_out) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
+    if ((s = sync_and_check(c)) != PA_OK) return s;
+    long long v[5];
+    long long R;
+    cudaError_t e = cudaMemcpy(v, &c->st->c0, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&R, &c->st->R_cur, sizeof(R), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "correlation sums copy");
+    // corr = cov(k0, k1) / sqrt(var k0 var k1), all from exact integer sums
+    const double Rd = (double)R;
+    const double cov = (double)v[4] - (double)v[0] * (double)v[2] / Rd;
+    const double v0 = (double)v[1] - (double)v[0] * (double)v[0] / Rd;
+    const double v1 = (double)v[3] - (double)v[2] * (double)v[2] / Rd;
+    *corr_out = (v0 > 0.0 && v1 > 0.0) ? cov / std::sqrt(v0 * v1) : 0.0;
+    if (sums_out)
+        for (int i = 0; i < 5; ++i) sums_out[i] = v[i];
+    return PA_OK;
+}
+
 // Features of the current population on the device (raw in feat[0..11], standardised in
 // feat[16..27]); the previous-step inputs come from the schedule log.
 static pa_status launch_feature_pass(pa_ctx *c, int theta0, const float *norm)
@@ -388,7 +413,8 @@ pa_status pa_propose_learned(pa_ctx *c, const pa_learned_model *model, double al
         return fail(c, PA_ERR_STATE, "beta_final %.17g below current beta %.17g", beta_final, c->beta);
     DeviceGuard g(c->device);
     if ((s = launch_feature_pass(c, theta0, model->norm)) != PA_OK) return s;
-    cudaError_t e = pa::launch_mlp_propose(model->params_bf16, model->norm, at<float>(c, c->ws.feat) + 16,
+    cudaError_t e = pa::launch_mlp_propose(model->params_bf16, model->norm, at<float>(c, c->ws.feat),
+                                           at<float>(c, c->ws.feat) + 16,
                                            c->cfg.L, dbeta_max, theta_max, c->st, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "network launch");
     pa::BisectArgs a{};

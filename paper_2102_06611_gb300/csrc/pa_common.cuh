@@ -160,6 +160,9 @@ struct DevState {
     int theta_prop;
     int source_next;          // PA_SCHED_* of beta_next
     float y_prop[2];          // raw network outputs of the proposal
+    // sums over replicas of the energy level at the start of the temperature step (k0) and
+    // after the last sweep call (k1): sum k0, k0^2, k1, k1^2, k0 k1 (exact)
+    long long c0, c00, c1, c11, c01;
     int theta;
     int pad;
 };

@@ -28,6 +28,7 @@ struct Workspace {
     size_t occ_w;       // double[N + 1]  reweighting factors at a trial step
     size_t occ_t;       // double[N + 1]  overlap terms at a trial step
     size_t feat;        // float[32]      learned-schedule features (raw, standardised)
+    size_t snap;        // int32[capacity] levels at the start of the temperature step
     size_t total;
     long long nblk;     // blocks of the copy-count / copy kernels
 };
@@ -45,6 +46,7 @@ struct SweepArgs {
     int *level;
     int *mag;
     int *fam;               // written only by the init kernel
+    int *level_snap;        // levels at the start of the temperature step (sweep kernel)
     int *hist;
     DevState *st;
     long long R_init;       // population size for the init kernel
@@ -132,8 +134,8 @@ struct FeatureArgs {
 };
 
 cudaError_t launch_features(const FeatureArgs &a, cudaStream_t s);
-cudaError_t launch_mlp_propose(const unsigned short *P, const float *norm, const float *x, int L, double dbeta_max,
-                               int theta_max, DevState *st, cudaStream_t s);
+cudaError_t launch_mlp_propose(const unsigned short *P, const float *norm, const float *raw, const float *x, int L,
+                               double dbeta_max, int theta_max, DevState *st, cudaStream_t s);
 
 cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
                           unsigned long long *out, cudaStream_t s);

@@ -230,10 +230,14 @@ __global__ void __launch_bounds__(1024) k_features(FeatureArgs a)
     }
 }
 
-// One network evaluation for the proposal: (dbeta, theta) from the standardised outputs
-// y0 = ln(dbeta L), y1 = ln(theta), clamped to dbeta in (0, dbeta_max], theta in [1, theta_max].
-__global__ void __launch_bounds__(kHid) k_mlp_propose(const unsigned short *P, const float *norm, const float *x,
-                                                      int L, double dbeta_max, int theta_max, DevState *st)
+// One network evaluation for the proposal: (dbeta, theta) from the de-standardised outputs
+// y0 = ln(dbeta sigma_E) (the overlap of nearby energy distributions depends mainly on
+// dbeta times the energy width sigma_E, so this target carries over between lattice sizes)
+// and y1 = ln(theta); sigma_E^2 = N exp(raw feature 4); clamped to dbeta in (0, dbeta_max],
+// theta in [1, theta_max].
+__global__ void __launch_bounds__(kHid) k_mlp_propose(const unsigned short *P, const float *norm, const float *raw,
+                                                      const float *x, int L, double dbeta_max, int theta_max,
+                                                      DevState *st)
 {
     __shared__ float sa[kActs];
     __shared__ float sy[kOut];
@@ -242,7 +246,8 @@ __global__ void __launch_bounds__(kHid) k_mlp_propose(const unsigned short *P, c
     if (j == 0) {
         const float y0 = sy[0] * norm[2 * kIn + kOut + 0] + norm[2 * kIn + 0];
         const float y1 = sy[1] * norm[2 * kIn + kOut + 1] + norm[2 * kIn + 1];
-        double dbeta = exp((double)y0) / (double)L;
+        const double sigma_E = sqrt((double)L * (double)L * exp((double)raw[4]));
+        double dbeta = exp((double)y0) / sigma_E;
         if (!(dbeta > 0.0)) dbeta = 1e-12;
         if (dbeta > dbeta_max) dbeta = dbeta_max;
         double th = rint(exp((double)y1));
@@ -261,10 +266,10 @@ cudaError_t launch_features(const FeatureArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_propose(const unsigned short *P, const float *norm, const float *x, int L, double dbeta_max,
-                               int theta_max, DevState *st, cudaStream_t s)
+cudaError_t launch_mlp_propose(const unsigned short *P, const float *norm, const float *raw, const float *x, int L,
+                               double dbeta_max, int theta_max, DevState *st, cudaStream_t s)
 {
-    k_mlp_propose<<<1, kHid, 0, s>>>(P, norm, x, L, dbeta_max, theta_max, st);
+    k_mlp_propose<<<1, kHid, 0, s>>>(P, norm, raw, x, L, dbeta_max, theta_max, st);
     return cudaGetLastError();
 }
 

@@ -49,6 +49,7 @@ Workspace plan_workspace(int L, long long capacity)
     w.occ_w = off;    off = align256(off + nlev * 8);
     w.occ_t = off;    off = align256(off + nlev * 8);
     w.feat = off;     off = align256(off + 32 * 4);
+    w.snap = off;     off = align256(off + (size_t)capacity * 4);
     w.total = off;
     w.nblk = nblk;
     return w;
@@ -126,6 +127,7 @@ __global__ void k_zero_measure(DevState *st, int *hist, int nlev)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->sum_absM = 0;
         st->sum_M2 = 0;
+        st->c0 = st->c00 = st->c1 = st->c11 = st->c01 = 0;
     }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlev; k += gridDim.x * blockDim.x) hist[k] = 0;
 }

@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
     const Accept<W> ac = make_accept<W>(a.st->T4, a.st->T8);
 
     unsigned long long s_abs = 0, s_m2 = 0;
+    long long c0 = 0, c00 = 0, c1 = 0, c11 = 0, c01 = 0;  // levels at step start (0) and now (1)
     W *spins = reinterpret_cast<W *>(a.spins);
 
     for (long long base = warp * RPW; base < R; base += nwarps * RPW) {
@@ -416,6 +417,17 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
             if (q == 0) {
                 const int level = anti >> 1;
                 const int M = 2 * ups - N;
+                if (!INIT) {
+                    // level at the start of this temperature step (right after resampling),
+                    // kept in level_snap by the step's first call
+                    const long long k0 = a.t0 == 0 ? a.level[j] : a.level_snap[j];
+                    if (a.t0 == 0) a.level_snap[j] = (int)k0;
+                    c0 += k0;
+                    c00 += k0 * k0;
+                    c1 += level;
+                    c11 += (long long)level * level;
+                    c01 += k0 * level;
+                }
                 a.level[j] = level;
                 a.mag[j] = M;
                 if (INIT) a.fam[j] = (int)j;
@@ -432,6 +444,20 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
     if (lane == 0 && (s_abs | s_m2)) {
         atomicAdd(&a.st->sum_absM, s_abs);
         atomicAdd(&a.st->sum_M2, s_m2);
+    }
+    if (!INIT) {
+        c0 = group_sum<32>(c0);
+        c00 = group_sum<32>(c00);
+        c1 = group_sum<32>(c1);
+        c11 = group_sum<32>(c11);
+        c01 = group_sum<32>(c01);
+        if (lane == 0 && c00) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), (unsigned long long)c0);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), (unsigned long long)c00);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), (unsigned long long)c1);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), (unsigned long long)c11);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), (unsigned long long)c01);
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k <= N; k += blockDim.x) {

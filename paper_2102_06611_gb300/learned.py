@@ -8,9 +8,12 @@ The paper has no learned schedule (it names self-adaptive steps, Sec. II, an ove
 histogram overlap reaches a floor, and falls back to the plain overlap bisection otherwise.
 
 Training data come from plain runs: dbeta from the overlap bisection (target 0.8) and theta
-from a relaxation rule -- after resampling, sweeps are run one at a time and theta is the first
-t <= theta_max at which the population mean energy moves by no more than its standard
-deviation over sqrt(R) (|E(t) - E(t-1)| <= sigma_t(E) / sqrt(R)).
+from a decorrelation rule -- after resampling, sweeps are run one at a time and theta is the
+first t <= theta_max at which the replicas' energies have decorrelated from their values right
+after resampling, corr_j(E_j(0), E_j(t)) <= 0.3.  Copies made by resampling start identical, so
+this measures how long the chain needs to make them independent; it grows where relaxation is
+slow (near the critical point) and is one or two sweeps elsewhere.  Targets: ln(dbeta sigma_E)
+with sigma_E the energy standard deviation of the population, and ln(theta).
 """
 from __future__ import annotations
 
@@ -73,8 +76,16 @@ class ScheduleMLP:
     def c_model(self) -> _lib.pa_learned_model:
         return _lib.pa_learned_model(self.params.data_ptr(), self.norm.data_ptr())
 
+    # Lower bounds of the input scales: an input that barely varies in the training runs (ln R
+    # at a fixed population size, the overlap near its target) must stay O(1) after
+    # standardisation for other lattice or population sizes.  Order: beta, ln L, ln R, e,
+    # ln(Var/N), skewness, kurtosis, dbeta_prev L, theta_prev/theta0, alpha_prev,
+    # ln rho_t / ln R, zero-copy fraction.
+    X_STD_FLOOR = np.array([0.05, 0.5, 2.0, 0.05, 0.1, 0.1, 0.1, 0.05, 0.1, 0.05, 0.05, 0.05])
+
     def set_norm(self, x_mean, x_std, y_mean, y_std):
-        n = np.concatenate([x_mean, np.maximum(x_std, 1e-6), y_mean, np.maximum(y_std, 1e-6)]).astype(np.float32)
+        n = np.concatenate([x_mean, np.maximum(x_std, self.X_STD_FLOOR), y_mean,
+                            np.maximum(y_std, 1e-6)]).astype(np.float32)
         self.norm.copy_(torch.from_numpy(n))
 
     def forward(self, x: torch.Tensor, act: torch.Tensor | None = None) -> torch.Tensor:
@@ -132,16 +143,24 @@ class ScheduleMLP:
 
 
 # ------------------------------------------------------------------------------ data
-def _mean_std_E(obs: dict):
-    R = obs["R"]
-    mean = obs["sum_E"] / R
-    var = max(obs["sum_E2"] / R - mean * mean, 0.0)
-    return mean, math.sqrt(var), R
+THETA_CORR = 0.3
+
+
+def _correlation(a: np.ndarray, b: np.ndarray) -> float:
+    a = a - a.mean()
+    b = b - b.mean()
+    d = math.sqrt(float((a * a).sum()) * float((b * b).sum()))
+    return float((a * b).sum()) / d if d > 0 else 0.0
+
+
+def energy_width(L: int, raw_features: np.ndarray) -> float:
+    """sigma_E of the population from raw feature 4 = ln(Var(E)/N + 1e-12), as the kernel does."""
+    return math.sqrt(L * L * math.exp(float(np.float32(raw_features[4]))))
 
 
 def plain_training_run(L: int, R: int, seed: int, alpha_target: float = 0.8, theta0: int = 10,
                        theta_max: int = 40, dbeta_max: float = 0.1, beta_final: float = 1.0, device="cuda"):
-    """(features, targets) of one plain adaptive run: targets ln(dbeta L), ln(theta)."""
+    """(features, targets) of one plain adaptive run: targets ln(dbeta sigma_E), ln(theta)."""
     pa = PopulationAnnealing(L, R, seed, device=device)
     X, Y = [], []
     beta = 0.0
@@ -149,21 +168,14 @@ def plain_training_run(L: int, R: int, seed: int, alpha_target: float = 0.8, the
         f = pa.features(theta0)
         b_next, _ = pa.propose_schedule(alpha_target, dbeta_max, beta_final)
         pa.resample(b_next)
-        means, stds = [], []
-        m, s, Ri = _mean_std_E(pa.observables())
-        means.append(m)
-        stds.append(s)
         theta = theta_max
         for t in range(1, theta_max + 1):
             pa.anneal_step(1)
-            m, s, Ri = _mean_std_E(pa.observables())
-            means.append(m)
-            stds.append(s)
-            if abs(means[t] - means[t - 1]) <= stds[t] / math.sqrt(Ri):
+            if pa.decorrelation() <= THETA_CORR:
                 theta = t
                 break
         X.append(f)
-        Y.append([math.log((b_next - beta) * L), math.log(theta)])
+        Y.append([math.log((b_next - beta) * energy_width(L, f)), math.log(theta)])
         beta = b_next
     pa.close()
     return np.array(X, np.float64), np.array(Y, np.float64)
@@ -172,12 +184,19 @@ def plain_training_run(L: int, R: int, seed: int, alpha_target: float = 0.8, the
 # ------------------------------------------------------------------------------ drivers
 def anneal(pa: PopulationAnnealing, mode: str = "plain", model: ScheduleMLP | None = None,
            alpha_target: float = 0.8, alpha_floor: float = 0.7, theta0: int = 10, theta_max: int = 40,
-           dbeta_max: float = 0.1, beta_final: float = 1.0) -> dict:
-    """Anneal from the population's current beta to beta_final with the plain adaptive schedule
-    (overlap bisection, theta0 sweeps) or the learned one; wall time includes every proposal."""
+           dbeta_max: float = 0.1, beta_final: float = 1.0, corr_target: float = THETA_CORR) -> dict:
+    """Anneal from the population's current beta to beta_final and time it (every proposal and
+    check included).
+
+    plain:   overlap bisection (alpha_target) and theta0 sweeps per temperature.
+    learned: the network proposes (dbeta, theta); dbeta is kept if the overlap reaches
+             alpha_floor (else the bisection decides and theta0 sweeps are used); after the
+             proposed sweeps the decorrelation since resampling is measured and, while it is
+             above corr_target, more sweeps run (half as many again each time, up to theta_max).
+    """
     torch.cuda.synchronize(pa.device)
     t0 = time.perf_counter()
-    beta, steps, sweeps, fallbacks = 0.0, 0, 0, 0
+    beta, steps, sweeps, fallbacks, extended = 0.0, 0, 0, 0, 0
     while beta < beta_final:
         if mode == "plain":
             b, _ = pa.propose_schedule(alpha_target, dbeta_max, beta_final)
@@ -188,10 +207,17 @@ def anneal(pa: PopulationAnnealing, mode: str = "plain", model: ScheduleMLP | No
             fallbacks += p["source"] == _lib.PA_SCHED_FALLBACK
         pa.resample(b)
         pa.anneal_step(theta)
+        if mode != "plain":
+            while theta < theta_max and pa.decorrelation() > corr_target:
+                more = min(max(1, theta // 2), theta_max - theta)
+                pa.anneal_step(more)
+                theta += more
+                extended += 1
         steps += 1
         sweeps += theta
         beta = b
     obs = pa.observables()
     wall = time.perf_counter() - t0
     return {"mode": mode, "wall_s": wall, "steps": steps, "sweeps": sweeps, "fallbacks": fallbacks,
-            "minus_betaF": obs["minus_betaF"], "e": obs["e"], "R": obs["R"], "beta": obs["beta"]}
+            "extensions": extended, "minus_betaF": obs["minus_betaF"], "e": obs["e"], "R": obs["R"],
+            "beta": obs["beta"]}

@@ -90,6 +90,28 @@ def test_features_match_oracle():
     assert np.allclose(f1, f1_ref, rtol=2e-6, atol=1e-6), (f1, f1_ref)
 
 
+def test_decorrelation_sums_match_oracle():
+    """The sweep kernel's exact sums of the levels at the step start and now, across two calls
+    at the same temperature, against the oracle's energies."""
+    from paper_2102_06611_gb300 import PopulationAnnealing
+    L, R, seed = 16, 2000, 6
+    N = L * L
+    gpu = PopulationAnnealing(L, R, seed)
+    ref = oracle.PA(L, R, seed, capacity=gpu.capacity)
+    ref.init()
+    gpu.resample(0.35)
+    ref.resample(0.35)
+    k0 = (ref.state()[0].astype(np.int64) + 2 * N) // 4
+    for theta in (2, 3):
+        gpu.anneal_step(theta)
+        ref.sweep(theta)
+        k1 = (ref.state()[0].astype(np.int64) + 2 * N) // 4
+        c, sums = gpu.decorrelation(with_sums=True)
+        want = [k0.sum(), (k0 * k0).sum(), k1.sum(), (k1 * k1).sum(), (k0 * k1).sum()]
+        assert [int(x) for x in sums] == [int(x) for x in want]
+        assert c == pytest.approx(float(np.corrcoef(k0, k1)[0, 1]), abs=1e-12)
+
+
 def test_learned_anneal_replayed_by_oracle():
     """The network's proposals go through the overlap floor; the oracle, given each proposed
     dbeta, takes the same decision and the same fallback bisection, and the populations stay

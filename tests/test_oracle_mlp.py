@@ -74,8 +74,17 @@ def test_features_from_population():
 
 
 def test_theta_label_rule():
-    means = [10.0, 6.0, 4.0, 3.5, 3.45, 3.44]
-    stds = [5.0] * 6
-    # threshold 5 / sqrt(100) = 0.5: first |dE| <= 0.5 is t = 3 (4.0 -> 3.5)
-    assert mlp.theta_label(means, stds, 100, 40) == 3
-    assert mlp.theta_label(means, stds, 10 ** 6, 40) == 40 or mlp.theta_label(means, stds, 10 ** 6, 5) == 5
+    """An AR(1) chain per replica with known autocorrelation rho^t crosses 0.3 at
+    t = ceil(ln 0.3 / ln rho)."""
+    rng = np.random.default_rng(6)
+    R = 200000
+    for rho, want in ((0.5, 2), (0.8, 6), (0.95, 24)):
+        E0 = rng.standard_normal(R)
+        E, after = E0.copy(), []
+        for t in range(40):
+            E = rho * E + math.sqrt(1 - rho * rho) * rng.standard_normal(R)
+            after.append(E)
+        assert mlp.theta_label(E0, after, 40) == want
+        assert mlp.replica_correlation(E0, after[0]) == pytest.approx(rho, abs=0.01)
+    assert mlp.theta_label(E0, [E0] * 5, 5) == 5          # never decorrelates: theta_max
+    assert mlp.replica_correlation(np.ones(10), np.arange(10)) == 0.0
