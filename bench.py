@@ -57,6 +57,7 @@ def _parse_args():
     p.add_argument("--R", type=int, default=R_DEFAULT)
     p.add_argument("--theta", type=int, default=THETA)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-schedule-eval", action="store_true")
     return p.parse_args()
 
 
@@ -130,6 +131,40 @@ def cpu_baseline(L: int, theta: int) -> dict:
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"L={L}, R={R_sample}, {steps} temperature steps beta=i/300, theta={theta}: "
                       f"{att:.3g} attempts in {dt:.1f} s (single-threaded C oracle)"}
+
+
+# ------------------------------------------------------------------------------ schedules
+SCHED_L, SCHED_R, SCHED_SEED, SCHED_TARGET = 128, 200_000, 1, 1e-4
+
+
+def schedule_eval(dev) -> dict:
+    """Second half of the metric: wall time of a whole anneal (beta 0 -> 1, L=128, R=2e5) with
+    the plain adaptive schedule (overlap bisection at 0.8, theta = 10) and with the learned one,
+    and each run's free-energy deviation per spin at beta = 1 from the exact finite-lattice
+    value (Kaufman's closed form, tests/golden/exact_lnZ.json)."""
+    import torch
+
+    from paper_2102_06611_gb300 import PopulationAnnealing
+    from paper_2102_06611_gb300.learned import ScheduleMLP, anneal
+    from paper_2102_06611_gb300.train_schedule import DEFAULT_WEIGHTS
+
+    with open(os.path.join(ROOT, "tests", "golden", "exact_lnZ.json")) as f:
+        exact = json.load(f)["lnZ"][str(SCHED_L)]["1.0"]
+    model = ScheduleMLP.load(DEFAULT_WEIGHTS, device=dev)
+    out = {"L": SCHED_L, "R": SCHED_R, "seed": SCHED_SEED, "target_abs_dbetaf_per_spin": SCHED_TARGET,
+           "exact_lnZ_beta1": exact}
+    for mode in ("plain", "learned"):
+        pa = PopulationAnnealing(SCHED_L, SCHED_R, SCHED_SEED, device=dev)
+        r = anneal(pa, mode, model)
+        r["abs_dbetaf_per_spin"] = abs(r["minus_betaF"] - exact) / (SCHED_L * SCHED_L)
+        r["reached_target"] = r["abs_dbetaf_per_spin"] <= SCHED_TARGET
+        out[mode] = {k: r[k] for k in ("wall_s", "steps", "sweeps", "fallbacks", "extensions",
+                                       "abs_dbetaf_per_spin", "reached_target")}
+        pa.close()
+        del pa
+        torch.cuda.empty_cache()
+    out["speedup"] = out["plain"]["wall_s"] / out["learned"]["wall_s"]
+    return out
 
 
 # ------------------------------------------------------------------------------ our arm
@@ -272,6 +307,8 @@ def run_ours(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if not args.no_schedule_eval and world == 1:
+            line["learned_schedule"] = schedule_eval(dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(L, theta)
         print(json.dumps(line), flush=True)

@@ -384,8 +384,11 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
     }
     const Accept<W> ac = make_accept<W>(a.st->T4, a.st->T8);
 
-    unsigned long long s_abs = 0, s_m2 = 0;
-    long long c0 = 0, c00 = 0, c1 = 0, c11 = 0, c01 = 0;  // levels at step start (0) and now (1)
+    // per-block exact sums: |M|, M^2, and the levels at the step start (0) and now (1):
+    // k0, k0^2, k1, k1^2, k0 k1
+    __shared__ unsigned long long sh_sum[7];
+    if (threadIdx.x < 7) sh_sum[threadIdx.x] = 0;
+    __syncthreads();
     W *spins = reinterpret_cast<W *>(a.spins);
 
     for (long long base = warp * RPW; base < R; base += nwarps * RPW) {
@@ -420,43 +423,38 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
                 if (!INIT) {
                     // level at the start of this temperature step (right after resampling),
                     // kept in level_snap by the step's first call
-                    const long long k0 = a.t0 == 0 ? a.level[j] : a.level_snap[j];
+                    const unsigned long long k0 = (unsigned long long)(a.t0 == 0 ? a.level[j] : a.level_snap[j]);
+                    const unsigned long long k1 = (unsigned long long)level;
                     if (a.t0 == 0) a.level_snap[j] = (int)k0;
-                    c0 += k0;
-                    c00 += k0 * k0;
-                    c1 += level;
-                    c11 += (long long)level * level;
-                    c01 += k0 * level;
+                    atomicAdd(&sh_sum[2], k0);
+                    atomicAdd(&sh_sum[3], k0 * k0);
+                    atomicAdd(&sh_sum[4], k1);
+                    atomicAdd(&sh_sum[5], k1 * k1);
+                    atomicAdd(&sh_sum[6], k0 * k1);
                 }
                 a.level[j] = level;
                 a.mag[j] = M;
                 if (INIT) a.fam[j] = (int)j;
                 atomicAdd(&sh_hist[level], 1);
-                s_abs += (unsigned long long)(M < 0 ? -M : M);
-                s_m2 += (unsigned long long)((long long)M * M);
+                atomicAdd(&sh_sum[0], (unsigned long long)(M < 0 ? -M : M));
+                atomicAdd(&sh_sum[1], (unsigned long long)((long long)M * M));
             }
         }
     }
 
-    // block reduction of the exact sums, then one global atomic per block
-    s_abs = group_sum<32>(s_abs);
-    s_m2 = group_sum<32>(s_m2);
-    if (lane == 0 && (s_abs | s_m2)) {
-        atomicAdd(&a.st->sum_absM, s_abs);
-        atomicAdd(&a.st->sum_M2, s_m2);
-    }
-    if (!INIT) {
-        c0 = group_sum<32>(c0);
-        c00 = group_sum<32>(c00);
-        c1 = group_sum<32>(c1);
-        c11 = group_sum<32>(c11);
-        c01 = group_sum<32>(c01);
-        if (lane == 0 && c00) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), (unsigned long long)c0);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), (unsigned long long)c00);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), (unsigned long long)c1);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), (unsigned long long)c11);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), (unsigned long long)c01);
+    // one global atomic per block and sum
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (sh_sum[0] | sh_sum[1]) {
+            atomicAdd(&a.st->sum_absM, sh_sum[0]);
+            atomicAdd(&a.st->sum_M2, sh_sum[1]);
+        }
+        if (!INIT && sh_sum[3]) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), sh_sum[2]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), sh_sum[3]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), sh_sum[4]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), sh_sum[5]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), sh_sum[6]);
         }
     }
     __syncthreads();
