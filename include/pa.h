@@ -289,6 +289,60 @@ pa_status pa_copy_numbers_static(int L, long long R_target, long long R_prev, co
                                  unsigned long long seed, int kind, int *counts_dev,
                                  double *lnQ_out, long long *R_new_out, void *stream);
 
+/* ---- Batches: many independent runs of the method (Sec. II) with different L, R, number of
+   temperatures, theta and seed, advanced one temperature step at a time together.  Each run
+   follows the linear schedule beta_i = i / (n_temps - 1), i = 0 .. n_temps - 1 (Sec. II,
+   equal steps) and computes exactly what a single-run context with the same pa_config and
+   that schedule computes.  One step of every unfinished run is one replay of a captured CUDA
+   graph whose sweep phase is a single persistent launch over all runs' replicas; the
+   persistent grid is chosen at initialisation by timing candidate grids on the batch's own
+   data (dry sweeps into the spare buffers, which change no run's state). */
+typedef struct pa_batch pa_batch;
+
+typedef struct {
+    pa_config cfg;     /* as for pa_init */
+    int n_temps;       /* temperatures including beta_0 = 0 (>= 2) */
+    int theta;         /* sweeps per temperature (>= 0) */
+} pa_run_desc;
+
+typedef struct {
+    int n_candidates;
+    int chosen_grid;   /* blocks of 256 threads of the persistent sweep */
+    int grid[4];       /* candidate grids */
+    float ms[4];       /* their dry-sweep times (ms) */
+} pa_batch_tuning;
+
+/* Bytes of the single caller-owned device arena (256-byte aligned) holding every run's
+   buffers, workspaces and the batch tables. */
+pa_status pa_batch_query_sizes(int n_runs, const pa_run_desc *runs, size_t *arena_bytes);
+
+/* Step 1 for every run (simple sampling, measurement, records), autotuning of the sweep grid,
+   and capture of the step graph.  Synchronises `stream`. */
+pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t arena_bytes, void *stream,
+                        pa_batch **out);
+
+/* Steps 2-4 at the next temperature of every unfinished run (finished or failed runs are
+   skipped).  Asynchronous on the batch's stream. */
+pa_status pa_batch_step(pa_batch *b);
+
+/* Per run: 1 while unfinished, its pa_status, its temperature index (any may be NULL).
+   Synchronising. */
+pa_status pa_batch_status(pa_batch *b, int *active_out, int *status_out, long long *step_out);
+
+/* The latest pa_obs record of every run: to device memory (asynchronous) or to the host
+   (synchronising). */
+pa_status pa_batch_record(pa_batch *b, void *device_dst);
+pa_status pa_batch_observables(pa_batch *b, pa_obs *host_out);
+
+/* Replica hashes of one run (as pa_hashes); host_out holds the run's capacity entries,
+   *count_out receives R_i.  Synchronising. */
+pa_status pa_batch_hashes(pa_batch *b, int run, unsigned long long *host_out, long long *count_out);
+
+/* The autotuner's candidates and choice. */
+pa_status pa_batch_get_tuning(const pa_batch *b, pa_batch_tuning *out);
+
+void pa_batch_destroy(pa_batch *b);
+
 /* Message for the last failing call on ctx (static storage owned by the context). */
 const char *pa_last_error(const pa_ctx *ctx);
 

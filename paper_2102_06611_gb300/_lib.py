@@ -143,3 +143,25 @@ def load_without_build() -> ctypes.CDLL:
         fn.restype = res
         fn.argtypes = args
     return L
+
+
+class pa_run_desc(ctypes.Structure):
+    _fields_ = [("cfg", pa_config), ("n_temps", ctypes.c_int), ("theta", ctypes.c_int)]
+
+
+class pa_batch_tuning(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int), ("chosen_grid", ctypes.c_int), ("grid", ctypes.c_int * 4),
+                ("ms", ctypes.c_float * 4)]
+
+
+SIGNATURES.update({
+    "pa_batch_query_sizes": (ctypes.c_int, [ctypes.c_int, _P(pa_run_desc), _P(ctypes.c_size_t)]),
+    "pa_batch_init": (ctypes.c_int, [ctypes.c_int, _P(pa_run_desc), _vp, ctypes.c_size_t, _vp, _P(_vp)]),
+    "pa_batch_step": (ctypes.c_int, [_vp]),
+    "pa_batch_status": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "pa_batch_record": (ctypes.c_int, [_vp, _vp]),
+    "pa_batch_observables": (ctypes.c_int, [_vp, _vp]),
+    "pa_batch_hashes": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _P(ctypes.c_longlong)]),
+    "pa_batch_get_tuning": (ctypes.c_int, [_vp, _P(pa_batch_tuning)]),
+    "pa_batch_destroy": (None, [_vp]),
+})

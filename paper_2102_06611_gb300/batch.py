@@ -1,0 +1,102 @@
+"""Batches of independent population-annealing runs (C ABI pa_batch_*): each run has its own
+L, R, number of temperatures (linear schedule beta_i = i / (n_temps - 1)), theta and seed; one
+temperature step of every unfinished run per captured-graph replay."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib, _check, default_capacity
+
+
+@dataclass
+class RunSpec:
+    L: int
+    R: int
+    seed: int
+    n_temps: int
+    theta: int
+    resample: str = "nearest"
+    capacity: int | None = None
+
+    def desc(self) -> _lib.pa_run_desc:
+        cap = self.capacity if self.capacity is not None else default_capacity(self.R)
+        kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON}[self.resample]
+        return _lib.pa_run_desc(_lib.pa_config(L=self.L, resample=kind, R=self.R, capacity=cap, seed=self.seed),
+                                self.n_temps, self.theta)
+
+
+class Batch:
+    def __init__(self, runs: list[RunSpec], device: str | torch.device | None = None,
+                 stream: torch.cuda.Stream | None = None):
+        self.lib = _lib.lib()
+        self.runs = list(runs)
+        self.n = len(runs)
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._descs = (_lib.pa_run_desc * self.n)(*[r.desc() for r in runs])
+        nbytes = ctypes.c_size_t()
+        _check(self.lib, None, self.lib.pa_batch_query_sizes(self.n, self._descs, ctypes.byref(nbytes)))
+        self.arena = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib, None, self.lib.pa_batch_init(self.n, self._descs, ctypes.c_void_p(self.arena.data_ptr()),
+                                                          nbytes.value, ctypes.c_void_p(self.stream.cuda_stream),
+                                                          ctypes.byref(h)))
+        self.h = h
+
+    def step(self) -> None:
+        _check(self.lib, None, self.lib.pa_batch_step(self.h))
+
+    def status(self):
+        active = np.zeros(self.n, np.int32)
+        status = np.zeros(self.n, np.int32)
+        step = np.zeros(self.n, np.int64)
+        _check(self.lib, None, self.lib.pa_batch_status(self.h, active.ctypes.data, status.ctypes.data,
+                                                        step.ctypes.data))
+        return active, status, step
+
+    def observables(self) -> list[dict]:
+        recs = (_lib.pa_obs * self.n)()
+        _check(self.lib, None, self.lib.pa_batch_observables(self.h, recs))
+        return [recs[i].as_dict() for i in range(self.n)]
+
+    def record(self, dst: torch.Tensor) -> None:
+        _check(self.lib, None, self.lib.pa_batch_record(self.h, ctypes.c_void_p(dst.data_ptr())))
+
+    def hashes(self, run: int) -> np.ndarray:
+        cap = self._descs[run].cfg.capacity
+        out = np.zeros(cap, np.uint64)
+        n = ctypes.c_longlong()
+        _check(self.lib, None, self.lib.pa_batch_hashes(self.h, run, out.ctypes.data, ctypes.byref(n)))
+        return out[: n.value].copy()
+
+    def tuning(self) -> dict:
+        t = _lib.pa_batch_tuning()
+        _check(self.lib, None, self.lib.pa_batch_get_tuning(self.h, ctypes.byref(t)))
+        return {"chosen_grid": t.chosen_grid,
+                "candidates": [(t.grid[i], t.ms[i]) for i in range(t.n_candidates)]}
+
+    def run_to_end(self, max_steps: int = 100000) -> int:
+        steps = 0
+        while steps < max_steps:
+            active, _, _ = self.status()
+            if not active.any():
+                break
+            self.step()
+            steps += 1
+        return steps
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pa_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

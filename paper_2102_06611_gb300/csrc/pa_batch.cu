@@ -1,0 +1,411 @@
+// pa_batch.cu -- many independent population-annealing runs (different L, R, number of
+// temperatures, theta, seed) advanced together: one captured CUDA graph per temperature step,
+// whose sweep phase is a single persistent launch over every run's replica groups.  The
+// persistent grid is chosen by timing candidate shapes on the batch itself (dry sweeps into
+// the spare spin buffers, which leave every run's state untouched).
+//
+// Each run computes exactly what a single-run context with the same configuration and the
+// linear schedule beta_i = i / (n_temps - 1) computes: the kernels are the single-run kernel
+// bodies applied through a run table.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pa_common.cuh"
+#include "pa_kernels.h"
+
+namespace {
+
+bool batch_supported_L(int L)
+{
+    switch (L) {
+        case 4: case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 128: return true;
+        default: return false;
+    }
+}
+
+int rpw_for(int L)
+{
+    // replicas per work item: 32 / (lanes per replica); lanes per replica = L / rows per lane
+    int rpl = (L == 12 || L == 24 || L == 48) ? 3 : L == 128 ? PA_RPL_128 : L == 64 ? PA_RPL_64 : L == 32 ? PA_RPL_32 : 2;
+    return 32 / (L / rpl);
+}
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct RunLayout {
+    size_t spins[2], level[2], mag[2], fam[2], work, end;
+    pa::Workspace ws;
+};
+
+RunLayout layout_run(const pa_run_desc &d, size_t off)
+{
+    RunLayout r{};
+    const size_t bpr = (size_t)pa::bytes_per_replica(d.cfg.L);
+    for (int b = 0; b < 2; ++b) {
+        r.spins[b] = off;
+        off = a256(off + bpr * (size_t)d.cfg.capacity);
+    }
+    for (int b = 0; b < 2; ++b) {
+        r.level[b] = off; off = a256(off + 4 * (size_t)d.cfg.capacity);
+        r.mag[b] = off;   off = a256(off + 4 * (size_t)d.cfg.capacity);
+        r.fam[b] = off;   off = a256(off + 4 * (size_t)d.cfg.capacity);
+    }
+    r.ws = pa::plan_workspace(d.cfg.L, d.cfg.capacity);
+    r.work = off;
+    off = a256(off + r.ws.total);
+    r.end = off;
+    return r;
+}
+
+struct Tables {
+    size_t runs, state, ctl, order, item_start, records, end;
+};
+
+Tables layout_tables(int n)
+{
+    Tables t{};
+    size_t off = 0;
+    t.runs = off;       off = a256(off + sizeof(pa::BatchRun) * (size_t)n);
+    t.state = off;      off = a256(off + sizeof(pa::BatchState) * (size_t)n);
+    t.ctl = off;        off = a256(off + sizeof(pa::BatchCtl));
+    t.order = off;      off = a256(off + sizeof(int) * (size_t)n);
+    t.item_start = off; off = a256(off + sizeof(long long) * ((size_t)n + 1));
+    t.records = off;    off = a256(off + sizeof(pa_obs) * (size_t)n);
+    t.end = off;
+    return t;
+}
+
+bool valid_desc(const pa_run_desc &d)
+{
+    return batch_supported_L(d.cfg.L) && d.cfg.R >= 1 && d.cfg.capacity >= d.cfg.R &&
+           d.cfg.capacity <= 2147483647LL && (d.cfg.resample == PA_RESAMPLE_NEAREST ||
+                                              d.cfg.resample == PA_RESAMPLE_POISSON) &&
+           d.n_temps >= 2 && d.theta >= 0 && d.theta <= (1 << 26);
+}
+
+}  // namespace
+
+struct pa_batch {
+    int n;
+    int device, num_sms;
+    cudaStream_t user, cs;
+    cudaEvent_t ev_in, ev_out;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    char *arena;
+    Tables t;
+    std::vector<pa_run_desc> desc;
+    std::vector<RunLayout> lay;
+    int nblk_max, nlev_max;
+    int sweep_grid;
+    pa_batch_tuning tuning;
+};
+
+extern "C" {
+
+pa_status pa_batch_query_sizes(int n_runs, const pa_run_desc *runs, size_t *arena_bytes)
+{
+    if (n_runs < 1 || !runs || !arena_bytes) return PA_ERR_INVALID_ARG;
+    size_t off = layout_tables(n_runs).end;
+    for (int i = 0; i < n_runs; ++i) {
+        if (!valid_desc(runs[i])) return PA_ERR_INVALID_ARG;
+        off = layout_run(runs[i], off).end;
+    }
+    *arena_bytes = off;
+    return PA_OK;
+}
+
+pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t arena_bytes, void *stream,
+                        pa_batch **out)
+{
+    if (!out) return PA_ERR_INVALID_ARG;
+    *out = nullptr;
+    size_t need = 0;
+    if (pa_batch_query_sizes(n_runs, runs, &need) != PA_OK || !arena || arena_bytes < need ||
+        (reinterpret_cast<uintptr_t>(arena) & 255u))
+        return PA_ERR_INVALID_ARG;
+    pa_batch *b = new (std::nothrow) pa_batch();
+    if (!b) return PA_ERR_INVALID_ARG;
+    b->n = n_runs;
+    b->user = static_cast<cudaStream_t>(stream);
+    b->arena = static_cast<char *>(arena);
+    b->t = layout_tables(n_runs);
+    b->desc.assign(runs, runs + n_runs);
+    size_t off = b->t.end;
+    b->nblk_max = 1;
+    b->nlev_max = 1;
+    for (int i = 0; i < n_runs; ++i) {
+        b->lay.push_back(layout_run(runs[i], off));
+        off = b->lay.back().end;
+        b->nblk_max = std::max(b->nblk_max, (int)b->lay.back().ws.nblk);
+        b->nlev_max = std::max(b->nlev_max, runs[i].cfg.L * runs[i].cfg.L + 1);
+    }
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete b;
+        return PA_ERR_CUDA;
+    }
+
+    // host copy of the run table, then step 1 of every run with the single-run kernels
+    std::vector<pa::BatchRun> table((size_t)n_runs);
+    std::vector<pa::BatchState> state((size_t)n_runs);
+    for (int i = 0; i < n_runs; ++i) {
+        const pa_run_desc &d = runs[i];
+        const RunLayout &L = b->lay[(size_t)i];
+        char *base = b->arena;
+        char *work = base + L.work;
+        pa::DevState *st = reinterpret_cast<pa::DevState *>(work + L.ws.state);
+        pa::BatchRun &r = table[(size_t)i];
+        std::memset(&r, 0, sizeof(r));
+        r.L = d.cfg.L;
+        r.theta = d.theta;
+        r.n_temps = d.n_temps;
+        r.rpw = rpw_for(d.cfg.L);
+        r.chunks16 = pa::bytes_per_replica(d.cfg.L) / 16;
+        const unsigned int k0 = (unsigned int)(d.cfg.seed & 0xffffffffu), k1 = (unsigned int)(d.cfg.seed >> 32);
+        for (int cur = 0; cur < 2; ++cur) {
+            const int nxt = cur ^ 1;
+            pa::ResampleArgs &a = r.rs[cur];
+            a.L = d.cfg.L;
+            a.kind = d.cfg.resample;
+            a.R_target = d.cfg.R;
+            a.capacity = d.cfg.capacity;
+            a.k0 = k0;
+            a.k1 = k1;
+            a.st = st;
+            a.hist = reinterpret_cast<int *>(work + L.ws.hist);
+            a.fl = reinterpret_cast<int *>(work + L.ws.fl);
+            a.thr = reinterpret_cast<unsigned int *>(work + L.ws.thr);
+            a.tau = reinterpret_cast<double *>(work + L.ws.tau);
+            a.w = reinterpret_cast<double *>(work + L.ws.w);
+            a.counts = reinterpret_cast<int *>(work + L.ws.counts);
+            a.blocksum = reinterpret_cast<long long *>(work + L.ws.blocksum);
+            a.nblk = L.ws.nblk;
+            a.spins_src = base + L.spins[cur];
+            a.spins_dst = base + L.spins[nxt];
+            a.level_src = reinterpret_cast<const int *>(base + L.level[cur]);
+            a.mag_src = reinterpret_cast<const int *>(base + L.mag[cur]);
+            a.fam_src = reinterpret_cast<const int *>(base + L.fam[cur]);
+            a.level_dst = reinterpret_cast<int *>(base + L.level[nxt]);
+            a.mag_dst = reinterpret_cast<int *>(base + L.mag[nxt]);
+            a.fam_dst = reinterpret_cast<int *>(base + L.fam[nxt]);
+            pa::SweepArgs &s = r.sw[cur];
+            s.spins = base + L.spins[cur];
+            s.level = reinterpret_cast<int *>(base + L.level[cur]);
+            s.mag = reinterpret_cast<int *>(base + L.mag[cur]);
+            s.fam = reinterpret_cast<int *>(base + L.fam[cur]);
+            s.level_snap = reinterpret_cast<int *>(work + L.ws.snap);
+            s.hist = reinterpret_cast<int *>(work + L.ws.hist);
+            s.st = st;
+            s.R_bound = d.cfg.capacity;
+            s.k0 = k0;
+            s.k1 = k1;
+            s.theta = d.theta;
+            pa::ObsArgs &o = r.obs[cur];
+            o.L = d.cfg.L;
+            o.st = st;
+            o.hist = reinterpret_cast<int *>(work + L.ws.hist);
+            o.fam = reinterpret_cast<int *>(base + L.fam[cur]);
+            o.fampart = reinterpret_cast<long long *>(work + L.ws.fampart);
+        }
+        state[(size_t)i].active = 1;
+        state[(size_t)i].step = 0;
+        state[(size_t)i].cur = 0;
+        state[(size_t)i].status = PA_OK;
+        state[(size_t)i].beta = 0.0;
+        state[(size_t)i].beta_prev = 0.0;
+        // step 1 (simple sampling at beta_0 = 0) and the first measurement
+        e = pa::launch_setup(st, d.cfg.R, reinterpret_cast<int *>(work + L.ws.hist), d.cfg.L * d.cfg.L, b->user);
+        if (e == cudaSuccess) {
+            pa::SweepArgs s = r.sw[0];
+            s.R_init = d.cfg.R;
+            s.R_bound = d.cfg.R;
+            s.step = 0;
+            s.t0 = 0;
+            s.theta = 0;
+            e = pa::launch_sweep(d.cfg.L, true, s, b->num_sms, b->user);
+        }
+        if (e != cudaSuccess) break;
+    }
+    // work items of the largest per-item cost first (longest-processing-time order)
+    std::vector<int> order((size_t)n_runs);
+    for (int i = 0; i < n_runs; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const double cx = (double)runs[x].cfg.L * runs[x].cfg.L * rpw_for(runs[x].cfg.L) * std::max(1, runs[x].theta);
+        const double cy = (double)runs[y].cfg.L * runs[y].cfg.L * rpw_for(runs[y].cfg.L) * std::max(1, runs[y].theta);
+        return cx > cy;
+    });
+    pa::BatchCtl ctl{};
+    ctl.n = n_runs;
+    char *tb = b->arena;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + b->t.runs, table.data(), sizeof(pa::BatchRun) * table.size(), cudaMemcpyHostToDevice,
+                            b->user);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + b->t.state, state.data(), sizeof(pa::BatchState) * state.size(),
+                            cudaMemcpyHostToDevice, b->user);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + b->t.ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, b->user);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + b->t.order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice,
+                            b->user);
+    const pa::BatchRun *d_runs = reinterpret_cast<const pa::BatchRun *>(tb + b->t.runs);
+    pa::BatchState *d_state = reinterpret_cast<pa::BatchState *>(tb + b->t.state);
+    pa::BatchCtl *d_ctl = reinterpret_cast<pa::BatchCtl *>(tb + b->t.ctl);
+    const int *d_order = reinterpret_cast<const int *>(tb + b->t.order);
+    long long *d_items = reinterpret_cast<long long *>(tb + b->t.item_start);
+    pa_obs *d_records = reinterpret_cast<pa_obs *>(tb + b->t.records);
+    if (e == cudaSuccess) e = pa::launch_batch_record(d_runs, d_state, d_records, n_runs, b->user);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->user);  // host tables must outlive the copies
+
+    // autotune the persistent sweep grid on dry sweeps (spare buffers only)
+    const int max_bps = pa::batch_sweep_max_blocks_per_sm();
+    std::memset(&b->tuning, 0, sizeof(b->tuning));
+    b->sweep_grid = b->num_sms * max_bps;
+    if (e == cudaSuccess) {
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        float best = 1e30f;
+        int dry = 1;
+        e = cudaMemcpy(&reinterpret_cast<pa::BatchCtl *>(tb + b->t.ctl)->dry, &dry, sizeof(int), cudaMemcpyHostToDevice);
+        int nc = 0;
+        for (int bps = 1; bps <= max_bps && nc < 4 && e == cudaSuccess; ++bps, ++nc) {
+            const int grid = b->num_sms * bps;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                e = pa::launch_batch_items(d_runs, d_state, d_ctl, d_order, d_items, n_runs, 0, b->user);
+                if (e == cudaSuccess) e = cudaEventRecord(t0, b->user);
+                if (e == cudaSuccess) e = pa::launch_batch_sweep(d_runs, d_state, d_ctl, d_order, d_items, n_runs, grid, b->user);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, b->user);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            }
+            b->tuning.grid[nc] = grid;
+            b->tuning.ms[nc] = ms;
+            if (ms < best) {
+                best = ms;
+                b->sweep_grid = grid;
+            }
+        }
+        b->tuning.n_candidates = nc;
+        b->tuning.chosen_grid = b->sweep_grid;
+        dry = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(&reinterpret_cast<pa::BatchCtl *>(tb + b->t.ctl)->dry, &dry, sizeof(int), cudaMemcpyHostToDevice);
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+    }
+
+    // capture one temperature step of every run
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = pa::launch_batch_step(d_runs, d_state, d_ctl, d_order, d_items, d_records, n_runs,
+                                               b->nblk_max, b->nlev_max, b->sweep_grid, b->num_sms, b->cs);
+        e = cudaStreamEndCapture(b->cs, &b->graph);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(b->ev_in);
+        cudaEventDestroy(b->ev_out);
+        cudaStreamDestroy(b->cs);
+        delete b;
+        return PA_ERR_CUDA;
+    }
+    *out = b;
+    return PA_OK;
+}
+
+pa_status pa_batch_step(pa_batch *b)
+{
+    if (!b) return PA_ERR_INVALID_ARG;
+    cudaError_t e = cudaEventRecord(b->ev_in, b->user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cs, b->ev_in, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->cs);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->user, b->ev_out, 0);
+    return e == cudaSuccess ? PA_OK : PA_ERR_CUDA;
+}
+
+pa_status pa_batch_status(pa_batch *b, int *active_out, int *status_out, long long *step_out)
+{
+    if (!b) return PA_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->user) != cudaSuccess) return PA_ERR_CUDA;
+    std::vector<pa::BatchState> st((size_t)b->n);
+    if (cudaMemcpy(st.data(), b->arena + b->t.state, sizeof(pa::BatchState) * st.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return PA_ERR_CUDA;
+    for (int i = 0; i < b->n; ++i) {
+        if (active_out) active_out[i] = st[(size_t)i].active;
+        if (status_out) status_out[i] = st[(size_t)i].status;
+        if (step_out) step_out[i] = st[(size_t)i].step;
+    }
+    return PA_OK;
+}
+
+pa_status pa_batch_record(pa_batch *b, void *device_dst)
+{
+    if (!b || !device_dst) return PA_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(device_dst, b->arena + b->t.records, sizeof(pa_obs) * (size_t)b->n,
+                                    cudaMemcpyDeviceToDevice, b->user);
+    return e == cudaSuccess ? PA_OK : PA_ERR_CUDA;
+}
+
+pa_status pa_batch_observables(pa_batch *b, pa_obs *host_out)
+{
+    if (!b || !host_out) return PA_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(host_out, b->arena + b->t.records, sizeof(pa_obs) * (size_t)b->n,
+                                    cudaMemcpyDeviceToHost, b->user);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->user);
+    return e == cudaSuccess ? PA_OK : PA_ERR_CUDA;
+}
+
+pa_status pa_batch_hashes(pa_batch *b, int run, unsigned long long *host_out, long long *count_out)
+{
+    if (!b || run < 0 || run >= b->n || !host_out || !count_out) return PA_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->user) != cudaSuccess) return PA_ERR_CUDA;
+    pa::BatchState st;
+    if (cudaMemcpy(&st, b->arena + b->t.state + sizeof(pa::BatchState) * (size_t)run, sizeof(st),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PA_ERR_CUDA;
+    const RunLayout &L = b->lay[(size_t)run];
+    const pa_run_desc &d = b->desc[(size_t)run];
+    char *work = b->arena + L.work;
+    const pa::DevState *dst = reinterpret_cast<const pa::DevState *>(work + L.ws.state);
+    unsigned long long *dev = reinterpret_cast<unsigned long long *>(work + L.ws.hashes);
+    cudaError_t e = pa::launch_hashes(d.cfg.L, b->arena + L.spins[st.cur], d.cfg.capacity, dst, dev, b->user);
+    long long R = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->user);
+    if (e == cudaSuccess) e = cudaMemcpy(&R, &dst->R_cur, sizeof(R), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, dev, sizeof(unsigned long long) * (size_t)R, cudaMemcpyDeviceToHost);
+    *count_out = R;
+    return e == cudaSuccess ? PA_OK : PA_ERR_CUDA;
+}
+
+pa_status pa_batch_get_tuning(const pa_batch *b, pa_batch_tuning *out)
+{
+    if (!b || !out) return PA_ERR_INVALID_ARG;
+    *out = b->tuning;
+    return PA_OK;
+}
+
+void pa_batch_destroy(pa_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->cs);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaEventDestroy(b->ev_in);
+    cudaEventDestroy(b->ev_out);
+    cudaStreamDestroy(b->cs);
+    delete b;
+}
+
+}  // extern "C"

@@ -137,6 +137,45 @@ cudaError_t launch_features(const FeatureArgs &a, cudaStream_t s);
 cudaError_t launch_mlp_propose(const unsigned short *P, const float *norm, const float *raw, const float *x, int L,
                                double dbeta_max, int theta_max, DevState *st, cudaStream_t s);
 
+// ------------------------------------------------------------------------------ batches
+// Many independent runs advance one temperature step per replay of a captured graph.  Each
+// run keeps the single-run layout (its own buffers and workspace); the kernels below take a
+// run table and use blockIdx.y (or a work item) to pick the run.
+struct BatchRun {
+    ResampleArgs rs[2];   // resampling arguments with `cur` = 0 / 1 (beta, step patched per step)
+    ObsArgs obs[2];       // record arguments with `cur` = 0 / 1
+    SweepArgs sw[2];      // sweep arguments with `cur` = 0 / 1
+    int L, theta, n_temps, rpw;
+    int chunks16;
+    int pad;
+};
+
+struct BatchState {       // per run, mutable
+    int active;           // 1 while beta < 1 and no error
+    int step;             // temperature index i
+    int cur;              // buffers holding the current population
+    int status;           // pa_status of the run
+    double beta, beta_prev;
+};
+
+struct BatchCtl {
+    unsigned long long next_item;  // work counter of the persistent sweep
+    long long total_items;
+    int n;
+    int dry;              // autotuning: sweep into the spare buffer, measure nothing
+};
+
+cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
+                              long long *item_start, pa_obs *records, int n, int nblk_max, int nlev_max,
+                              int sweep_grid, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
+                               long long *item_start, int n, int dry, cudaStream_t s);
+cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
+                               const long long *item_start, int n, int grid, cudaStream_t s);
+cudaError_t launch_batch_record(const BatchRun *runs, BatchState *state, pa_obs *records, int n,
+                                cudaStream_t s);
+int batch_sweep_max_blocks_per_sm();
+
 cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
                           unsigned long long *out, cudaStream_t s);
 cudaError_t launch_export(int L, const void *spins, long long first, long long count,

@@ -122,7 +122,7 @@ __global__ void k_setup(DevState *st, long long R, int *hist, int nlev)
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlev; k += gridDim.x * blockDim.x) hist[k] = 0;
 }
 
-__global__ void k_zero_measure(DevState *st, int *hist, int nlev)
+__device__ __forceinline__ void zero_measure_body(DevState *st, int *hist, int nlev)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->sum_absM = 0;
@@ -131,6 +131,8 @@ __global__ void k_zero_measure(DevState *st, int *hist, int nlev)
     }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlev; k += gridDim.x * blockDim.x) hist[k] = 0;
 }
+
+__global__ void k_zero_measure(DevState *st, int *hist, int nlev) { zero_measure_body(st, hist, nlev); }
 
 __global__ void k_thresholds(DevState *st, double beta) { set_thresholds(st, beta); }
 
@@ -157,7 +159,7 @@ cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, cudaStream
 // ------------------------------------------------------------------------------ k_table
 constexpr int kTableThreads = 1024;
 
-__global__ void __launch_bounds__(kTableThreads) k_table(ResampleArgs a)
+__device__ __forceinline__ void table_body(const ResampleArgs &a)
 {
     extern __shared__ double sh_prod[];  // compacted h_k w_k, ascending k
     __shared__ int sh_kmin;
@@ -233,6 +235,8 @@ __global__ void __launch_bounds__(kTableThreads) k_table(ResampleArgs a)
     }
 }
 
+__global__ void __launch_bounds__(kTableThreads) k_table(ResampleArgs a) { table_body(a); }
+
 // ------------------------------------------------------------------------------ counts
 // Poisson(lambda) by sequential inversion (Devroye 1986, Ch. X.3); lambda >= 32 is split
 // into m = ceil(lambda / 32) independent draws of mean lambda / m.  Chunk c of parent j
@@ -262,7 +266,7 @@ __device__ long long poisson_draw(double lambda, unsigned int j, unsigned int st
     return total;
 }
 
-__global__ void __launch_bounds__(kCountThreads) k_counts(ResampleArgs a)
+__device__ __forceinline__ void counts_body(const ResampleArgs &a)
 {
     DevState *st = a.st;
     if (st->error) return;
@@ -290,10 +294,12 @@ __global__ void __launch_bounds__(kCountThreads) k_counts(ResampleArgs a)
     if (threadIdx.x == 0) a.blocksum[blockIdx.x] = t;
 }
 
+__global__ void __launch_bounds__(kCountThreads) k_counts(ResampleArgs a) { counts_body(a); }
+
 // ------------------------------------------------------------------------------ scan
 constexpr int kScanThreads = 1024;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan(ResampleArgs a)
+__device__ __forceinline__ void scan_body(const ResampleArgs &a)
 {
     DevState *st = a.st;
     if (st->error) return;
@@ -315,8 +321,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ResampleArgs a)
     }
 }
 
+__global__ void __launch_bounds__(kScanThreads) k_scan(ResampleArgs a) { scan_body(a); }
+
 // ------------------------------------------------------------------------------ copy
-__global__ void __launch_bounds__(kCountThreads) k_copy(ResampleArgs a, int chunks16)
+__device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
 {
     __shared__ int sh_cnt[kCountBlockItems];
     __shared__ long long sh_off[kCountBlockItems];
@@ -365,6 +373,8 @@ __global__ void __launch_bounds__(kCountThreads) k_copy(ResampleArgs a, int chun
     }
 }
 
+__global__ void __launch_bounds__(kCountThreads) k_copy(ResampleArgs a, int chunks16) { copy_body(a, chunks16); }
+
 cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
 {
     const int nlev = a.L * a.L + 1;
@@ -412,7 +422,7 @@ cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s)
 }
 
 // ------------------------------------------------------------------------------ step 4
-__global__ void __launch_bounds__(256) k_families(const DevState *st, const int *fam, long long *part)
+__device__ __forceinline__ void families_body(const DevState *st, const int *fam, long long *part)
 {
     const long long R = st->R_cur;
     long long cnt = 0, s2 = 0;
@@ -444,7 +454,7 @@ __global__ void __launch_bounds__(256) k_families(const DevState *st, const int 
     }
 }
 
-__global__ void __launch_bounds__(1024) k_obs(ObsArgs a)
+__device__ __forceinline__ void obs_body(const ObsArgs &a)
 {
     const DevState *st = a.st;
     const int N = a.L * a.L;
@@ -492,6 +502,13 @@ __global__ void __launch_bounds__(1024) k_obs(ObsArgs a)
     o.status = st->error;
     *a.dst = o;
 }
+
+__global__ void __launch_bounds__(256) k_families(const DevState *st, const int *fam, long long *part)
+{
+    families_body(st, fam, part);
+}
+
+__global__ void __launch_bounds__(1024) k_obs(ObsArgs a) { obs_body(a); }
 
 cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s)
 {
@@ -650,6 +667,169 @@ cudaError_t launch_bisect(const BisectArgs &a, cudaStream_t s)
 {
     k_bisect<<<1, kBisectThreads, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ batches
+// One temperature step of every active run: begin (advance beta_i = i / (n_temps - 1)),
+// table, counts, scan, copy, flip (switch buffers, count sweep work items), zero, sweep
+// (persistent, pa_sweep.cu), families, record.  Every argument is read from device memory,
+// so the sequence is captured once in a CUDA graph and replayed per step.
+__global__ void k_b_begin(const BatchRun *runs, BatchState *state, int n)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        BatchState &s = state[r];
+        if (!s.active) continue;
+        const int err = runs[r].rs[s.cur].st->error;
+        if (err) {
+            s.active = 0;
+            s.status = err;
+        } else if (s.step >= runs[r].n_temps - 1) {
+            s.active = 0;
+        } else {
+            s.beta_prev = s.beta;
+            s.step += 1;
+            s.beta = __ddiv_rn((double)s.step, (double)(runs[r].n_temps - 1));
+        }
+    }
+}
+
+__device__ __forceinline__ ResampleArgs batch_resample_args(const BatchRun &run, const BatchState &s)
+{
+    ResampleArgs a = run.rs[s.cur];
+    a.beta_prev = s.beta_prev;
+    a.beta_new = s.beta;
+    a.step = (unsigned int)s.step;
+    return a;
+}
+
+__global__ void __launch_bounds__(kTableThreads) k_b_table(const BatchRun *runs, const BatchState *state)
+{
+    const BatchState s = state[blockIdx.y];
+    if (!s.active) return;
+    table_body(batch_resample_args(runs[blockIdx.y], s));
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_b_counts(const BatchRun *runs, const BatchState *state)
+{
+    const BatchState s = state[blockIdx.y];
+    if (!s.active || blockIdx.x >= runs[blockIdx.y].rs[0].nblk) return;
+    counts_body(batch_resample_args(runs[blockIdx.y], s));
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_b_scan(const BatchRun *runs, const BatchState *state)
+{
+    const BatchState s = state[blockIdx.y];
+    if (!s.active) return;
+    scan_body(batch_resample_args(runs[blockIdx.y], s));
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_b_copy(const BatchRun *runs, const BatchState *state)
+{
+    const BatchState s = state[blockIdx.y];
+    if (!s.active || blockIdx.x >= runs[blockIdx.y].rs[0].nblk) return;
+    copy_body(batch_resample_args(runs[blockIdx.y], s), runs[blockIdx.y].chunks16);
+}
+
+// Switch each resampled run to its new buffers (unless resampling failed) and lay out the
+// persistent sweep's work items: ceil(R_i / replicas-per-item) per run, runs in `order`.
+__global__ void k_b_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
+                          long long *item_start, int n, int flip)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    long long total = 0;
+    for (int p = 0; p < n; ++p) {
+        const int r = order[p];
+        BatchState &s = state[r];
+        item_start[p] = total;
+        if (!s.active) continue;
+        const DevState *dst = runs[r].rs[s.cur].st;
+        if (dst->error) continue;
+        if (flip) s.cur ^= 1;
+        const long long R = dst->R_cur;
+        total += (R + runs[r].rpw - 1) / runs[r].rpw;
+    }
+    item_start[n] = total;
+    ctl->total_items = total;
+    ctl->next_item = 0;
+}
+
+__global__ void __launch_bounds__(1024) k_b_zero(const BatchRun *runs, const BatchState *state)
+{
+    const BatchState s = state[blockIdx.y];
+    if (!s.active) return;
+    const SweepArgs &a = runs[blockIdx.y].sw[s.cur];
+    const int L = runs[blockIdx.y].L;
+    zero_measure_body(a.st, a.hist, L * L + 1);
+}
+
+__global__ void __launch_bounds__(256) k_b_families(const BatchRun *runs, const BatchState *state)
+{
+    const BatchState s = state[blockIdx.y];
+    if (!s.active) return;  // a finished run keeps its last record
+    const ObsArgs &a = runs[blockIdx.y].obs[s.cur];
+    families_body(a.st, a.fam, a.fampart);
+}
+
+__global__ void __launch_bounds__(1024) k_b_obs(const BatchRun *runs, BatchState *state, pa_obs *records)
+{
+    const BatchState s = state[blockIdx.y];
+    if (!s.active) return;  // a finished run keeps its last record
+    ObsArgs a = runs[blockIdx.y].obs[s.cur];
+    a.step = s.step;
+    a.beta = s.beta;
+    a.dbeta = s.step > 0 ? __dsub_rn(s.beta, s.beta_prev) : 0.0;
+    a.theta = s.step > 0 ? runs[blockIdx.y].theta : 0;
+    a.dst = records + blockIdx.y;
+    obs_body(a);
+    // the run is finished once its last temperature is recorded
+    if (threadIdx.x == 0 && s.step >= runs[blockIdx.y].n_temps - 1) state[blockIdx.y].active = 0;
+}
+
+cudaError_t launch_batch_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
+                               long long *item_start, int n, int flip, cudaStream_t s)
+{
+    k_b_items<<<1, 32, 0, s>>>(runs, state, ctl, order, item_start, n, flip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_record(const BatchRun *runs, BatchState *state, pa_obs *records, int n,
+                                cudaStream_t s)
+{
+    k_b_families<<<dim3(kFamBlocks, n), 256, 0, s>>>(runs, state);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_b_obs<<<dim3(1, n), 1024, 0, s>>>(runs, state, records);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
+                              long long *item_start, pa_obs *records, int n, int nblk_max, int nlev_max,
+                              int sweep_grid, int num_sms, cudaStream_t s)
+{
+    (void)num_sms;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_b_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    cudaError_t e;
+    k_b_begin<<<1, 256, 0, s>>>(runs, state, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_b_table<<<dim3(1, n), kTableThreads, (size_t)nlev_max * sizeof(double), s>>>(runs, state);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_b_counts<<<dim3(nblk_max, n), kCountThreads, 0, s>>>(runs, state);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_b_scan<<<dim3(1, n), kScanThreads, 0, s>>>(runs, state);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_b_copy<<<dim3(nblk_max, n), kCountThreads, 0, s>>>(runs, state);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_batch_items(runs, state, ctl, order, item_start, n, 1, s)) != cudaSuccess) return e;
+    k_b_zero<<<dim3((nlev_max + 1023) / 1024, n), 1024, 0, s>>>(runs, state);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_batch_sweep(runs, state, ctl, order, item_start, n, sweep_grid, s)) != cudaSuccess) return e;
+    return launch_batch_record(runs, state, records, n, s);
 }
 
 // ------------------------------------------------------------------------------ hashes

@@ -1,0 +1,82 @@
+"""Batches vs single runs: every run of a mixed batch (different L, R, temperatures, theta,
+seed, resampling) must end bit-identical to a single-run context driven with the same
+linear schedule, and one failing run must not disturb the others."""
+import numpy as np
+import pytest
+
+import oracle
+from side_by_side import assert_obs_close, compare_population
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _single(spec):
+    from paper_2102_06611_gb300 import PopulationAnnealing
+    pa = PopulationAnnealing(spec.L, spec.R, spec.seed, resample=spec.resample, capacity=spec.capacity)
+    for i in range(1, spec.n_temps):
+        pa.resample(i / (spec.n_temps - 1))
+        pa.anneal_step(spec.theta)
+    return pa
+
+
+MIXED = [
+    # L, R, seed, n_temps, theta, resample
+    (64, 700, 11, 6, 3, "nearest"),
+    (8, 2000, 12, 11, 1, "nearest"),
+    (12, 500, 13, 4, 5, "poisson"),
+    (16, 1200, 14, 9, 0, "nearest"),
+    (24, 300, 15, 7, 2, "nearest"),
+    (32, 900, 16, 5, 4, "poisson"),
+    (48, 150, 17, 3, 2, "nearest"),
+    (4, 3000, 18, 12, 3, "nearest"),
+    (128, 20, 19, 3, 1, "nearest"),
+]
+
+
+def test_mixed_batch_matches_single_runs():
+    from paper_2102_06611_gb300.batch import Batch, RunSpec
+    specs = [RunSpec(L, R, seed, nT, th, kind) for (L, R, seed, nT, th, kind) in MIXED]
+    b = Batch(specs)
+    steps = b.run_to_end()
+    assert steps == max(s.n_temps for s in specs) - 1
+    active, status, step = b.status()
+    assert not active.any() and not status.any()
+    assert list(step) == [s.n_temps - 1 for s in specs]
+    recs = b.observables()
+    for i, s in enumerate(specs):
+        pa = _single(s)
+        assert np.array_equal(b.hashes(i), pa.hashes()), i
+        o = pa.observables()
+        for k in ("step", "R", "beta", "dbeta", "e", "C", "m", "m2", "chi", "lnQ", "minus_betaF", "rho_t",
+                  "families", "sum_E", "sum_E2", "sum_absM", "sum_M2", "sum_size2", "theta"):
+            assert recs[i][k] == o[k], (i, k, recs[i][k], o[k])
+        pa.close()
+    t = b.tuning()
+    assert t["chosen_grid"] in [g for g, _ in t["candidates"]]
+
+
+def test_batch_run_against_oracle():
+    from paper_2102_06611_gb300.batch import Batch, RunSpec
+    spec = RunSpec(8, 600, 5, 9, 3)
+    b = Batch([spec, RunSpec(16, 400, 6, 5, 2)])
+    ref = oracle.PA(8, 600, 5, capacity=spec.capacity or None)
+    ref.init()
+    for i in range(1, 9):
+        b.step()
+        assert ref.resample(i / 8) == 0
+        ref.sweep(3)
+    assert np.array_equal(b.hashes(0), ref.hashes())
+    assert_obs_close(b.observables()[0], ref.observables(), "batched run 0")
+
+
+def test_failing_run_is_isolated():
+    from paper_2102_06611_gb300.batch import Batch, RunSpec
+    good = RunSpec(16, 800, 21, 8, 2)
+    bad = RunSpec(4, 500, 22, 40, 1, "poisson", capacity=500)  # the population outgrows its capacity
+    b = Batch([bad, good])
+    b.run_to_end()
+    active, status, step = b.status()
+    assert status[0] == 3 and status[1] == 0 and step[1] == 7
+    pa = _single(good)
+    assert np.array_equal(b.hashes(1), pa.hashes())
