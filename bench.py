@@ -58,6 +58,8 @@ def _parse_args():
     p.add_argument("--theta", type=int, default=THETA)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-schedule-eval", action="store_true")
+    p.add_argument("--workload", choices=["single", "batch"], default="single",
+                   help="single: the L=64, R=1e6 run (default); batch: 64 mixed independent runs")
     return p.parse_args()
 
 
@@ -352,10 +354,74 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_batch(args):
+    """64 independent runs (mixed L, R, temperature count, theta) to completion, batched (one
+    graph replay per temperature step) and, for comparison, the same runs one after another
+    through the single-run API."""
+    import ctypes
+
+    import torch
+
+    from paper_2102_06611_gb300 import OBS_BYTES, PopulationAnnealing, pa_obs
+    from paper_2102_06611_gb300.batch import Batch, mixed_runs
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    specs = mixed_runs()
+    n = len(specs)
+    steps = max(s.n_temps for s in specs) - 1
+    words = (OBS_BYTES + 7) // 8
+    b = Batch(specs, device=dev)
+    rec = torch.zeros((steps, n, words), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for s in range(steps):
+        b.step()
+        b.record(rec[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    recs = rec.cpu().numpy()
+    attempts = 0.0
+    for s in range(steps):
+        for r in range(n):
+            o = pa_obs.from_buffer_copy(recs[s, r].tobytes()[: ctypes.sizeof(pa_obs)])
+            if o.step == s + 1:
+                attempts += float(specs[r].L ** 2) * o.R * specs[r].theta
+    tuning = b.tuning()
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    # the same runs through the single-run API, one after another
+    ctxs = [PopulationAnnealing(sp.L, sp.R, sp.seed, device=dev) for sp in specs]
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for sp, pa in zip(specs, ctxs):
+        for i in range(1, sp.n_temps):
+            pa.resample(i / (sp.n_temps - 1))
+            pa.anneal_step(sp.theta)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = t0.elapsed_time(t1)
+    line = {"metric": METRIC + " (64 mixed runs, batched)", "value": attempts / (ms * 1e6), "unit": UNIT,
+            "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "64 independent runs: L in {8..64}, R log-uniform [1e3, 2e5], 51-301 "
+                                   "temperatures, theta in {1, 5, 10}, seeds 100-163", "runs": n},
+            "sequential_single_run": {"value": attempts / (ms_seq * 1e6), "unit": UNIT, "ms": ms_seq},
+            "gain_over_sequential": ms_seq / ms, "batch_ms": ms, "tuning": tuning,
+            "gpu_launches": 11 * steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -100,3 +100,20 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def mixed_runs(n: int = 64, seed: int = 2102, first_seed: int = 100) -> list[RunSpec]:
+    """A batch of n independent runs with L drawn from {8, 12, 16, 24, 32, 48, 64}, R
+    log-uniform in [1e3, 2e5], 51 - 301 temperatures, theta in {1, 5, 10}, nearest-integer
+    resampling, run seeds first_seed .. first_seed + n - 1 (the parameters come from a numpy
+    generator seeded with `seed`)."""
+    rng = np.random.default_rng(seed)
+    Ls = np.array([8, 12, 16, 24, 32, 48, 64])
+    out = []
+    for i in range(n):
+        L = int(rng.choice(Ls))
+        R = int(round(10 ** rng.uniform(3.0, np.log10(2e5))))
+        n_temps = int(rng.integers(51, 302))
+        theta = int(rng.choice([1, 5, 10]))
+        out.append(RunSpec(L, R, first_seed + i, n_temps, theta))
+    return out

@@ -112,6 +112,31 @@ def test_decorrelation_sums_match_oracle():
         assert c == pytest.approx(float(np.corrcoef(k0, k1)[0, 1]), abs=1e-12)
 
 
+def test_decorrelation_and_magnetisation_sums_in_the_ground_state():
+    """Deep in the ordered phase nearly every replica starts the step at level 0; the sums
+    must still count every replica (|M|, M^2 and the level sums)."""
+    from paper_2102_06611_gb300 import PopulationAnnealing
+    L, R, seed = 4, 3000, 9
+    N = L * L
+    gpu = PopulationAnnealing(L, R, seed)
+    ref = oracle.PA(L, R, seed, capacity=gpu.capacity)
+    ref.init()
+    for beta in (0.5, 1.0, 2.0, 3.0):
+        gpu.resample(beta)
+        ref.resample(beta)
+        k0 = (ref.state()[0].astype(np.int64) + 2 * N) // 4
+        gpu.anneal_step(1)
+        ref.sweep(1)
+    E1, M1, _ = ref.state()
+    k1 = (E1.astype(np.int64) + 2 * N) // 4
+    assert (k0 == 0).mean() > 0.9
+    c, sums = gpu.decorrelation(with_sums=True)
+    assert [int(x) for x in sums] == [int(k0.sum()), int((k0 * k0).sum()), int(k1.sum()), int((k1 * k1).sum()),
+                                      int((k0 * k1).sum())]
+    o = gpu.observables()
+    assert o["sum_absM"] == int(np.abs(M1).sum()) and o["sum_M2"] == int((M1.astype(np.int64) ** 2).sum())
+
+
 def test_learned_anneal_replayed_by_oracle():
     """The network's proposals go through the overlap floor; the oracle, given each proposed
     dbeta, takes the same decision and the same fallback bisection, and the populations stay
