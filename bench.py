@@ -189,7 +189,8 @@ def run_ours(args):
     K, W = args.steps, args.warmup
     assert W + K <= N_TEMPS - 1, "schedule has 300 steps"
     stream = torch.cuda.current_stream(dev)
-    pa = PopulationAnnealing(L, R, SEED + rank, device=dev, stream=stream)
+    from paper_2102_06611_gb300.multi import rank_seed
+    pa = PopulationAnnealing(L, R, rank_seed(SEED, rank), device=dev, stream=stream)
     records = torch.zeros((K, (OBS_BYTES + 7) // 8), dtype=torch.int64, device=dev)
 
     def beta(i):
@@ -261,13 +262,8 @@ def run_ours(args):
                "note": "public API per step: pa_resample(beta) + pa_anneal_step(theta) + pa_observables "
                        "(host record, synchronising); beta passes by value, no input tensor is copied"}
 
-    if world > 1:
-        t = torch.tensor([ms, sweep_ms, attempts], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:2], op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum[2:], op=dist.ReduceOp.SUM)
-        ms, sweep_ms, attempts = float(tmax[0]), float(tmax[1]), float(tsum[2])
+    from paper_2102_06611_gb300.multi import aggregate
+    ms, sweep_ms, attempts = aggregate(ms, sweep_ms, attempts, device=dev)
 
     if rank == 0:
         value = attempts / (ms * 1e6)

@@ -343,6 +343,17 @@ pa_status pa_batch_get_tuning(const pa_batch *b, pa_batch_tuning *out);
 
 void pa_batch_destroy(pa_batch *b);
 
+/* Checkpoint and resume (not a step of the method; the counter-based random numbers make
+   the population, its exact sums, the step index, the running sum of ln Q and the schedule
+   log the whole state of a run).  pa_checkpoint_size gives the bytes pa_save needs for the
+   current population; pa_save writes them to host memory; pa_load restores them into a
+   context created with the same pa_config, after which the run continues exactly as the
+   uninterrupted one.  All synchronising; PA_ERR_INVALID_ARG for a short buffer, a foreign or
+   truncated checkpoint, or a different configuration. */
+pa_status pa_checkpoint_size(pa_ctx *ctx, size_t *bytes);
+pa_status pa_save(pa_ctx *ctx, void *host_buf, size_t n);
+pa_status pa_load(pa_ctx *ctx, const void *host_buf, size_t n);
+
 /* Message for the last failing call on ctx (static storage owned by the context). */
 const char *pa_last_error(const pa_ctx *ctx);
 

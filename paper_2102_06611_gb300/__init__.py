@@ -172,6 +172,19 @@ class PopulationAnnealing:
         _check(self.lib, self.ctx, self.lib.pa_export_spins(self.ctx, int(first), int(count), out.ctypes.data))
         return out
 
+    def save(self) -> bytes:
+        """Checkpoint of the whole run state (host bytes)."""
+        n = ctypes.c_size_t()
+        _check(self.lib, self.ctx, self.lib.pa_checkpoint_size(self.ctx, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.lib, self.ctx, self.lib.pa_save(self.ctx, buf, n.value))
+        return buf.raw
+
+    def load(self, data: bytes) -> None:
+        """Restore a checkpoint written by save() for the same configuration."""
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(self.lib, self.ctx, self.lib.pa_load(self.ctx, buf, len(data)))
+
     def close(self) -> None:
         if getattr(self, "ctx", None):
             self.lib.pa_destroy(self.ctx)

@@ -165,3 +165,9 @@ SIGNATURES.update({
     "pa_batch_get_tuning": (ctypes.c_int, [_vp, _P(pa_batch_tuning)]),
     "pa_batch_destroy": (None, [_vp]),
 })
+
+SIGNATURES.update({
+    "pa_checkpoint_size": (ctypes.c_int, [_vp, _P(ctypes.c_size_t)]),
+    "pa_save": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "pa_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+})

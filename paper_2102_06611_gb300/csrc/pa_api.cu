@@ -595,6 +595,140 @@ pa_status pa_export_spins(pa_ctx *c, long long first, long long count, unsigned 
     return PA_OK;
 }
 
+// ------------------------------------------------------------------------------ checkpoints
+// Layout: header, device state block, level histogram, then per replica of the current
+// population the packed spins, level, magnetisation, family id and step-start level, then the
+// R_{i-1} copy numbers of the last resampling, then the schedule log.  The random numbers are
+// counter based, so this is the whole state of a run.
+namespace {
+constexpr unsigned long long kCkptMagic = 0x3131363630323150ull;  // "P2066611" tag
+struct CkptHeader {
+    unsigned long long magic;
+    pa_config cfg;
+    long long step, R_cur, R_prev, n_log;
+    double beta, dbeta;
+    int sweeps_in_step, theta_last, measured, version;
+};
+
+size_t ckpt_bytes(const pa_ctx *c, long long R, long long Rp, long long nlog)
+{
+    const size_t bpr = (size_t)pa::bytes_per_replica(c->cfg.L);
+    return sizeof(CkptHeader) + sizeof(pa::DevState) + sizeof(int) * (size_t)(c->N + 1) +
+           (size_t)R * (bpr + 4 * sizeof(int)) + (size_t)Rp * sizeof(int) + (size_t)nlog * sizeof(pa_sched_entry);
+}
+
+pa_status read_sizes(pa_ctx *c, long long *R, long long *Rp)
+{
+    pa_status s = sync_and_check(c);
+    if (s != PA_OK) return s;
+    cudaError_t e = cudaMemcpy(R, &c->st->R_cur, sizeof(*R), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(Rp, &c->st->R_prev, sizeof(*Rp), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PA_OK : cuda_fail(c, e, "checkpoint sizes");
+}
+}  // namespace
+
+pa_status pa_checkpoint_size(pa_ctx *c, size_t *bytes)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!bytes) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    long long R, Rp;
+    if ((s = read_sizes(c, &R, &Rp)) != PA_OK) return s;
+    *bytes = ckpt_bytes(c, R, Rp, (long long)c->log.size());
+    return PA_OK;
+}
+
+pa_status pa_save(pa_ctx *c, void *host_buf, size_t n)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!host_buf) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    long long R, Rp;
+    if ((s = read_sizes(c, &R, &Rp)) != PA_OK) return s;
+    if (n < ckpt_bytes(c, R, Rp, (long long)c->log.size()))
+        return fail(c, PA_ERR_INVALID_ARG, "checkpoint buffer of %zu bytes is too small", n);
+    char *p = static_cast<char *>(host_buf);
+    CkptHeader h{};
+    h.magic = kCkptMagic;
+    h.version = 1;
+    h.cfg = c->cfg;
+    h.step = c->step;
+    h.R_cur = R;
+    h.R_prev = Rp;
+    h.n_log = (long long)c->log.size();
+    h.beta = c->beta;
+    h.dbeta = c->dbeta;
+    h.sweeps_in_step = c->sweeps_in_step;
+    h.theta_last = c->theta_last;
+    h.measured = c->measured ? 1 : 0;
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const size_t bpr = (size_t)pa::bytes_per_replica(c->cfg.L);
+    struct Piece { const void *src; size_t bytes; } pieces[] = {
+        {c->st, sizeof(pa::DevState)},
+        {at<int>(c, c->ws.hist), sizeof(int) * (size_t)(c->N + 1)},
+        {c->buf.spins[c->cur], bpr * (size_t)R},
+        {c->buf.level[c->cur], sizeof(int) * (size_t)R},
+        {c->buf.mag[c->cur], sizeof(int) * (size_t)R},
+        {c->buf.fam[c->cur], sizeof(int) * (size_t)R},
+        {at<int>(c, c->ws.snap), sizeof(int) * (size_t)R},
+        {at<int>(c, c->ws.counts), sizeof(int) * (size_t)Rp},
+    };
+    for (const Piece &q : pieces) {
+        cudaError_t e = cudaMemcpy(p, q.src, q.bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
+        p += q.bytes;
+    }
+    if (!c->log.empty()) std::memcpy(p, c->log.data(), sizeof(pa_sched_entry) * c->log.size());
+    return PA_OK;
+}
+
+pa_status pa_load(pa_ctx *c, const void *host_buf, size_t n)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!host_buf || n < sizeof(CkptHeader)) return PA_ERR_INVALID_ARG;
+    CkptHeader h;
+    std::memcpy(&h, host_buf, sizeof(h));
+    if (h.magic != kCkptMagic || h.version != 1) return fail(c, PA_ERR_INVALID_ARG, "not a checkpoint");
+    if (std::memcmp(&h.cfg, &c->cfg, sizeof(pa_config)) != 0)
+        return fail(c, PA_ERR_INVALID_ARG, "checkpoint of a different configuration");
+    if (h.R_cur < 1 || h.R_cur > c->cfg.capacity || h.R_prev < 0 || h.R_prev > c->cfg.capacity || h.n_log < 0 ||
+        n < ckpt_bytes(c, h.R_cur, h.R_prev, h.n_log))
+        return fail(c, PA_ERR_INVALID_ARG, "truncated or inconsistent checkpoint");
+    DeviceGuard g(c->device);
+    if ((s = sync_and_check(c)) != PA_OK) return s;
+    const char *p = static_cast<const char *>(host_buf) + sizeof(h);
+    c->cur = 0;
+    const size_t bpr = (size_t)pa::bytes_per_replica(c->cfg.L);
+    struct Piece { void *dst; size_t bytes; } pieces[] = {
+        {c->st, sizeof(pa::DevState)},
+        {at<int>(c, c->ws.hist), sizeof(int) * (size_t)(c->N + 1)},
+        {c->buf.spins[0], bpr * (size_t)h.R_cur},
+        {c->buf.level[0], sizeof(int) * (size_t)h.R_cur},
+        {c->buf.mag[0], sizeof(int) * (size_t)h.R_cur},
+        {c->buf.fam[0], sizeof(int) * (size_t)h.R_cur},
+        {at<int>(c, c->ws.snap), sizeof(int) * (size_t)h.R_cur},
+        {at<int>(c, c->ws.counts), sizeof(int) * (size_t)h.R_prev},
+    };
+    for (const Piece &q : pieces) {
+        cudaError_t e = cudaMemcpy(q.dst, p, q.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint restore");
+        p += q.bytes;
+    }
+    c->log.assign(reinterpret_cast<const pa_sched_entry *>(p), reinterpret_cast<const pa_sched_entry *>(p) + h.n_log);
+    c->step = h.step;
+    c->beta = h.beta;
+    c->dbeta = h.dbeta;
+    c->sweeps_in_step = h.sweeps_in_step;
+    c->theta_last = h.theta_last;
+    c->measured = h.measured != 0;
+    c->prop_valid = false;
+    return PA_OK;
+}
+
 const char *pa_last_error(const pa_ctx *c)
 {
     if (!c) return "null context";
