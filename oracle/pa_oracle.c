@@ -218,10 +218,11 @@ void orc_init_replica(int L, uint64_t seed, uint32_t j, int8_t *s)
  * The uniform x of site (r, c) of colour q in sweep t of step i, replica slot j, is built
  * from two independent parts (every bit is an independent uniform bit, so x is uniform on
  * [0, 2^32)).  Let p = c / 2 (index of the site among the L/2 colour-q sites of row r),
- * h = p / 32, b = p mod 32, nh = ceil(L / 64) (32-bit chunks per half-row), tag =
- * (2t + q):
+ * H' = the smallest power of two >= L/2, n = r H' + p (the colour-q sites numbered row
+ * after row, each row padded to H'), chunk = n / 32, b = n mod 32, tag = (2t + q).  For
+ * L >= 64 a chunk is 32 sites of one row; for smaller L it spans 32 / H' rows:
  *   top 8 bits:   bit (31 - k) of x, k = 0..7, is bit b of word (k mod 4) of
- *                 Philox(ctr = (2 (nh r + h) + k / 4, j, (SWEEP << 28) | tag, i));
+ *                 Philox(ctr = (2 chunk + k / 4, j, (SWEEP << 28) | tag, i));
  *   low 24 bits:  the low 24 bits of word 0 of
  *                 Philox(ctr = (64 r + p, j, (REFINE << 28) | tag, i)).
  * ---------------------------------------------------------------------------------- */
@@ -229,12 +230,14 @@ enum { STREAM_REFINE = 4 };
 
 uint32_t orc_sweep_uniform(int L, uint64_t seed, uint32_t step, uint32_t slot, int tag, int r, int p)
 {
-    int nh = (L + 63) / 64;
-    int h = p / 32, b = p % 32;
+    int hp = 1;
+    while (hp < L / 2) hp *= 2;
+    uint32_t n = (uint32_t)(r * hp + p);
+    uint32_t chunk = n / 32, b = n % 32;
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t planes[8];
     for (int call = 0; call < 2; ++call) {
-        uint32_t ctr[4] = {(uint32_t)(2 * (nh * r + h) + call), slot,
+        uint32_t ctr[4] = {2 * chunk + (uint32_t)call, slot,
                            ((uint32_t)STREAM_SWEEP << 28) | (uint32_t)tag, step};
         orc_philox4x32_10(ctr, key, planes + 4 * call);
     }

@@ -28,8 +28,7 @@ bool batch_supported_L(int L)
 int rpw_for(int L)
 {
     // replicas per work item: 32 / (lanes per replica); lanes per replica = L / rows per lane
-    int rpl = (L == 12 || L == 24 || L == 48) ? 3 : L == 128 ? PA_RPL_128 : L == 64 ? PA_RPL_64 : L == 32 ? PA_RPL_32 : 2;
-    return 32 / (L / rpl);
+    return 32 / (L / pa::rows_per_lane(L));
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }

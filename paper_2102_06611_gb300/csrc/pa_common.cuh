@@ -10,8 +10,11 @@
 
 // Rows of a replica held by one lane in the sweep kernel (tuning knobs; lanes per replica =
 // L / rows, a power of two <= 32).
+#ifndef PA_RPL_16
+#define PA_RPL_16 8
+#endif
 #ifndef PA_RPL_32
-#define PA_RPL_32 4
+#define PA_RPL_32 8
 #endif
 #ifndef PA_RPL_64
 #define PA_RPL_64 4
@@ -32,7 +35,26 @@ namespace pa {
 // half (r + q) mod 2 of that row, so one colour of one row is one whole word.
 //
 // A replica is handled by G lanes of a warp; lane g holds rows g*RPL .. g*RPL + RPL - 1.
+//
+// Random bit planes of the Metropolis test come per 32-site chunk of one colour: the sites
+// of colour q are numbered n = r H' + p (p = c / 2, rows padded to H', the smallest power of
+// two >= H) and chunk n / 32 holds bit n mod 32.  For L >= 48 a chunk lies within one row;
+// for smaller L it spans P = 32 / H' rows (all L rows when L = 4), and the sweep kernel
+// packs the P rows of a chunk into one register word ("packed" sizes).
 // ------------------------------------------------------------------------------------
+__host__ __device__ constexpr int rows_per_lane(int L)
+{
+    return L == 4 ? 4 : L == 8 ? 8 : L == 12 ? 12 : L == 16 ? PA_RPL_16 : L == 24 ? 6 : L == 32 ? PA_RPL_32
+           : L == 48 ? 3 : L == 64 ? PA_RPL_64 : PA_RPL_128;
+}
+
+__host__ __device__ constexpr int padded_half(int L)
+{
+    int h = 1;
+    while (h < L / 2) h *= 2;
+    return h;
+}
+
 template <int L_>
 struct Geo {
     static constexpr int L = L_;
@@ -40,18 +62,20 @@ struct Geo {
     static constexpr int H = L / 2;                      // sites per half-row
     static constexpr bool WIDE = (H > 32);
     using W = typename std::conditional<WIDE, unsigned long long, unsigned int>::type;
-    static constexpr int RPL = (L == 12 || L == 24 || L == 48) ? 3
-                               : L == 128                     ? PA_RPL_128
-                               : L == 64                      ? PA_RPL_64
-                               : L == 32                      ? PA_RPL_32
-                                                              : 2;
+    static constexpr int RPL = rows_per_lane(L);
     static constexpr int G = L / RPL;                    // lanes per replica (power of 2)
     static constexpr int RPW = 32 / G;                   // replicas per warp
     static constexpr int WORD_BYTES = WIDE ? 8 : 4;
     static constexpr int BYTES = L * 2 * WORD_BYTES;     // bytes per replica
     static constexpr int LANE_WORDS = 2 * RPL;           // half-row words held per lane
+    static constexpr int HP = padded_half(L);            // H' (row pitch of the chunk numbering)
+    static constexpr bool PACK = HP < 32;                // chunks span several rows
+    static constexpr int P = PACK ? (32 / HP < L ? 32 / HP : L) : 1;  // rows per chunk
+    static constexpr int CB = P * HP;                    // bits of a packed chunk word (32, or 8 at L = 4)
+    static constexpr int C = RPL / P;                    // packed chunks per lane
     static_assert(L % RPL == 0, "rows per lane must divide L");
-    static_assert((G & (G - 1)) == 0 && G <= 32 && G >= 2, "lanes per replica");
+    static_assert((G & (G - 1)) == 0 && G <= 32 && G >= 1, "lanes per replica");
+    static_assert(!PACK || (RPL % P == 0 && P % 2 == 0 && RPL % 2 == 0), "whole chunks of even rows per lane");
 };
 
 __host__ __device__ constexpr int bytes_per_replica(int L) { return L * 2 * (L / 2 > 32 ? 8 : 4); }

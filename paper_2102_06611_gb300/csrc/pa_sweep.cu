@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
         rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
         rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
     }
-    const Accept<W> ac = make_accept<W>(a.st->T4, a.st->T8);
+    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
 
     // per-block exact sums: |M|, M^2, and the levels at the step start (0) and now (1):
     // k0, k0^2, k1, k1^2, k0 k1
@@ -53,20 +53,18 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
                 for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
             }
         }
-#pragma unroll 1
-        for (int t = 0; t < a.theta; ++t) {
-            const unsigned int tag0 = (unsigned int)(2 * (a.t0 + t));
-            half_sweep<L, 0>(A, B, r0, lane, (unsigned int)j, tag0, a.step, rk0, rk1, a.k0, a.k1, ac);
-            half_sweep<L, 1>(A, B, r0, lane, (unsigned int)j, tag0 | 1u, a.step, rk0, rk1, a.k0, a.k1, ac);
-        }
+        sweep_rows<L>(A, B, r0, lane, (unsigned int)j, a.t0, a.theta, a.step, rk0, rk1, a.k0, a.k1, ac);
         int anti, ups;
         measure_rows<L>(A, B, r0, lane, anti, ups);
         anti = group_sum<G>(anti);
         ups = group_sum<G>(ups);
+        // exact sums of this group of replicas: |M|, M^2, k0, k0^2, k1, k1^2, k0 k1
+        unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
+        int level = -1;
         if (active) {
             if (INIT || a.theta > 0) store_rows<L>(rep, r0, A, B);
             if (q == 0) {
-                const int level = anti >> 1;
+                level = anti >> 1;
                 const int M = 2 * ups - N;
                 if (!INIT) {
                     // level at the start of this temperature step (right after resampling),
@@ -74,19 +72,35 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
                     const unsigned long long k0 = (unsigned long long)(a.t0 == 0 ? a.level[j] : a.level_snap[j]);
                     const unsigned long long k1 = (unsigned long long)level;
                     if (a.t0 == 0) a.level_snap[j] = (int)k0;
-                    atomicAdd(&sh_sum[2], k0);
-                    atomicAdd(&sh_sum[3], k0 * k0);
-                    atomicAdd(&sh_sum[4], k1);
-                    atomicAdd(&sh_sum[5], k1 * k1);
-                    atomicAdd(&sh_sum[6], k0 * k1);
+                    v[2] = k0;
+                    v[3] = k0 * k0;
+                    v[4] = k1;
+                    v[5] = k1 * k1;
+                    v[6] = k0 * k1;
                 }
                 a.level[j] = level;
                 a.mag[j] = M;
                 if (INIT) a.fam[j] = (int)j;
-                atomicAdd(&sh_hist[level], 1);
-                atomicAdd(&sh_sum[0], (unsigned long long)(M < 0 ? -M : M));
-                atomicAdd(&sh_sum[1], (unsigned long long)((long long)M * M));
+                v[0] = (unsigned long long)(M < 0 ? -M : M);
+                v[1] = (unsigned long long)((long long)M * M);
             }
+        }
+        constexpr int NSUM = INIT ? 2 : 7;
+        if constexpr (RPW >= 8) {
+            // many replicas per warp: reduce over the warp first, and count equal levels once
+            const unsigned int grp = __match_any_sync(0xffffffffu, level);
+            if (level >= 0 && lane == __ffs((int)grp) - 1) atomicAdd(&sh_hist[level], __popc(grp));
+#pragma unroll
+            for (int i = 0; i < NSUM; ++i)
+#pragma unroll
+                for (int o = 16; o >= G; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+            if (lane == 0)
+#pragma unroll
+                for (int i = 0; i < NSUM; ++i) atomicAdd(&sh_sum[i], v[i]);
+        } else if (level >= 0) {
+            atomicAdd(&sh_hist[level], 1);
+#pragma unroll
+            for (int i = 0; i < NSUM; ++i) atomicAdd(&sh_sum[i], v[i]);
         }
     }
 
@@ -179,7 +193,7 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
         rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
         rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
     }
-    const Accept<W> ac = make_accept<W>(a.st->T4, a.st->T8);
+    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
     W A[RPL], B[RPL];
     W *rep = reinterpret_cast<W *>(a.spins) + (size_t)(active ? j : 0) * (2 * L);
     if (active) load_rows<L>(rep, r0, A, B);
@@ -187,12 +201,7 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
 #pragma unroll
         for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
     }
-#pragma unroll 1
-    for (int t = 0; t < a.theta; ++t) {
-        const unsigned int tag0 = (unsigned int)(2 * t);
-        half_sweep<L, 0>(A, B, r0, lane, (unsigned int)j, tag0, a.step, rk0, rk1, a.k0, a.k1, ac);
-        half_sweep<L, 1>(A, B, r0, lane, (unsigned int)j, tag0 | 1u, a.step, rk0, rk1, a.k0, a.k1, ac);
-    }
+    sweep_rows<L>(A, B, r0, lane, (unsigned int)j, 0, a.theta, a.step, rk0, rk1, a.k0, a.k1, ac);
     int anti, ups;
     measure_rows<L>(A, B, r0, lane, anti, ups);
     anti = group_sum<G>(anti);

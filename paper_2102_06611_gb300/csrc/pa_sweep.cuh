@@ -6,7 +6,7 @@
 // two half-row words per row), so all theta sweeps run without touching memory: a replica
 // is read once and written once per call.  Neighbouring rows owned by other lanes come in
 // through warp shuffles.  The update of one colour of one row is bit-sliced over the whole
-// half-row word: aligned-neighbour classes come from XNORs of the four neighbour words, and
+// half-row word: aligned-neighbour classes come from XORs with the four neighbour words, and
 // only the acceptance bits need per-site random numbers.
 //
 // Metropolis rule (Sec. IV, acceptance min[1, exp(-beta dE)], dE = 4a - 8 for a aligned
@@ -24,6 +24,9 @@
 // registers at 65536 / (256 * n)).
 #ifndef PA_SWEEP_MIN_BLOCKS
 #define PA_SWEEP_MIN_BLOCKS 2
+#endif
+#ifndef PA_PREFETCH_MAX_C
+#define PA_PREFETCH_MAX_C 3
 #endif
 
 namespace pa {
@@ -186,9 +189,26 @@ __device__ __forceinline__ void init_rows(unsigned int slot, int r0, unsigned in
     }
 }
 
-// Per-launch constants of the acceptance test.  T = floor(e^{-4 beta} 2^32) (class a = 3)
-// or floor(e^{-8 beta} 2^32) (class a = 4), T in [0, 2^32]: m[k] = all ones iff bit 31 - k of
-// T is set (top 8 bits as bit-plane masks), low = T mod 2^24, alw = all ones iff T = 2^32.
+// ------------------------------------------------------------------------------------
+// The Metropolis test on one 32-site word.
+//
+// Neighbour classes: a site with a aligned neighbours flips always for a <= 2, with the
+// class-3 threshold T4 for a = 3 and with T8 for a = 4.  Two equivalent Boolean
+// formulations are used, chosen per lattice size because nvcc turns them into code of
+// different speed depending on the word layout (measured): XNOR masks of the four
+// neighbours with an explicit always-accept mask for T = 2^32, or pair masks (any / exactly
+// one antiparallel per pair of neighbours) with T = 2^32 folded into the threshold.
+// ------------------------------------------------------------------------------------
+template <int L>
+struct SweepStyle {
+    static constexpr bool XNOR = (L == 24 || L == 32 || L == 48 || L == 64);
+};
+
+// Per-launch constants.  T = floor(e^{-4 beta} 2^32) (class a = 3) or floor(e^{-8 beta} 2^32)
+// (a = 4), T in [0, 2^32], split as T = top 2^24 + low: m[k] = all ones iff bit 7 - k of top
+// is set (k = 0 most significant).  T = 2^32 (beta = 0) is either the always-accept mask alw
+// (XNOR style, top = low = 0) or top = 255, low = 2^24 (x < 2^32 holds, and so does the
+// split test: x_top < 255, or x_top = 255 and x_low < 2^24).
 template <typename W>
 struct Accept {
     W m4[8], m8[8];
@@ -196,30 +216,84 @@ struct Accept {
     unsigned int low4, low8;
 };
 
-template <typename W>
-__device__ __forceinline__ Accept<W> make_accept(unsigned long long T4, unsigned long long T8)
+template <int L>
+__device__ __forceinline__ Accept<typename Geo<L>::W> make_accept(unsigned long long T4, unsigned long long T8)
 {
+    using W = typename Geo<L>::W;
     Accept<W> c;
     const bool all4 = T4 >= (1ull << 32), all8 = T8 >= (1ull << 32);
-    const unsigned int t4 = all4 ? 0u : (unsigned int)T4, t8 = all8 ? 0u : (unsigned int)T8;
+    unsigned int top4, top8;
+    if constexpr (SweepStyle<L>::XNOR) {
+        const unsigned int t4 = all4 ? 0u : (unsigned int)T4, t8 = all8 ? 0u : (unsigned int)T8;
+        top4 = t4 >> 24;
+        top8 = t8 >> 24;
+        c.low4 = t4 & 0xFFFFFFu;
+        c.low8 = t8 & 0xFFFFFFu;
+        c.alw4 = all4 ? ~W(0) : W(0);
+        c.alw8 = all8 ? ~W(0) : W(0);
+    } else {
+        top4 = all4 ? 255u : (unsigned int)(T4 >> 24);
+        top8 = all8 ? 255u : (unsigned int)(T8 >> 24);
+        c.low4 = all4 ? (1u << 24) : (unsigned int)(T4 & 0xFFFFFFu);
+        c.low8 = all8 ? (1u << 24) : (unsigned int)(T8 & 0xFFFFFFu);
+        c.alw4 = W(0);
+        c.alw8 = W(0);
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        c.m4[k] = ((t4 >> (31 - k)) & 1u) ? ~W(0) : W(0);
-        c.m8[k] = ((t8 >> (31 - k)) & 1u) ? ~W(0) : W(0);
+        c.m4[k] = ((top4 >> (7 - k)) & 1u) ? ~W(0) : W(0);
+        c.m8[k] = ((top8 >> (7 - k)) & 1u) ? ~W(0) : W(0);
     }
-    c.alw4 = all4 ? ~W(0) : W(0);
-    c.alw8 = all8 ? ~W(0) : W(0);
-    c.low4 = t4 & 0xFFFFFFu;
-    c.low8 = t8 & 0xFFFFFFu;
     return c;
 }
 
-// One colour (compile-time Q) of one sweep over the rows a lane holds.
+// Classes of the sites of word s with neighbour words up, dn, ha, hb (bits outside `valid`
+// are cleared): all4 = four aligned neighbours, eq3 = exactly three, ge3 = all4 | eq3.
+template <bool XNOR, typename W>
+__device__ __forceinline__ void classify(W s, W up, W dn, W ha, W hb, W valid, W &all4, W &eq3, W &ge3)
+{
+    if constexpr (XNOR) {
+        const W x1 = ~(s ^ up), x2 = ~(s ^ dn), x3 = ~(s ^ ha), x4 = ~(s ^ hb);
+        all4 = x1 & x2 & x3 & x4 & valid;
+        ge3 = ((x1 & x2 & (x3 | x4)) | (x3 & x4 & (x1 | x2))) & valid;
+        eq3 = ge3 & ~all4;
+    } else {
+        // with y_n = s ^ n (antiparallel): z = y_1 | y_2 (any of the pair) and
+        // x = y_1 ^ y_2 = n_1 ^ n_2 (exactly one of the pair)
+        const W z12 = (s ^ up) | (s ^ dn), x12 = up ^ dn;
+        const W z34 = (s ^ ha) | (s ^ hb), x34 = ha ^ hb;
+        all4 = ~(z12 | z34) & valid;
+        eq3 = ((x12 & ~z34) | (x34 & ~z12)) & valid;
+        ge3 = all4 | eq3;
+    }
+}
+
+// x_top < T_top for every site of classes a = 3, 4 from the 8 bit planes, as a borrow chain
+// from the least significant plane (borrow = majority of ~x_k, t_k and the incoming borrow):
+// lt = decided accepts, eq = ties x_top = T_top (decided by the low 24 bits).
+template <bool XNOR, typename W>
+__device__ __forceinline__ void compare_planes(const W *plane, W all4, W eq3, W ge3, const Accept<W> &ac, W &lt,
+                                               W &eq)
+{
+    W dec = 0;
+    if constexpr (XNOR) dec = (eq3 & ac.alw4) | (all4 & ac.alw8);
+    W l = 0, e = XNOR ? (ge3 & ~dec) : ge3;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        const W tm = (all4 & ac.m8[k]) | (~all4 & ac.m4[k]);  // threshold bit of each site
+        const W np = ~plane[k];
+        l = (np & tm) | (np & l) | (tm & l);
+        e &= ~(plane[k] ^ tm);
+    }
+    lt = XNOR ? (l | dec) : l;
+    eq = e;
+}
+
+// One colour (compile-time Q) of one sweep over the rows a lane holds (sizes L >= 48).
 //
-// Acceptance x < T is decided bit-serially over the 32 sites of a word at once: the top 8
-// bits of every site's uniform x are 8 bit planes (bit j of plane k is bit 31 - k of site j's
-// x), compared most significant first against the class threshold's bits; a site stays
-// undecided only while its bits equal the threshold's, which after 8 planes happens with
+// Acceptance x < T is decided over the 32 sites of a word at once: the top 8 bits of every
+// site's uniform x are 8 bit planes (bit j of plane k is bit 31 - k of site j's x); a site
+// stays undecided only if its top bits equal the threshold's, which happens with
 // probability 2^-8, and only then is its low 24-bit part drawn.  Plane k of row r is word
 // k mod 4 of Philox(ctr = (2 (nh r + h) + k / 4, slot, SWEEP << 28 | tag, i)) for the 32-site
 // chunk h of the half-row (nh = chunks per half-row); the low part of site j is the low 24
@@ -235,6 +309,7 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
     using W = typename Gm::W;
     constexpr int RPL = Gm::RPL, G = Gm::G, H = Gm::H;
     constexpr int NH = Gm::WIDE ? 2 : 1;  // 32-site chunks per half-row
+    constexpr bool XNOR = SweepStyle<L>::XNOR;
     W *T = (Q == 0) ? A : B;          // words updated by this colour
     const W *O = (Q == 0) ? B : A;    // the other half of each row (read only here)
 
@@ -251,17 +326,13 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
         const int r = r0 + i;
-        const W s = T[i];
         const W up = (i == 0) ? from_up : O[i - 1];
         const W dn = (i == RPL - 1) ? from_down : O[i + 1];
-        const W h_a = O[i];
         // the updated half is the even-column half iff (r + Q) is even
         const bool even_half = ((r + Q) & 1) == 0;
-        const W h_b = even_half ? rot_up<W, H>(O[i]) : rot_down<W, H>(O[i]);
-        const W x1 = ~(s ^ up), x2 = ~(s ^ dn), x3 = ~(s ^ h_a), x4 = ~(s ^ h_b);
-        const W all4 = x1 & x2 & x3 & x4 & half_mask<W, H>();
-        const W ge3 = ((x1 & x2 & (x3 | x4)) | (x3 & x4 & (x1 | x2))) & half_mask<W, H>();
-        const W eq3 = ge3 & ~all4;
+        const W hb = even_half ? rot_up<W, H>(O[i]) : rot_down<W, H>(O[i]);
+        W all4, eq3, ge3;
+        classify<XNOR>(T[i], up, dn, O[i], hb, half_mask<W, H>(), all4, eq3, ge3);
 
         // bit planes of the top 8 bits of every site's uniform
         W plane[8];
@@ -280,16 +351,7 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
 #pragma unroll
             for (int k = 0; k < 8; ++k) plane[k] = (W)lo[k] | ((W)hi[k] << 32);
         }
-        W l = (eq3 & ac.alw4) | (all4 & ac.alw8);   // decided: x < T
-        W e = (eq3 & ~ac.alw4) | (all4 & ~ac.alw8); // undecided: top bits equal so far
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const W tm = (eq3 & ac.m4[k]) | (all4 & ac.m8[k]);  // threshold bit of each site
-            l |= e & ~plane[k] & tm;
-            e &= ~(plane[k] ^ tm);
-        }
-        lt[i] = l;
-        eq[i] = e;
+        compare_planes<XNOR>(plane, all4, eq3, ge3, ac, lt[i], eq[i]);
         a4[i] = all4;
         g3[i] = ge3;
     }
@@ -327,6 +389,229 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
     }
 #pragma unroll
     for (int i = 0; i < RPL; ++i) T[i] ^= (~g3[i] | lt[i]) & half_mask<W, H>();
+}
+
+// ------------------------------------------------------------------------------------
+// Packed sizes (L < 48): the P rows of one chunk are one register word, field i (bits
+// i H' .. i H' + H - 1) = row (first row of the chunk + i).  PA[c] packs the colour-0 words
+// A_r of chunk c, PB[c] the colour-1 words B_r.  The first row of every chunk is even.
+// ------------------------------------------------------------------------------------
+template <int L>
+struct PackMasks {
+    using Gm = Geo<L>;
+    static constexpr unsigned int field(int i, unsigned int bits) { return bits << (i * Gm::HP); }
+    static constexpr unsigned int rep(unsigned int bits, int parity)  // parity -1: every field
+    {
+        unsigned int m = 0;
+        for (int i = 0; i < Gm::P; ++i)
+            if (parity < 0 || (i & 1) == parity) m |= field(i, bits);
+        return m;
+    }
+    static constexpr unsigned int VALID = rep((1u << Gm::H) - 1u, -1);
+    static constexpr unsigned int LSBF = rep(1u, -1);
+    static constexpr unsigned int MSBF = rep(1u << (Gm::H - 1), -1);
+    static constexpr unsigned int EVENF = rep(Gm::HP >= 32 ? 0xffffffffu : (1u << Gm::HP) - 1u, 0);
+};
+
+template <int L>
+__device__ __forceinline__ void pack_rows(const unsigned int *A, const unsigned int *B, unsigned int *PA,
+                                          unsigned int *PB)
+{
+    using Gm = Geo<L>;
+#pragma unroll
+    for (int c = 0; c < Gm::C; ++c) {
+        unsigned int a = 0, b = 0;
+#pragma unroll
+        for (int i = 0; i < Gm::P; ++i) {
+            a |= A[c * Gm::P + i] << (i * Gm::HP);
+            b |= B[c * Gm::P + i] << (i * Gm::HP);
+        }
+        PA[c] = a;
+        PB[c] = b;
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void unpack_rows(const unsigned int *PA, const unsigned int *PB, unsigned int *A,
+                                            unsigned int *B)
+{
+    using Gm = Geo<L>;
+    constexpr unsigned int m = (1u << Gm::H) - 1u;
+#pragma unroll
+    for (int c = 0; c < Gm::C; ++c)
+#pragma unroll
+        for (int i = 0; i < Gm::P; ++i) {
+            A[c * Gm::P + i] = (PA[c] >> (i * Gm::HP)) & m;
+            B[c * Gm::P + i] = (PB[c] >> (i * Gm::HP)) & m;
+        }
+}
+
+// The 8 bit planes of the lane's C chunks for one colour and sweep (chunk index = first row
+// of the chunk / P): words of Philox(ctr = (2 chunk + k / 4, slot, SWEEP << 28 | tag, i)).
+template <int L>
+__device__ __forceinline__ void packed_planes(int r0, unsigned int slot, unsigned int tag, unsigned int step,
+                                              const unsigned int *rk0, const unsigned int *rk1,
+                                              unsigned int (*plane)[8])
+{
+    using Gm = Geo<L>;
+    const PhiloxC0 pc = philox_c0_setup(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
+    const unsigned int chunk0 = (unsigned int)(r0 / Gm::P);
+#pragma unroll
+    for (int c = 0; c < Gm::C; ++c) {
+        const unsigned int ch = chunk0 + (unsigned int)c;
+        const uint4 p0 = philox_c0(2 * ch, pc, rk0, rk1);
+        const uint4 p1 = philox_c0(2 * ch + 1, pc, rk0, rk1);
+        plane[c][0] = p0.x; plane[c][1] = p0.y; plane[c][2] = p0.z; plane[c][3] = p0.w;
+        plane[c][4] = p1.x; plane[c][5] = p1.y; plane[c][6] = p1.z; plane[c][7] = p1.w;
+    }
+}
+
+// One colour (compile-time Q) of one sweep over the packed chunks of a lane, given that
+// colour's bit planes.  The same Metropolis test as half_sweep on 32 sites of P rows per
+// word: the vertical neighbours are the other colour's chunk word shifted by one field (the
+// field across a chunk boundary comes from the neighbouring chunk, lane or, at G = 1, the
+// periodic wrap), the horizontal ones the other colour's word as it is and rotated by one
+// site within every field, up in the fields whose row updates its even-column half and down
+// in the others.
+//
+// With PRE the planes come in `plane` (drawn by packed_planes); otherwise they are drawn
+// here, chunk by chunk.
+template <int L, int Q, bool PRE>
+__device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB, const unsigned int (*plane)[8],
+                                              int r0, int lane, unsigned int slot, unsigned int tag,
+                                              unsigned int step, const unsigned int *rk0, const unsigned int *rk1,
+                                              unsigned int k0, unsigned int k1, const Accept<unsigned int> &ac)
+{
+    using Gm = Geo<L>;
+    using Mk = PackMasks<L>;
+    constexpr int C = Gm::C, G = Gm::G, H = Gm::H, HP = Gm::HP, P = Gm::P, CB = Gm::CB;
+    constexpr bool XNOR = SweepStyle<L>::XNOR;
+    constexpr unsigned int LSBF = Mk::LSBF, MSBF = Mk::MSBF;
+    // fields whose row updates its even-column half: rows with (r + Q) even
+    constexpr unsigned int SEL_UP = (Q == 0) ? Mk::EVENF : ~Mk::EVENF;
+    unsigned int *T = (Q == 0) ? PA : PB;
+    const unsigned int *O = (Q == 0) ? PB : PA;
+
+    unsigned int from_up, from_down;
+    if constexpr (G > 1) {
+        const int gbase = lane & ~(G - 1);
+        const int q = lane & (G - 1);
+        from_up = __shfl_sync(0xffffffffu, O[C - 1], gbase | ((q - 1) & (G - 1)));
+        from_down = __shfl_sync(0xffffffffu, O[0], gbase | ((q + 1) & (G - 1)));
+    } else {
+        from_up = O[C - 1];
+        from_down = O[0];
+    }
+
+    PhiloxC0 pc;
+    if constexpr (!PRE) pc = philox_c0_setup(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
+
+    unsigned int lt[C], eq[C], a4[C], g3[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const unsigned int o = O[c];
+        const unsigned int prev = (c == 0) ? from_up : O[c - 1];
+        const unsigned int next = (c == C - 1) ? from_down : O[c + 1];
+        unsigned int up, dn;
+        if constexpr (CB == 32) {
+            up = __funnelshift_l(prev, o, HP);   // field i <- field i - 1, field 0 <- prev's last
+            dn = __funnelshift_r(o, next, HP);   // field i <- field i + 1, last <- next's field 0
+        } else {  // one chunk word holds the whole replica (L = 4): rotate by one field
+            constexpr unsigned int all = (1u << CB) - 1u;
+            up = ((o << HP) | (o >> (CB - HP))) & all;
+            dn = ((o >> HP) | (o << (CB - HP))) & all;
+        }
+        const unsigned int ru = ((o << 1) & ~LSBF) | ((o >> (H - 1)) & LSBF);  // site j <- j - 1
+        const unsigned int rd = ((o >> 1) & ~MSBF) | ((o << (H - 1)) & MSBF);  // site j <- j + 1
+        const unsigned int hb = (ru & SEL_UP) | (rd & ~SEL_UP);
+        unsigned int all4, eq3, ge3;
+        classify<XNOR>(T[c], up, dn, o, hb, Mk::VALID, all4, eq3, ge3);
+        if constexpr (PRE) {
+            compare_planes<XNOR>(plane[c], all4, eq3, ge3, ac, lt[c], eq[c]);
+        } else {
+            const unsigned int ch = (unsigned int)(r0 / P + c);
+            const uint4 p0 = philox_c0(2 * ch, pc, rk0, rk1);
+            const uint4 p1 = philox_c0(2 * ch + 1, pc, rk0, rk1);
+            const unsigned int pl[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+            compare_planes<XNOR>(pl, all4, eq3, ge3, ac, lt[c], eq[c]);
+        }
+        a4[c] = all4;
+        g3[c] = ge3;
+    }
+
+    unsigned int pending = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) pending |= eq[c];
+    while (pending) {
+        int csel = 0;
+        unsigned int w = 0, a4s = 0;
+#pragma unroll
+        for (int c = C - 1; c >= 0; --c)
+            if (eq[c]) {
+                csel = c;
+                w = eq[c];
+                a4s = a4[c];
+            }
+        const int b = __ffs((int)w) - 1;
+        const int r = r0 + csel * P + b / HP, j = b % HP;
+        const uint4 xr = philox(make_uint4((unsigned int)(64 * r + j), slot, (kStreamRefine << 28) | tag, step),
+                                k0, k1);
+        const unsigned int thr = ((a4s >> b) & 1u) ? ac.low8 : ac.low4;
+        const unsigned int bit = 1u << b;
+        const unsigned int acc = ((xr.x & 0xFFFFFFu) < thr) ? bit : 0u;
+        pending = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            if (c == csel) {
+                eq[c] &= ~bit;
+                lt[c] |= acc;
+            }
+            pending |= eq[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) T[c] ^= (~g3[c] | lt[c]) & Mk::VALID;
+}
+
+// theta sweeps (numbered t0 .. t0 + theta - 1 within the temperature step) of the rows a
+// lane holds: on packed chunks for L < 48 and row by row otherwise.  With at most two chunks
+// per lane both colours' planes are drawn before either update (they do not depend on the
+// spins), which gives the scheduler independent work.
+template <int L>
+__device__ __forceinline__ void sweep_rows(typename Geo<L>::W *A, typename Geo<L>::W *B, int r0, int lane,
+                                           unsigned int slot, int t0, int theta, unsigned int step,
+                                           const unsigned int *rk0, const unsigned int *rk1, unsigned int k0,
+                                           unsigned int k1, const Accept<typename Geo<L>::W> &ac)
+{
+    using Gm = Geo<L>;
+    if constexpr (Gm::PACK) {
+        constexpr int C = Gm::C;
+        if (theta <= 0) return;
+        unsigned int PA[C], PB[C];
+        pack_rows<L>(A, B, PA, PB);
+#pragma unroll 1
+        for (int t = 0; t < theta; ++t) {
+            const unsigned int tag0 = (unsigned int)(2 * (t0 + t));
+            if constexpr (C <= PA_PREFETCH_MAX_C) {
+                unsigned int pl0[C][8], pl1[C][8];
+                packed_planes<L>(r0, slot, tag0, step, rk0, rk1, pl0);
+                packed_planes<L>(r0, slot, tag0 | 1u, step, rk0, rk1, pl1);
+                packed_update<L, 0, true>(PA, PB, pl0, r0, lane, slot, tag0, step, rk0, rk1, k0, k1, ac);
+                packed_update<L, 1, true>(PA, PB, pl1, r0, lane, slot, tag0 | 1u, step, rk0, rk1, k0, k1, ac);
+            } else {
+                packed_update<L, 0, false>(PA, PB, nullptr, r0, lane, slot, tag0, step, rk0, rk1, k0, k1, ac);
+                packed_update<L, 1, false>(PA, PB, nullptr, r0, lane, slot, tag0 | 1u, step, rk0, rk1, k0, k1, ac);
+            }
+        }
+        unpack_rows<L>(PA, PB, A, B);
+    } else {
+#pragma unroll 1
+        for (int t = 0; t < theta; ++t) {
+            const unsigned int tag0 = (unsigned int)(2 * (t0 + t));
+            half_sweep<L, 0>(A, B, r0, lane, slot, tag0, step, rk0, rk1, k0, k1, ac);
+            half_sweep<L, 1>(A, B, r0, lane, slot, tag0 | 1u, step, rk0, rk1, k0, k1, ac);
+        }
+    }
 }
 
 // Energy level n_anti / 2 and number of up spins of the rows a lane holds (summed over the

@@ -151,21 +151,39 @@ def test_init_is_uniform():
 
 
 # ---------------------------------------------------------------------------- sweep
-@pytest.mark.parametrize("L,r,p", [(8, 3, 2), (64, 63, 31), (128, 5, 40), (128, 127, 63)])
+@pytest.mark.parametrize("L,r,p", [(4, 3, 1), (8, 3, 2), (12, 5, 4), (24, 23, 11), (32, 7, 9), (48, 47, 23),
+                                   (64, 63, 31), (128, 5, 40), (128, 127, 63)])
 def test_sweep_uniform_follows_its_definition(L, r, p):
-    """Top 8 bits from bit p mod 32 of eight Philox words (bit planes), low 24 bits from a
-    separate refinement draw, as documented in the oracle."""
+    """Top 8 bits from bit n mod 32 of eight Philox words (bit planes) of chunk n / 32, with
+    n = r H' + p the site's colour index (rows padded to H', the power of two >= L/2), low 24
+    bits from a separate refinement draw, as documented in the oracle."""
     seed, step, slot, tag = 0x1234_5678_9ABC, 17, 4242, 7
     key = [seed & 0xFFFFFFFF, seed >> 32]
-    nh = (L + 63) // 64
-    h, b = p // 32, p % 32
-    planes = np.concatenate([oracle.philox4x32_10([2 * (nh * r + h) + c, slot, (1 << 28) | tag, step], key)
+    hp = 1 << max(0, (L // 2 - 1).bit_length())
+    n = r * hp + p
+    chunk, b = n // 32, n % 32
+    planes = np.concatenate([oracle.philox4x32_10([2 * chunk + c, slot, (1 << 28) | tag, step], key)
                              for c in (0, 1)])
     top = 0
     for k in range(8):
         top |= ((int(planes[k]) >> b) & 1) << (31 - k)
     low = int(oracle.philox4x32_10([64 * r + p, slot, (4 << 28) | tag, step], key)[0]) & 0xFFFFFF
     assert oracle.sweep_uniform(L, seed, step, slot, tag, r, p) == top | low
+
+
+@pytest.mark.parametrize("L", [4, 8, 12, 16, 24, 32, 48, 64, 128])
+def test_sweep_planes_are_distinct_per_site(L):
+    """No two sites of one colour share a plane bit: two sites that did would have equal top
+    bytes in every sweep, while independent ones agree in a given sweep with probability
+    1/256 only."""
+    seed, step, slot = 99, 3, 11
+    H = L // 2
+    tops = np.array([[oracle.sweep_uniform(L, seed, step, slot, tag, r, p) >> 24
+                      for r in range(min(L, 8)) for p in range(H)] for tag in range(40)], dtype=np.int64)
+    # sites that shared a plane bit would have identical top bytes in every draw
+    n = tops.shape[1]
+    same = (tops[:, :, None] == tops[:, None, :]).all(axis=0)
+    assert not same[~np.eye(n, dtype=bool)].any()
 
 
 def test_sweep_uniform_is_uniform():
