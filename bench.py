@@ -32,25 +32,25 @@ METRIC = "Metropolis flips/ns on 1 GB300"
 UNIT = "attempts/ns"
 KERNELS_PER_STEP = 8  # k_table, k_counts, k_scan, k_copy, k_zero_measure, k_sweep, k_families, k_obs
 
-# Integer roofline of the sweep kernel (derivation in the design doc).  Peak: 152 SMs x 4
-# partitions x 32 lanes issue 128 32-bit integer operations per clock per SM.  Algorithmic
-# 32-bit integer operations per attempt of the bit-plane Metropolis step, per 32-site word:
-# 2 Philox4x32-10 calls for 8 bit planes (each call 20 widening multiplies counted as 2 ops
-# and 20 three-input XORs: 60 ops), 8 planes x 5 ops of bit-serial comparison, 15 ops of
-# neighbour classes and update; plus one 62-op low-bits draw for the 2^-8 of sites whose top
-# 8 bits tie with the threshold.
+# Integer roofline of the sweep kernel.  Peak: 152 SMs x 4 partitions x 32 lanes issue 128
+# 32-bit integer operations per clock per SM.  Algorithmic 32-bit integer operations per
+# attempt of the bit-plane Metropolis step, per 32-site word: 2 Philox4x32-10 calls for 8 bit
+# planes (each call 20 widening multiplies counted as 2 ops and 20 three-input XORs: 60 ops),
+# 8 planes x 3 ops of the borrow-chain comparison (threshold-bit select, majority, tie
+# update), 15 ops of neighbour classes and update; plus one 62-op low-bits draw for the 2^-8
+# of sites whose top 8 bits tie with the threshold.
 SMS = 152
 INT_OPS_PER_SM_CLK = 128.0
-OPS_PER_ATTEMPT = (2 * 60 + 8 * 5 + 15) / 32 + 62 / 256
+OPS_PER_ATTEMPT = (2 * 60 + 8 * 3 + 15) / 32 + 62 / 256
 # DRAM bytes per attempt of k_sweep<64> from one ncu capture; None until the current kernel
 # has been captured.
-SWEEP64_DRAM_BYTES_PER_ATTEMPT = (134.423296e6 + 75.671808e6) / (262144 * 4096 * 10)
+SWEEP64_DRAM_BYTES_PER_ATTEMPT = None
 
 
 def _parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--steps", type=int, default=297)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--L", type=int, default=L_DEFAULT)
@@ -238,29 +238,34 @@ def run_ours(args):
         Rs.append(o.R)
     attempts = float(N) * float(sum(Rs)) * theta
 
-    # end to end through the public API with host results: each step reads its record
-    # (pa_obs, D2H) and synchronises
-    pa2 = pa
-    e2e_steps = min(K, N_TEMPS - 1 - (W + K))
-    e2e = None
-    if e2e_steps >= 3:
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e2e_att = 0.0
-        ev0.record(stream)
-        for s in range(e2e_steps):
-            i = W + K + 1 + s
-            pa2.resample(beta(i))
-            pa2.anneal_step(theta)
-            o = pa2.observables()
-            e2e_att += float(N) * o["R"] * theta
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = ev0.elapsed_time(ev1)
-        e2e = {"value": e2e_att / (e2e_ms * 1e6), "unit": UNIT, "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": ctypes.sizeof(pa_obs), "steps": e2e_steps,
-               "note": "public API per step: pa_resample(beta) + pa_anneal_step(theta) + pa_observables "
-                       "(host record, synchronising); beta passes by value, no input tensor is copied"}
+    # end to end through the public API with host results, over the same temperature steps of
+    # a second run with the same seed: each step reads its record (pa_obs, D2H) and
+    # synchronises
+    pa.close()
+    del pa
+    pa2 = PopulationAnnealing(L, R, rank_seed(SEED, rank), device=dev, stream=stream)
+    for i in range(1, W + 1):
+        pa2.resample(beta(i))
+        pa2.anneal_step(theta)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_att = 0.0
+    ev0.record(stream)
+    for s in range(K):
+        i = W + 1 + s
+        pa2.resample(beta(i))
+        pa2.anneal_step(theta)
+        o = pa2.observables()
+        e2e_att += float(N) * o["R"] * theta
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ev0.elapsed_time(ev1)
+    e2e = {"value": e2e_att / (e2e_ms * 1e6), "unit": UNIT, "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": ctypes.sizeof(pa_obs), "steps": K,
+           "note": "public API per step: pa_resample(beta) + pa_anneal_step(theta) + pa_observables "
+                   "(host record, synchronising); beta passes by value, no input tensor is copied"}
+    pa2.close()
+    del pa2
 
     from paper_2102_06611_gb300.multi import aggregate
     ms, sweep_ms, attempts = aggregate(ms, sweep_ms, attempts, device=dev)
@@ -287,6 +292,7 @@ def run_ours(args):
             "config": {"workload": f"2D Ising PA L={L} R={R} theta={theta} beta=i/300 nearest-integer",
                        "L": L, "R": R, "theta": theta, "temperatures": N_TEMPS, "resampling": "nearest",
                        "parallelism": f"independent runs x{world}" if world > 1 else "single run",
+                       "beta_timed": [beta(W + 1), beta(W + K)],
                        "l2": "inputs larger than L2 (2 x %.0f MB spin buffers)" % (R * L * 2 * 4 / 1e6)},
             "roofline": {"bound": "alu", "kernel": f"k_sweep<{L}>", "achieved": achieved_tops,
                          "peak": peak_tops, "unit": "Tops/s (int32)", "frac": achieved_tops / peak_tops,

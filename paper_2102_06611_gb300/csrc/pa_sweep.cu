@@ -38,6 +38,11 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
     if (threadIdx.x < 7) sh_sum[threadIdx.x] = 0;
     __syncthreads();
     W *spins = reinterpret_cast<W *>(a.spins);
+    constexpr int TQ = SweepStyle<L>::TIE_QUEUE ? kTieQueueLen : 1;  // per warp; 8 warps per block
+    __shared__ W tq_eq[8 * TQ], tq_a4[8 * TQ];
+    __shared__ unsigned int tq_code[8 * TQ];
+    const int wib = threadIdx.x >> 5;
+    const TieQueue<W> tq{tq_eq + wib * TQ, tq_a4 + wib * TQ, tq_code + wib * TQ};
 
     for (long long base = warp * RPW; base < R; base += nwarps * RPW) {
         const long long j = base + sub;
@@ -53,7 +58,8 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
                 for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
             }
         }
-        sweep_rows<L>(A, B, r0, lane, (unsigned int)j, a.t0, a.theta, a.step, rk0, rk1, a.k0, a.k1, ac);
+        sweep_rows<L>(A, B, r0, lane, (unsigned int)j, (unsigned int)base, a.t0, a.theta, a.step, rk0, rk1, a.k0,
+                      a.k1, ac, tq);
         int anti, ups;
         measure_rows<L>(A, B, r0, lane, anti, ups);
         anti = group_sum<G>(anti);
@@ -176,7 +182,9 @@ cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cuda
 // cost), and dispatch on the run's lattice size.  The per-replica arithmetic is exactly the
 // single-run kernel's, with the histogram and sums going to the run's own workspace.
 template <int L>
-__device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare, long long g, int lane, int dry)
+__device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
+                                           unsigned long long *tq_eq, unsigned long long *tq_a4,
+                                           unsigned int *tq_code)
 {
     using Gm = Geo<L>;
     using W = typename Gm::W;
@@ -201,7 +209,9 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
 #pragma unroll
         for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
     }
-    sweep_rows<L>(A, B, r0, lane, (unsigned int)j, 0, a.theta, a.step, rk0, rk1, a.k0, a.k1, ac);
+    const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), tq_code};
+    sweep_rows<L>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, a.k0, a.k1,
+                  ac, tq);
     int anti, ups;
     measure_rows<L>(A, B, r0, lane, anti, ups);
     anti = group_sum<G>(anti);
@@ -250,6 +260,11 @@ __global__ void __launch_bounds__(256, 2) k_b_sweep(const BatchRun *runs, const 
 {
     const int lane = threadIdx.x & 31;
     const int dry = ctl->dry;
+    __shared__ unsigned long long tq_eq[8 * kTieQueueLen], tq_a4[8 * kTieQueueLen];
+    __shared__ unsigned int tq_code[8 * kTieQueueLen];
+    const int wib = threadIdx.x >> 5;
+    unsigned long long *qe = tq_eq + wib * kTieQueueLen, *qa = tq_a4 + wib * kTieQueueLen;
+    unsigned int *qc = tq_code + wib * kTieQueueLen;
     const long long total = ctl->total_items;
     for (;;) {
         long long item = 0;
@@ -272,15 +287,15 @@ __global__ void __launch_bounds__(256, 2) k_b_sweep(const BatchRun *runs, const 
         const void *spare = run.sw[s.cur ^ 1].spins;
         const long long g = item - item_start[lo];
         switch (run.L) {
-            case 4: batch_item<4>(a, spare, g, lane, dry); break;
-            case 8: batch_item<8>(a, spare, g, lane, dry); break;
-            case 12: batch_item<12>(a, spare, g, lane, dry); break;
-            case 16: batch_item<16>(a, spare, g, lane, dry); break;
-            case 24: batch_item<24>(a, spare, g, lane, dry); break;
-            case 32: batch_item<32>(a, spare, g, lane, dry); break;
-            case 48: batch_item<48>(a, spare, g, lane, dry); break;
-            case 64: batch_item<64>(a, spare, g, lane, dry); break;
-            case 128: batch_item<128>(a, spare, g, lane, dry); break;
+            case 4: batch_item<4>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 8: batch_item<8>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 12: batch_item<12>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 16: batch_item<16>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 24: batch_item<24>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 32: batch_item<32>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 48: batch_item<48>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 64: batch_item<64>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 128: batch_item<128>(a, spare, g, lane, dry, qe, qa, qc); break;
             default: break;
         }
     }

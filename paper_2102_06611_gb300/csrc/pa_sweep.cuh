@@ -29,6 +29,7 @@
 #define PA_PREFETCH_MAX_C 3
 #endif
 
+
 namespace pa {
 
 template <typename W, int H>
@@ -202,6 +203,10 @@ __device__ __forceinline__ void init_rows(unsigned int slot, int r0, unsigned in
 template <int L>
 struct SweepStyle {
     static constexpr bool XNOR = (L == 24 || L == 32 || L == 48 || L == 64);
+    // ties resolved through the warp's queue (below) when a lane holds 3 or more words;
+    // with 1 or 2 words the lane's own loop is cheaper (measured)
+    static constexpr int WORDS = Geo<L>::PACK ? Geo<L>::C : Geo<L>::RPL;
+    static constexpr bool TIE_QUEUE = WORDS >= 3;
 };
 
 // Per-launch constants.  T = floor(e^{-4 beta} 2^32) (class a = 3) or floor(e^{-8 beta} 2^32)
@@ -289,6 +294,74 @@ __device__ __forceinline__ void compare_planes(const W *plane, W all4, W eq3, W 
     eq = e;
 }
 
+// ------------------------------------------------------------------------------------
+// Ties x_top = T_top are rare (2^-8 per site) but land on few lanes of a warp, so a loop in
+// which every lane resolves its own ties runs as many Philox passes as the busiest lane has
+// ties.  Instead the warp resolves them together: every (lane, word) with ties becomes one
+// entry of a per-warp queue in shared memory, lane t draws the low bits of the sites of entry
+// t (t + 32, ... if there are more), and the owners read the accept bits back.  One pass
+// usually serves the whole warp.
+// ------------------------------------------------------------------------------------
+template <typename W>
+struct TieQueue {
+    W *eq;              // tie mask of the entry's word (overwritten with the accept mask)
+    W *a4;              // class-4 mask of the word
+    unsigned int *code; // owner lane << 4 | word index
+};
+
+// entries per warp: 32 lanes x up to 4 words
+constexpr int kTieQueueLen = 128;
+
+struct TieSite {
+    unsigned int slot;  // replica slot
+    int r, j;           // row and position within the colour's half-row
+};
+
+template <int NW, typename W, typename SiteOf>
+__device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, int lane, const TieQueue<W> &q,
+                                             SiteOf site_of, unsigned int tag, unsigned int step, unsigned int k0,
+                                             unsigned int k1, unsigned int low4, unsigned int low8)
+{
+    static_assert(NW <= 4, "tie queue holds 4 words per lane");
+    const unsigned int below = (1u << lane) - 1u;
+    int pos[NW];
+    int total = 0;
+    __syncwarp();  // the previous call's read-back is complete
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        const unsigned int b = __ballot_sync(0xffffffffu, eq[i] != W(0));
+        pos[i] = total + __popc(b & below);
+        if (eq[i] != W(0)) {
+            q.eq[pos[i]] = eq[i];
+            q.a4[pos[i]] = a4[i];
+            q.code[pos[i]] = ((unsigned int)lane << 4) | (unsigned int)i;
+        }
+        total += __popc(b);
+    }
+    if (total == 0) return;
+    __syncwarp();
+    for (int t = lane; t < total; t += 32) {
+        W w = q.eq[t];
+        const W a = q.a4[t];
+        const unsigned int code = q.code[t];
+        W acc = 0;
+        while (w) {
+            const int b = (sizeof(W) == 8) ? __ffsll((long long)w) - 1 : __ffs((int)w) - 1;
+            const TieSite s = site_of((int)(code >> 4), (int)(code & 15u), b);
+            const uint4 x = philox(make_uint4((unsigned int)(64 * s.r + s.j), s.slot, (kStreamRefine << 28) | tag,
+                                              step), k0, k1);
+            const unsigned int thr = ((a >> b) & W(1)) ? low8 : low4;
+            if ((x.x & 0xFFFFFFu) < thr) acc |= W(1) << b;
+            w &= w - W(1);
+        }
+        q.eq[t] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < NW; ++i)
+        if (eq[i] != W(0)) lt[i] |= q.eq[pos[i]];
+}
+
 // One colour (compile-time Q) of one sweep over the rows a lane holds (sizes L >= 48).
 //
 // Acceptance x < T is decided over the 32 sites of a word at once: the top 8 bits of every
@@ -300,10 +373,11 @@ __device__ __forceinline__ void compare_planes(const W *plane, W all4, W eq3, W 
 // bits of word 0 of Philox(ctr = (64 r + j, slot, REFINE << 28 | tag, i)), tag = 2t + Q.
 template <int L, int Q>
 __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L>::W *B, int r0,
-                                           int lane, unsigned int slot, unsigned int tag,
+                                           int lane, unsigned int slot, unsigned int slot0, unsigned int tag,
                                            unsigned int step, const unsigned int *rk0,
                                            const unsigned int *rk1, unsigned int k0, unsigned int k1,
-                                           const Accept<typename Geo<L>::W> &ac)
+                                           const Accept<typename Geo<L>::W> &ac,
+                                           const TieQueue<typename Geo<L>::W> &tq)
 {
     using Gm = Geo<L>;
     using W = typename Gm::W;
@@ -356,37 +430,14 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
         g3[i] = ge3;
     }
 
-    // rare: the low 24 bits decide the sites whose top 8 bits equal the threshold's; one
-    // loop over all rows of the lane keeps the warp's divergent iterations few
-    W pending = 0;
-#pragma unroll
-    for (int i = 0; i < RPL; ++i) pending |= eq[i];
-    while (pending) {
-        int isel = 0;
-        W w = 0, a4s = 0;
-#pragma unroll
-        for (int i = RPL - 1; i >= 0; --i)
-            if (eq[i]) {
-                isel = i;
-                w = eq[i];
-                a4s = a4[i];
-            }
-        const int j = Gm::WIDE ? __ffsll((long long)w) - 1 : __ffs((int)w) - 1;
-        const uint4 xr = philox(make_uint4((unsigned int)(64 * (r0 + isel) + j), slot, (kStreamRefine << 28) | tag,
-                                           step), k0, k1);
-        const unsigned int thr = ((a4s >> j) & W(1)) ? ac.low8 : ac.low4;
-        const W bit = W(1) << j;
-        const W acc = ((xr.x & 0xFFFFFFu) < thr) ? bit : W(0);
-        pending = 0;
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-            if (i == isel) {
-                eq[i] &= ~bit;
-                lt[i] |= acc;
-            }
-            pending |= eq[i];
-        }
-    }
+    // rare: the low 24 bits decide the sites whose top 8 bits equal the threshold's
+    static_assert(SweepStyle<L>::TIE_QUEUE, "row-wise sizes hold 3 or more words per lane");
+    (void)slot;
+    resolve_ties<RPL>(eq, a4, lt, lane, tq,
+                      [&](int src, int i, int b) {
+                          return TieSite{slot0 + (unsigned int)(src / G), (src & (G - 1)) * RPL + i, b};
+                      },
+                      tag, step, k0, k1, ac.low4, ac.low8);
 #pragma unroll
     for (int i = 0; i < RPL; ++i) T[i] ^= (~g3[i] | lt[i]) & half_mask<W, H>();
 }
@@ -478,9 +529,10 @@ __device__ __forceinline__ void packed_planes(int r0, unsigned int slot, unsigne
 // here, chunk by chunk.
 template <int L, int Q, bool PRE>
 __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB, const unsigned int (*plane)[8],
-                                              int r0, int lane, unsigned int slot, unsigned int tag,
-                                              unsigned int step, const unsigned int *rk0, const unsigned int *rk1,
-                                              unsigned int k0, unsigned int k1, const Accept<unsigned int> &ac)
+                                              int r0, int lane, unsigned int slot, unsigned int slot0,
+                                              unsigned int tag, unsigned int step, const unsigned int *rk0,
+                                              const unsigned int *rk1, unsigned int k0, unsigned int k1,
+                                              const Accept<unsigned int> &ac, const TieQueue<unsigned int> &tq)
 {
     using Gm = Geo<L>;
     using Mk = PackMasks<L>;
@@ -539,34 +591,44 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
         g3[c] = ge3;
     }
 
-    unsigned int pending = 0;
+    if constexpr (SweepStyle<L>::TIE_QUEUE) {
+        resolve_ties<C>(eq, a4, lt, lane, tq,
+                        [&](int src, int c, int b) {
+                            return TieSite{slot0 + (unsigned int)(src / G), (src & (G - 1)) * Gm::RPL + c * P + b / HP,
+                                           b % HP};
+                        },
+                        tag, step, k0, k1, ac.low4, ac.low8);
+    } else {
+        // the lane resolves its own ties, one per iteration over all its words
+        unsigned int pending = 0;
 #pragma unroll
-    for (int c = 0; c < C; ++c) pending |= eq[c];
-    while (pending) {
-        int csel = 0;
-        unsigned int w = 0, a4s = 0;
+        for (int c = 0; c < C; ++c) pending |= eq[c];
+        while (pending) {
+            int csel = 0;
+            unsigned int w = 0, a4s = 0;
 #pragma unroll
-        for (int c = C - 1; c >= 0; --c)
-            if (eq[c]) {
-                csel = c;
-                w = eq[c];
-                a4s = a4[c];
+            for (int c = C - 1; c >= 0; --c)
+                if (eq[c]) {
+                    csel = c;
+                    w = eq[c];
+                    a4s = a4[c];
+                }
+            const int b = __ffs((int)w) - 1;
+            const int r = r0 + csel * P + b / HP, j = b % HP;
+            const uint4 xr = philox(make_uint4((unsigned int)(64 * r + j), slot, (kStreamRefine << 28) | tag, step),
+                                    k0, k1);
+            const unsigned int thr = ((a4s >> b) & 1u) ? ac.low8 : ac.low4;
+            const unsigned int bit = 1u << b;
+            const unsigned int acc = ((xr.x & 0xFFFFFFu) < thr) ? bit : 0u;
+            pending = 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (c == csel) {
+                    eq[c] &= ~bit;
+                    lt[c] |= acc;
+                }
+                pending |= eq[c];
             }
-        const int b = __ffs((int)w) - 1;
-        const int r = r0 + csel * P + b / HP, j = b % HP;
-        const uint4 xr = philox(make_uint4((unsigned int)(64 * r + j), slot, (kStreamRefine << 28) | tag, step),
-                                k0, k1);
-        const unsigned int thr = ((a4s >> b) & 1u) ? ac.low8 : ac.low4;
-        const unsigned int bit = 1u << b;
-        const unsigned int acc = ((xr.x & 0xFFFFFFu) < thr) ? bit : 0u;
-        pending = 0;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            if (c == csel) {
-                eq[c] &= ~bit;
-                lt[c] |= acc;
-            }
-            pending |= eq[c];
         }
     }
 #pragma unroll
@@ -577,11 +639,15 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
 // lane holds: on packed chunks for L < 48 and row by row otherwise.  With at most two chunks
 // per lane both colours' planes are drawn before either update (they do not depend on the
 // spins), which gives the scheduler independent work.
+//
+// slot = the lane's replica slot, slot0 = the slot of the warp's first replica; tq = the
+// warp's tie queue.
 template <int L>
 __device__ __forceinline__ void sweep_rows(typename Geo<L>::W *A, typename Geo<L>::W *B, int r0, int lane,
-                                           unsigned int slot, int t0, int theta, unsigned int step,
-                                           const unsigned int *rk0, const unsigned int *rk1, unsigned int k0,
-                                           unsigned int k1, const Accept<typename Geo<L>::W> &ac)
+                                           unsigned int slot, unsigned int slot0, int t0, int theta,
+                                           unsigned int step, const unsigned int *rk0, const unsigned int *rk1,
+                                           unsigned int k0, unsigned int k1, const Accept<typename Geo<L>::W> &ac,
+                                           const TieQueue<typename Geo<L>::W> &tq)
 {
     using Gm = Geo<L>;
     if constexpr (Gm::PACK) {
@@ -596,11 +662,11 @@ __device__ __forceinline__ void sweep_rows(typename Geo<L>::W *A, typename Geo<L
                 unsigned int pl0[C][8], pl1[C][8];
                 packed_planes<L>(r0, slot, tag0, step, rk0, rk1, pl0);
                 packed_planes<L>(r0, slot, tag0 | 1u, step, rk0, rk1, pl1);
-                packed_update<L, 0, true>(PA, PB, pl0, r0, lane, slot, tag0, step, rk0, rk1, k0, k1, ac);
-                packed_update<L, 1, true>(PA, PB, pl1, r0, lane, slot, tag0 | 1u, step, rk0, rk1, k0, k1, ac);
+                packed_update<L, 0, true>(PA, PB, pl0, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
+                packed_update<L, 1, true>(PA, PB, pl1, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
             } else {
-                packed_update<L, 0, false>(PA, PB, nullptr, r0, lane, slot, tag0, step, rk0, rk1, k0, k1, ac);
-                packed_update<L, 1, false>(PA, PB, nullptr, r0, lane, slot, tag0 | 1u, step, rk0, rk1, k0, k1, ac);
+                packed_update<L, 0, false>(PA, PB, nullptr, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
+                packed_update<L, 1, false>(PA, PB, nullptr, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
             }
         }
         unpack_rows<L>(PA, PB, A, B);
@@ -608,8 +674,8 @@ __device__ __forceinline__ void sweep_rows(typename Geo<L>::W *A, typename Geo<L
 #pragma unroll 1
         for (int t = 0; t < theta; ++t) {
             const unsigned int tag0 = (unsigned int)(2 * (t0 + t));
-            half_sweep<L, 0>(A, B, r0, lane, slot, tag0, step, rk0, rk1, k0, k1, ac);
-            half_sweep<L, 1>(A, B, r0, lane, slot, tag0 | 1u, step, rk0, rk1, k0, k1, ac);
+            half_sweep<L, 0>(A, B, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
+            half_sweep<L, 1>(A, B, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
         }
     }
 }
