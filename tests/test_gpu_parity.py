@@ -72,6 +72,27 @@ def test_run_parity(L, R, kind, nT, theta):
     run_side_by_side(gpu, ref, betas, theta)
 
 
+# Low temperatures after a fast quench: most sites have three or four aligned neighbours, so
+# the top 8 bits of many uniforms tie with the threshold's (2^-8 per site) and the low 24
+# bits decide.  At L = 128 (256 sites per lane) a warp often holds more than 32 tie words,
+# which the tie queue resolves in several passes; L = 24 and 32 use the queue on packed
+# chunks, L = 16 the per-lane loop.
+TIE_HEAVY = [
+    (128, 400, [0.5, 0.8, 1.0], 2),
+    (64, 1500, [0.45, 0.7, 0.95], 3),
+    (32, 3000, [0.5, 0.9], 3),
+    (24, 3000, [0.5, 0.9], 3),
+    (16, 5000, [0.5, 0.9], 3),
+]
+
+
+@pytest.mark.parametrize("L,R,betas,theta", TIE_HEAVY)
+def test_tie_heavy_parity(L, R, betas, theta):
+    gpu = _pa(L, R, seed=3)
+    ref = oracle.PA(L, R, 3, capacity=gpu.capacity)
+    run_side_by_side(gpu, ref, betas, theta)
+
+
 def test_split_sweeps_equal_one_call():
     """Sweeps are numbered within a temperature step, so 3 + 7 sweeps == 10 sweeps."""
     L, R = 16, 200
