@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
     if (threadIdx.x < 7) sh_sum[threadIdx.x] = 0;
     __syncthreads();
     W *spins = reinterpret_cast<W *>(a.spins);
-    constexpr int TQ = SweepStyle<L>::TIE_QUEUE ? kTieQueueLen : 1;  // per warp; 8 warps per block
+    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp; 8 warps per block
     __shared__ W tq_eq[8 * TQ], tq_a4[8 * TQ];
     __shared__ unsigned int tq_code[8 * TQ];
     const int wib = threadIdx.x >> 5;
@@ -260,11 +260,12 @@ __global__ void __launch_bounds__(256, 2) k_b_sweep(const BatchRun *runs, const 
 {
     const int lane = threadIdx.x & 31;
     const int dry = ctl->dry;
-    __shared__ unsigned long long tq_eq[8 * kTieQueueLen], tq_a4[8 * kTieQueueLen];
-    __shared__ unsigned int tq_code[8 * kTieQueueLen];
+    constexpr int TQ = batch_tie_queue_len();  // per warp; 8 warps per block
+    __shared__ unsigned long long tq_eq[8 * TQ], tq_a4[8 * TQ];
+    __shared__ unsigned int tq_code[8 * TQ];
     const int wib = threadIdx.x >> 5;
-    unsigned long long *qe = tq_eq + wib * kTieQueueLen, *qa = tq_a4 + wib * kTieQueueLen;
-    unsigned int *qc = tq_code + wib * kTieQueueLen;
+    unsigned long long *qe = tq_eq + wib * TQ, *qa = tq_a4 + wib * TQ;
+    unsigned int *qc = tq_code + wib * TQ;
     const long long total = ctl->total_items;
     for (;;) {
         long long item = 0;

@@ -99,6 +99,19 @@ __device__ __forceinline__ uint4 philox_c0(unsigned int c0, const PhiloxC0 &p, c
     return c;
 }
 
+// Philox4x32-10 with the round keys precomputed (rk[i] = k + i W).
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const unsigned int *rk0, const unsigned int *rk1)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        unsigned int hi0, lo0, hi1, lo1;
+        mulhilo(kPhiloxM0, c.x, hi0, lo0);
+        mulhilo(kPhiloxM1, c.z, hi1, lo1);
+        c = make_uint4(hi1 ^ c.y ^ rk0[i], lo1, hi0 ^ c.w ^ rk1[i], lo0);
+    }
+    return c;
+}
+
 // Load / store the RPL rows of one lane as (A, B) pairs: A_r = half (r & 1) of row r (the
 // half updated by colour 0), B_r = the other half (updated by colour 1).
 template <int L>
@@ -207,7 +220,19 @@ struct SweepStyle {
     // with 1 or 2 words the lane's own loop is cheaper (measured)
     static constexpr int WORDS = Geo<L>::PACK ? Geo<L>::C : Geo<L>::RPL;
     static constexpr bool TIE_QUEUE = WORDS >= 3;
+    static constexpr int TQ_LEN = TIE_QUEUE ? 32 * WORDS : 1;  // queue entries per warp
 };
+
+// tie queue entries per warp that serve every lattice size (persistent batch kernel)
+constexpr int batch_tie_queue_len()
+{
+    const int v[] = {SweepStyle<4>::TQ_LEN,  SweepStyle<8>::TQ_LEN,  SweepStyle<12>::TQ_LEN,
+                     SweepStyle<16>::TQ_LEN, SweepStyle<24>::TQ_LEN, SweepStyle<32>::TQ_LEN,
+                     SweepStyle<48>::TQ_LEN, SweepStyle<64>::TQ_LEN, SweepStyle<128>::TQ_LEN};
+    int m = 1;
+    for (int x : v) m = x > m ? x : m;
+    return m;
+}
 
 // Per-launch constants.  T = floor(e^{-4 beta} 2^32) (class a = 3) or floor(e^{-8 beta} 2^32)
 // (a = 4), T in [0, 2^32], split as T = top 2^24 + low: m[k] = all ones iff bit 7 - k of top
@@ -309,9 +334,6 @@ struct TieQueue {
     unsigned int *code; // owner lane << 4 | word index
 };
 
-// entries per warp: 32 lanes x up to 4 words
-constexpr int kTieQueueLen = 128;
-
 struct TieSite {
     unsigned int slot;  // replica slot
     int r, j;           // row and position within the colour's half-row
@@ -319,10 +341,11 @@ struct TieSite {
 
 template <int NW, typename W, typename SiteOf>
 __device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, int lane, const TieQueue<W> &q,
-                                             SiteOf site_of, unsigned int tag, unsigned int step, unsigned int k0,
-                                             unsigned int k1, unsigned int low4, unsigned int low8)
+                                             SiteOf site_of, unsigned int tag, unsigned int step,
+                                             const unsigned int *rk0, const unsigned int *rk1, unsigned int low4,
+                                             unsigned int low8)
 {
-    static_assert(NW <= 4, "tie queue holds 4 words per lane");
+    static_assert(NW <= 15, "word index is 4 bits of the entry code");
     const unsigned int below = (1u << lane) - 1u;
     int pos[NW];
     int total = 0;
@@ -348,8 +371,8 @@ __device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, in
         while (w) {
             const int b = (sizeof(W) == 8) ? __ffsll((long long)w) - 1 : __ffs((int)w) - 1;
             const TieSite s = site_of((int)(code >> 4), (int)(code & 15u), b);
-            const uint4 x = philox(make_uint4((unsigned int)(64 * s.r + s.j), s.slot, (kStreamRefine << 28) | tag,
-                                              step), k0, k1);
+            const uint4 x = philox_rk(make_uint4((unsigned int)(64 * s.r + s.j), s.slot, (kStreamRefine << 28) | tag,
+                                                 step), rk0, rk1);
             const unsigned int thr = ((a >> b) & W(1)) ? low8 : low4;
             if ((x.x & 0xFFFFFFu) < thr) acc |= W(1) << b;
             w &= w - W(1);
@@ -437,7 +460,7 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
                       [&](int src, int i, int b) {
                           return TieSite{slot0 + (unsigned int)(src / G), (src & (G - 1)) * RPL + i, b};
                       },
-                      tag, step, k0, k1, ac.low4, ac.low8);
+                      tag, step, rk0, rk1, ac.low4, ac.low8);
 #pragma unroll
     for (int i = 0; i < RPL; ++i) T[i] ^= (~g3[i] | lt[i]) & half_mask<W, H>();
 }
@@ -597,7 +620,7 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
                             return TieSite{slot0 + (unsigned int)(src / G), (src & (G - 1)) * Gm::RPL + c * P + b / HP,
                                            b % HP};
                         },
-                        tag, step, k0, k1, ac.low4, ac.low8);
+                        tag, step, rk0, rk1, ac.low4, ac.low8);
     } else {
         // the lane resolves its own ties, one per iteration over all its words
         unsigned int pending = 0;
@@ -615,8 +638,8 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
                 }
             const int b = __ffs((int)w) - 1;
             const int r = r0 + csel * P + b / HP, j = b % HP;
-            const uint4 xr = philox(make_uint4((unsigned int)(64 * r + j), slot, (kStreamRefine << 28) | tag, step),
-                                    k0, k1);
+            const uint4 xr = philox_rk(make_uint4((unsigned int)(64 * r + j), slot, (kStreamRefine << 28) | tag, step),
+                                       rk0, rk1);
             const unsigned int thr = ((a4s >> b) & 1u) ? ac.low8 : ac.low4;
             const unsigned int bit = 1u << b;
             const unsigned int acc = ((xr.x & 0xFFFFFFu) < thr) ? bit : 0u;
