@@ -136,14 +136,14 @@ def cpu_baseline(L: int, theta: int) -> dict:
 
 
 # ------------------------------------------------------------------------------ schedules
-SCHED_L, SCHED_R, SCHED_SEED, SCHED_TARGET = 128, 200_000, 1, 1e-4
+SCHED_L, SCHED_R, SCHED_SEEDS, SCHED_TARGET = 128, 200_000, (1, 2, 3, 4), 1e-4
 
 
 def schedule_eval(dev) -> dict:
     """Second half of the metric: wall time of a whole anneal (beta 0 -> 1, L=128, R=2e5) with
     the plain adaptive schedule (overlap bisection at 0.8, theta = 10) and with the learned one,
     and each run's free-energy deviation per spin at beta = 1 from the exact finite-lattice
-    value (Kaufman's closed form, tests/golden/exact_lnZ.json)."""
+    value (Kaufman's closed form, tests/golden/exact_lnZ.json); seeds 1-4."""
     import torch
 
     from paper_2102_06611_gb300 import PopulationAnnealing
@@ -153,19 +153,26 @@ def schedule_eval(dev) -> dict:
     with open(os.path.join(ROOT, "tests", "golden", "exact_lnZ.json")) as f:
         exact = json.load(f)["lnZ"][str(SCHED_L)]["1.0"]
     model = ScheduleMLP.load(DEFAULT_WEIGHTS, device=dev)
-    out = {"L": SCHED_L, "R": SCHED_R, "seed": SCHED_SEED, "target_abs_dbetaf_per_spin": SCHED_TARGET,
-           "exact_lnZ_beta1": exact}
+    out = {"L": SCHED_L, "R": SCHED_R, "seeds": list(SCHED_SEEDS), "target_abs_dbetaf_per_spin": SCHED_TARGET,
+           "exact_lnZ_beta1": exact, "runs": []}
+    for seed in SCHED_SEEDS:
+        run = {"seed": seed}
+        for mode in ("plain", "learned"):
+            pa = PopulationAnnealing(SCHED_L, SCHED_R, seed, device=dev)
+            r = anneal(pa, mode, model)
+            r["abs_dbetaf_per_spin"] = abs(r["minus_betaF"] - exact) / (SCHED_L * SCHED_L)
+            r["reached_target"] = r["abs_dbetaf_per_spin"] <= SCHED_TARGET
+            run[mode] = {k: r[k] for k in ("wall_s", "steps", "sweeps", "fallbacks", "extensions",
+                                           "abs_dbetaf_per_spin", "reached_target")}
+            pa.close()
+            del pa
+            torch.cuda.empty_cache()
+        run["speedup"] = run["plain"]["wall_s"] / run["learned"]["wall_s"]
+        out["runs"].append(run)
     for mode in ("plain", "learned"):
-        pa = PopulationAnnealing(SCHED_L, SCHED_R, SCHED_SEED, device=dev)
-        r = anneal(pa, mode, model)
-        r["abs_dbetaf_per_spin"] = abs(r["minus_betaF"] - exact) / (SCHED_L * SCHED_L)
-        r["reached_target"] = r["abs_dbetaf_per_spin"] <= SCHED_TARGET
-        out[mode] = {k: r[k] for k in ("wall_s", "steps", "sweeps", "fallbacks", "extensions",
-                                       "abs_dbetaf_per_spin", "reached_target")}
-        pa.close()
-        del pa
-        torch.cuda.empty_cache()
-    out["speedup"] = out["plain"]["wall_s"] / out["learned"]["wall_s"]
+        out[mode + "_wall_s_total"] = sum(r[mode]["wall_s"] for r in out["runs"])
+        out[mode + "_reached_target"] = sum(bool(r[mode]["reached_target"]) for r in out["runs"])
+    out["speedup"] = out["plain_wall_s_total"] / out["learned_wall_s_total"]
     return out
 
 

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.p
 ``cpu_baseline`` / ``--impl reference`` leg may import this package.  The product path
 (``paper_2102_06611_gb300``) never imports it and shares no code with it.
 
-The arithmetic lives in plain C (``pa_oracle.c``, ``exact_ising.c``), built with gcc
+The arithmetic lives in plain C (``pa_oracle.c``, ``exact_ising.c``, ``pa_analysis.c``), built with gcc
 and ``-ffp-contract=off`` so that every binary64 multiply and add is rounded on its own.
 This module only marshals arguments through ctypes and adds nothing to the method.
 
@@ -28,7 +28,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liborapa.so")
-_SOURCES = ["pa_oracle.c", "exact_ising.c"]
+_SOURCES = ["pa_oracle.c", "exact_ising.c", "pa_analysis.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -119,6 +119,9 @@ def lib():
                                                            ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                            ctypes.c_double, ctypes.c_int, dp,
                                                            ctypes.POINTER(ctypes.c_int)]),
+                "orc_analysis": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int64, i32p, i32p,
+                                                i32p, ctypes.c_int, dp]),
+                "orc_pa_analysis": (ctypes.c_int, [vp, ctypes.c_int, dp]),
                 "orc_bruteforce": (ctypes.c_int, [ctypes.c_int, i64p, i64p, i64p]),
                 "orc_transfer_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
                 "orc_kaufman_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
@@ -278,6 +281,26 @@ OBS_FIELDS = ["beta", "dbeta", "R", "e", "C", "m", "m2", "chi", "lnQ", "minus_be
               "families", "rho_t", "step", "theta"]
 
 
+ANALYSIS_FIELDS = ["n_blocks", "mean_E", "var_E", "var_mean_E_jack", "var_mean_E_blocked", "R_eff_E",
+                   "mean_absM", "var_absM", "var_mean_absM_jack", "var_mean_absM_blocked", "R_eff_M",
+                   "C", "var_C_jack", "S_f", "rho_s", "families"]
+
+
+def analysis(N: int, beta: float, E, M, fam, n_blocks: int = 100) -> dict:
+    """Blocked / jackknife errors, R_eff(E), R_eff(|M|), family entropy of a population given
+    as arrays in slot (tree) order (Sec. IV Eqs. neff, blocks, blocked_variance,
+    jackknife-blocks, jackknife-variance; Sec. V Eq. rhos)."""
+    E = np.ascontiguousarray(E, np.int32)
+    M = np.ascontiguousarray(M, np.int32)
+    fam = np.ascontiguousarray(fam, np.int32)
+    out = np.zeros(16)
+    st = lib().orc_analysis(int(N), float(beta), len(E), _ptr(E, ctypes.c_int32), _ptr(M, ctypes.c_int32),
+                            _ptr(fam, ctypes.c_int32), int(n_blocks), _ptr(out, ctypes.c_double))
+    if st != 0:
+        raise ValueError("need 2 <= n_blocks <= R")
+    return dict(zip(ANALYSIS_FIELDS, out.tolist()))
+
+
 class PA:
     """Plain single-threaded population annealing run (Sec. II steps 1-5)."""
 
@@ -319,6 +342,13 @@ class PA:
         d = dict(zip(OBS_FIELDS, out.tolist()))
         d["sums"] = isums
         return d
+
+    def analysis(self, n_blocks: int = 100) -> dict:
+        out = np.zeros(16)
+        st = lib().orc_pa_analysis(self._h, int(n_blocks), _ptr(out, ctypes.c_double))
+        if st != 0:
+            raise ValueError("need 2 <= n_blocks <= R")
+        return dict(zip(ANALYSIS_FIELDS, out.tolist()))
 
     def histogram(self) -> np.ndarray:
         h = np.zeros(self.N + 1, np.int32)

@@ -727,3 +727,13 @@ int orc_pa_set(orc_pa *p, int64_t R, const int8_t *spins, const int32_t *fam,
     measure_all(p);
     return 0;
 }
+
+/* Population analysis of the current population (blocked and jackknife errors, effective
+   population sizes, family entropy): see pa_analysis.c. */
+int orc_analysis(int N, double beta, int64_t R, const int32_t *E, const int32_t *M, const int32_t *fam,
+                 int n, double *out);
+
+int orc_pa_analysis(const orc_pa *p, int n, double *out)
+{
+    return orc_analysis(p->N, p->beta, p->R, p->E, p->M, p->fam, n, out);
+}
