@@ -160,6 +160,37 @@ pa_status pa_record(pa_ctx *ctx, void *device_dst);
    returns the sticky device error, if any. */
 pa_status pa_observables(pa_ctx *ctx, pa_obs *host_out);
 
+/* Population analysis (Sec. IV, Eqs. neff, blocks, blocked_variance, jackknife-blocks,
+   jackknife-variance; Sec. V, Eq. rhos).  The R_i replicas are taken in slot order, which
+   is tree order (the children of one parent sit next to each other, so correlations are
+   local), and cut into n contiguous blocks, block b = slots [floor(b R / n),
+   floor((b + 1) R / n)).  From exact int64 block sums of E, E^2, |M|, M^2 every field below
+   is formed in binary64 in a fixed order:
+     var_X            unbiased variance of the unblocked series, (sum x^2 - R mean^2)/(R-1)
+     var_mean_X_blocked   1/(n(n-1)) sum_b (X^B_b - mean_b X^B)^2, X^B_b = block mean
+     var_mean_X_jack  (n-1)/n sum_b (X^J_b - mean_b X^J)^2, X^J_b = mean outside block b
+     R_eff_X          var_X / var_mean_X_jack (effective number of independent replicas)
+     var_C_jack       the same jackknife for C = beta^2 (<E^2> - <E>^2) / N
+     S_f              -sum_k (s_k/R) ln(s_k/R) over families k of size s_k, summed by size
+     rho_s            R / exp(S_f)
+   for X = E (energy) and |M|. */
+typedef struct {
+    long long R;              /* population size R_i */
+    long long families;       /* number of families f */
+    int n_blocks;             /* n */
+    int pad;
+    double beta;              /* beta_i */
+    double mean_E, var_E, var_mean_E_jack, var_mean_E_blocked, R_eff_E;
+    double mean_absM, var_absM, var_mean_absM_jack, var_mean_absM_blocked, R_eff_M;
+    double C, var_C_jack;
+    double S_f, rho_s;
+} pa_analysis;
+
+/* Analyse the current population (measured first if a resampling came since) in n_blocks
+   blocks, 2 <= n_blocks <= min(R_i, 1024), and copy the result to host memory.
+   Synchronising; PA_ERR_INVALID_ARG for a bad n_blocks (checked against R_i on the host). */
+pa_status pa_analyze(pa_ctx *ctx, int n_blocks, pa_analysis *host_out);
+
 /* Adaptive temperature step (the paper's self-adaptive steps, Sec. II; overlap guideline
    alpha > 0.7, Sec. X).  From the energy-level histogram h_k of the current population
    (measured at the current beta; measured first if a resampling came since), the overlap

@@ -59,7 +59,7 @@ int orc_analysis(int N, double beta, int64_t R, const int32_t *E, const int32_t 
     }
 
     const double meanE = (double)tE / Rd, meanE2 = (double)tE2 / Rd;
-    const double meanA = (double)tA / Rd, meanA2 = (double)tA2 / Rd;
+    const double meanA = (double)tA / Rd;
     /* unbiased variances of the unblocked series: (sum x^2 - R mean^2) / (R - 1) */
     const double varE = (R > 1) ? ((double)tE2 - Rd * (meanE * meanE)) / (Rd - 1.0) : 0.0;
     const double varA = (R > 1) ? ((double)tA2 - Rd * (meanA * meanA)) / (Rd - 1.0) : 0.0;
@@ -113,19 +113,22 @@ int orc_analysis(int N, double beta, int64_t R, const int32_t *E, const int32_t 
     vJA *= fj;
     vJC *= fj;
 
-    /* families: runs of equal ids in slot order; S_f = -sum_k (size_k / R) ln(size_k / R) */
-    double Sf = 0.0;
+    /* families: runs of equal ids in slot order; S_f = -sum_k (size_k / R) ln(size_k / R),
+       accumulated in long double: up to R terms, many of them equal, whose binary64
+       rounding errors would add up coherently */
+    long double acc = 0.0L;
     int64_t f = 0, run = 0;
     for (int64_t j = 0; j <= R; ++j) {
         if (j == R || (j > 0 && fam[j] != fam[j - 1])) {
-            const double nk = (double)run / Rd;
-            Sf -= nk * log(nk);
+            const long double nk = (long double)run / (long double)R;
+            acc -= nk * logl(nk);
             ++f;
             run = 0;
             if (j == R) break;
         }
         ++run;
     }
+    const double Sf = (double)acc;
 
     out[0] = nd;
     out[1] = meanE;

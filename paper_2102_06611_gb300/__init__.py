@@ -94,6 +94,14 @@ class PopulationAnnealing:
         _check(self.lib, self.ctx, self.lib.pa_observables(self.ctx, ctypes.byref(o)))
         return o.as_dict()
 
+    def analyze(self, n_blocks: int = 100) -> dict:
+        """Blocked and jackknife errors of <E> and <|M|> over the tree-ordered population,
+        R_eff(E), R_eff(|M|), the jackknife error of C and the family entropy S_f with
+        rho_s = R / exp(S_f) (pa_analyze; synchronising)."""
+        out = _lib.pa_analysis()
+        _check(self.lib, self.ctx, self.lib.pa_analyze(self.ctx, int(n_blocks), ctypes.byref(out)))
+        return out.as_dict()
+
     def propose_schedule(self, alpha_target: float = 0.8, dbeta_max: float = 0.1, beta_final: float = 1.0):
         """Adaptive step: (beta_next, alpha) from overlap bisection on the current histogram."""
         b, a = ctypes.c_double(), ctypes.c_double()

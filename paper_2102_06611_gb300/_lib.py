@@ -54,6 +54,20 @@ class pa_obs(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class pa_analysis(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_longlong), ("families", ctypes.c_longlong), ("n_blocks", ctypes.c_int),
+                ("pad", ctypes.c_int), ("beta", ctypes.c_double),
+                ("mean_E", ctypes.c_double), ("var_E", ctypes.c_double), ("var_mean_E_jack", ctypes.c_double),
+                ("var_mean_E_blocked", ctypes.c_double), ("R_eff_E", ctypes.c_double),
+                ("mean_absM", ctypes.c_double), ("var_absM", ctypes.c_double),
+                ("var_mean_absM_jack", ctypes.c_double), ("var_mean_absM_blocked", ctypes.c_double),
+                ("R_eff_M", ctypes.c_double), ("C", ctypes.c_double), ("var_C_jack", ctypes.c_double),
+                ("S_f", ctypes.c_double), ("rho_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+
+
 class pa_sched_entry(ctypes.Structure):
     _fields_ = [("step", ctypes.c_longlong), ("beta", ctypes.c_double), ("dbeta", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("theta", ctypes.c_int), ("source", ctypes.c_int)]
@@ -84,6 +98,7 @@ SIGNATURES = {
     "pa_anneal_step": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pa_record": (ctypes.c_int, [_vp, _vp]),
     "pa_observables": (ctypes.c_int, [_vp, _P(pa_obs)]),
+    "pa_analyze": (ctypes.c_int, [_vp, ctypes.c_int, _P(pa_analysis)]),
     "pa_propose_schedule": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            _P(ctypes.c_double), _P(ctypes.c_double)]),
     "pa_schedule_log": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, _P(ctypes.c_longlong)]),

@@ -497,6 +497,27 @@ pa_status pa_observables(pa_ctx *c, pa_obs *host_out)
     return sync_and_check(c);
 }
 
+pa_status pa_analyze(pa_ctx *c, int n_blocks, pa_analysis *host_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!host_out || n_blocks < 2 || n_blocks > pa::kMaxAnaBlocks)
+        return fail(c, PA_ERR_INVALID_ARG, "n_blocks %d outside [2, %d]", n_blocks, pa::kMaxAnaBlocks);
+    DeviceGuard g(c->device);
+    if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
+    const long long R = read_R(c, false, &s);
+    if (s != PA_OK) return s;
+    if ((long long)n_blocks > R) return fail(c, PA_ERR_INVALID_ARG, "n_blocks %d above R_i = %lld", n_blocks, R);
+    cudaError_t e = pa::launch_analysis(c->st, cur_level(c), cur_mag(c), cur_fam(c), c->N, c->beta, n_blocks,
+                                        c->cfg.capacity, at<long long>(c, c->ws.ana_blk), at<int>(c, c->ws.ana_sizes),
+                                        at<pa_analysis>(c, c->ws.ana_out), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "analysis launch");
+    e = cudaMemcpyAsync(host_out, at<void>(c, c->ws.ana_out), sizeof(pa_analysis), cudaMemcpyDeviceToHost,
+                        c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "analysis copy");
+    return sync_and_check(c);
+}
+
 pa_status pa_sync(pa_ctx *c)
 {
     pa_status s = check_live(c);

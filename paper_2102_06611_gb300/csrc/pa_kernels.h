@@ -29,6 +29,9 @@ struct Workspace {
     size_t occ_t;       // double[N + 1]  overlap terms at a trial step
     size_t feat;        // float[32]      learned-schedule features (raw, standardised)
     size_t snap;        // int32[capacity] levels at the start of the temperature step
+    size_t ana_blk;     // int64[4 * kMaxAnaBlocks] analysis block sums
+    size_t ana_sizes;   // int32[capacity + 1]     family-size histogram (entry 0: largest size)
+    size_t ana_out;     // pa_analysis
     size_t total;
     long long nblk;     // blocks of the copy-count / copy kernels
 };
@@ -38,6 +41,7 @@ constexpr int kCountItems = 4;                              // parents per threa
 constexpr int kCountBlockItems = kCountThreads * kCountItems; // parents per block
 constexpr int kFamBlocks = 512;
 constexpr long long kStageReplicas = 4096;
+constexpr int kMaxAnaBlocks = 1024;
 
 Workspace plan_workspace(int L, long long capacity);
 
@@ -101,6 +105,11 @@ struct ObsArgs {
 };
 
 cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s);
+
+// Population analysis (pa_analysis.cu): block sums, family-size histogram, binary64 results.
+cudaError_t launch_analysis(const DevState *st, const int *level, const int *mag, const int *fam, int N,
+                            double beta, int n, long long capacity, long long *blk, int *sizes, pa_analysis *out,
+                            cudaStream_t s);
 
 // Adaptive temperature step: bisection on dbeta for the histogram overlap (see k_bisect).
 struct BisectArgs {

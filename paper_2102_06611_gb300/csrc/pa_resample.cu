@@ -50,6 +50,9 @@ Workspace plan_workspace(int L, long long capacity)
     w.occ_t = off;    off = align256(off + nlev * 8);
     w.feat = off;     off = align256(off + 32 * 4);
     w.snap = off;     off = align256(off + (size_t)capacity * 4);
+    w.ana_blk = off;  off = align256(off + (size_t)kMaxAnaBlocks * 4 * 8);
+    w.ana_sizes = off; off = align256(off + ((size_t)capacity + 1) * 4);
+    w.ana_out = off;  off = align256(off + sizeof(pa_analysis));
     w.total = off;
     w.nblk = nblk;
     return w;
