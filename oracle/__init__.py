@@ -83,6 +83,11 @@ def lib():
                 "orc_sweep_replica_t0": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                                 ctypes.c_uint32, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_int, i8p]),
+                "orc_heatbath_threshold": (ctypes.c_uint64, [ctypes.c_double]),
+                "orc_sweep_replica_u": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_uint32, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, i8p]),
+                "orc_pa_set_update": (None, [vp, ctypes.c_int]),
                 "orc_sweep_uniform": (ctypes.c_uint32, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                                         ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                                                         ctypes.c_int]),
@@ -189,13 +194,24 @@ def init_replica(L: int, seed: int, j: int) -> np.ndarray:
     return s
 
 
+METROPOLIS, HEATBATH = 0, 1
+
+
 def sweep_replica(L: int, seed: int, step: int, slot: int, beta: float, theta: int,
-                  s: np.ndarray, t0: int = 0) -> np.ndarray:
+                  s: np.ndarray, t0: int = 0, update: int = METROPOLIS) -> np.ndarray:
     """theta sweeps numbered t0 .. t0 + theta - 1 within temperature step `step`."""
     out = np.array(s, dtype=np.int8, copy=True).reshape(L * L)
-    lib().orc_sweep_replica_t0(L, seed, step, slot, float(beta), int(t0), int(theta),
-                               _ptr(out, ctypes.c_int8))
+    if update == METROPOLIS:
+        lib().orc_sweep_replica_t0(L, seed, step, slot, float(beta), int(t0), int(theta),
+                                   _ptr(out, ctypes.c_int8))
+    else:
+        lib().orc_sweep_replica_u(L, seed, step, slot, float(beta), int(t0), int(theta), int(update),
+                                  _ptr(out, ctypes.c_int8))
     return out
+
+
+def heatbath_threshold(y: float) -> int:
+    return int(lib().orc_heatbath_threshold(float(y)))
 
 
 def sweep_uniform(L: int, seed: int, step: int, slot: int, tag: int, r: int, p: int) -> int:
@@ -304,13 +320,15 @@ def analysis(N: int, beta: float, E, M, fam, n_blocks: int = 100) -> dict:
 class PA:
     """Plain single-threaded population annealing run (Sec. II steps 1-5)."""
 
-    def __init__(self, L: int, R: int, seed: int, kind: int = NEAREST, capacity: int | None = None):
+    def __init__(self, L: int, R: int, seed: int, kind: int = NEAREST, capacity: int | None = None,
+                 update: int = METROPOLIS):
         if capacity is None:
             capacity = default_capacity(R)
         self.L, self.N, self.R_target, self.capacity = L, L * L, R, capacity
         self._h = lib().orc_pa_create(L, R, capacity, seed, kind)
         if not self._h:
             raise ValueError("invalid oracle configuration")
+        lib().orc_pa_set_update(self._h, int(update))
 
     def __del__(self):
         h = getattr(self, "_h", None)

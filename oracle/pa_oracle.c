@@ -121,6 +121,19 @@ uint64_t orc_metropolis_threshold(double y)
     return (uint64_t)floor(p * 4294967296.0);
 }
 
+/* Heatbath (Sec. IV; for Ising spins the same as Glauber): a site with a aligned neighbours
+   flips with probability p_a = 1 / (1 + exp(beta dE)), dE = 4a - 8, so p_a + p_{4-a} = 1 and
+   p_2 = 1/2.  Reading: flip iff x < T_a with the 32-bit uniform x of the site and
+     T_3 = floor(p_3 2^32), T_4 = floor(p_4 2^32)          (p_3, p_4 <= 1/2),
+     T_1 = 2^32 - T_3,      T_0 = 2^32 - T_4,    T_2 = 2^31,
+   i.e. every p_a to 2^-32 and exactly complementary in pairs.  orc_heatbath_threshold(y)
+   is floor(2^32 / (1 + exp(y))) for y = 4 beta (T_3) or 8 beta (T_4). */
+uint64_t orc_heatbath_threshold(double y)
+{
+    double p = 1.0 / (1.0 + orc_exp(y));
+    return (uint64_t)floor(p * 4294967296.0);
+}
+
 /* ------------------------------------------------------------------------------------
  * Lattice helpers.  E = -sum over the 2N nearest-neighbour bonds of s_i s_j
  * (Eq. hamiltonian with J = 1), M = sum of spins.  The energy level is
@@ -246,6 +259,37 @@ uint32_t orc_sweep_uniform(int L, uint64_t seed, uint32_t step, uint32_t slot, i
     uint32_t low = philox_word(seed, (uint32_t)(64 * r + p), slot,
                                ((uint32_t)STREAM_REFINE << 28) | (uint32_t)tag, step, 0);
     return x | (low & 0xFFFFFFu);
+}
+
+/* update 0: Metropolis (above); update 1: heatbath (thresholds T_a of
+   orc_heatbath_threshold: every site draws its x and flips iff x < T_a). */
+void orc_sweep_replica_u(int L, uint64_t seed, uint32_t step, uint32_t slot, double beta,
+                         int t0, int theta, int update, int8_t *s)
+{
+    uint64_t T[5];
+    if (update == 1) {
+        T[3] = orc_heatbath_threshold(4.0 * beta);
+        T[4] = orc_heatbath_threshold(8.0 * beta);
+        T[2] = (uint64_t)1 << 31;
+        T[1] = ((uint64_t)1 << 32) - T[3];
+        T[0] = ((uint64_t)1 << 32) - T[4];
+    }
+    for (int t = t0; t < t0 + theta; ++t)
+        for (int q = 0; q < 2; ++q)
+            for (int r = 0; r < L; ++r)
+                for (int c = 0; c < L; ++c) {
+                    if (((r + c) & 1) != q) continue;
+                    int si = s[site(L, r, c)];
+                    int a = (s[site(L, r - 1, c)] == si) + (s[site(L, r + 1, c)] == si) +
+                            (s[site(L, r, c - 1)] == si) + (s[site(L, r, c + 1)] == si);
+                    uint32_t x = orc_sweep_uniform(L, seed, step, slot, 2 * t + q, r, c / 2);
+                    int flip;
+                    if (update == 1) flip = (uint64_t)x < T[a];
+                    else if (a <= 2) flip = 1;
+                    else if (a == 3) flip = (uint64_t)x < orc_metropolis_threshold(4.0 * beta);
+                    else flip = (uint64_t)x < orc_metropolis_threshold(8.0 * beta);
+                    if (flip) s[site(L, r, c)] = (int8_t)(-si);
+                }
 }
 
 void orc_sweep_replica_t0(int L, uint64_t seed, uint32_t step, uint32_t slot, double beta,
@@ -398,6 +442,7 @@ int orc_resample_levels(int L, int64_t R_target, int64_t R_prev, const int32_t *
  * ---------------------------------------------------------------------------------- */
 typedef struct {
     int L, N, kind;
+    int update;             /* 0 Metropolis, 1 heatbath */
     int64_t R_target, capacity, R;
     uint64_t seed;
     uint32_t step;          /* index i of the current temperature beta_i */
@@ -507,11 +552,13 @@ int orc_pa_resample(orc_pa *p, double beta_new)
 
 /* Step 3 then the measurement of step 4: theta sweeps of every replica at the current
    beta, then energies and magnetisations. */
+void orc_pa_set_update(orc_pa *p, int update) { p->update = update; }
+
 void orc_pa_sweep(orc_pa *p, int theta)
 {
     for (int64_t j = 0; j < p->R; ++j)
-        orc_sweep_replica_t0(p->L, p->seed, p->step, (uint32_t)j, p->beta, p->t_done, theta,
-                             p->s + (size_t)j * p->N);
+        orc_sweep_replica_u(p->L, p->seed, p->step, (uint32_t)j, p->beta, p->t_done, theta, p->update,
+                            p->s + (size_t)j * p->N);
     p->t_done += theta;
     p->theta_last = theta;
     measure_all(p);

@@ -150,14 +150,15 @@ def test_capacity_overflow_is_reported():
 
 
 @pytest.mark.slow
-def test_full_anneal_L4_matches_enumeration():
+@pytest.mark.parametrize("update", [oracle.METROPOLIS, oracle.HEATBATH])
+def test_full_anneal_L4_matches_enumeration(update):
     """A whole anneal at L=4 reproduces the exact ln Z (Sec. VII estimator), <E> and C
-    within a few standard errors."""
+    within a few standard errors, with the Metropolis and the heatbath update (Sec. IV)."""
     L, R, theta = 4, 20000, 5
     N = L * L
     g, _, _ = oracle.bruteforce(L)
     Ek = (4 * np.arange(N + 1) - 2 * N).astype(float)
-    pa = oracle.PA(L, R, seed=31)
+    pa = oracle.PA(L, R, seed=31, update=update)
     pa.init()
     for i in range(1, 21):
         beta = i / 20.0
@@ -178,10 +179,11 @@ def test_full_anneal_L4_matches_enumeration():
 
 
 @pytest.mark.slow
-def test_anneal_L8_against_kaufman():
+@pytest.mark.parametrize("update", [oracle.METROPOLIS, oracle.HEATBATH])
+def test_anneal_L8_against_kaufman(update):
     L, R, theta = 8, 5000, 10
     N = L * L
-    pa = oracle.PA(L, R, seed=1)
+    pa = oracle.PA(L, R, seed=1, update=update)
     pa.init()
     for i in range(1, 51):
         beta = i / 50.0

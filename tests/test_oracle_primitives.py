@@ -304,3 +304,55 @@ def test_specific_heat_peak_near_onsager_point():
     cs = [oracle.kaufman_thermo(64, b)[1] for b in bs]
     peak = bs[int(np.argmax(cs))]
     assert abs(peak - bc) < 0.01
+
+
+# ---------------------------------------------------------------------------- heatbath
+def test_heatbath_thresholds():
+    """T_3, T_4 = floor(2^32 / (1 + e^{4 beta})), floor(2^32 / (1 + e^{8 beta})) within the 1-ulp
+    exp; beta = 0 gives 2^31 (p = 1/2); the pairs T_a + T_{4-a} = 2^32 make the flip
+    probabilities of a and 4 - a complementary, and T_a / T_{4-a} = e^{-beta dE_a} is
+    detailed balance of the heatbath rule (Sec. IV)."""
+    getcontext().prec = 60
+    assert oracle.heatbath_threshold(0.0) == 2 ** 31
+    for beta in [0.05, 0.2, 0.4406867935097715, 0.9, 2.0]:
+        T3, T4 = oracle.heatbath_threshold(4 * beta), oracle.heatbath_threshold(8 * beta)
+        for T, y in ((T3, 4 * beta), (T4, 8 * beta)):
+            exact = Decimal(2) ** 32 / (1 + Decimal(y).exp())
+            assert abs(Decimal(T) - exact) <= 1
+        T1, T0 = 2 ** 32 - T3, 2 ** 32 - T4
+        # exact up to the floor of T_3, T_4 (one unit in the numerator)
+        assert abs(T3 / T1 - math.exp(-4 * beta)) <= 2 / T1
+        assert abs(T4 / T0 - math.exp(-8 * beta)) <= 2 / T0
+
+
+@pytest.mark.parametrize("beta", [0.25, 0.4406867935097715, 0.7])
+def test_heatbath_sweep_samples_boltzmann_distribution_L4(beta):
+    """Long checkerboard heatbath chains at L=4 reproduce the exact level distribution from
+    enumeration (chi-square with a 6 sigma cut)."""
+    L, seed, reps, blocks, theta = 4, 23, 400, 30, 6
+    counts = np.zeros(17)
+    for j in range(reps):
+        s = oracle.init_replica(L, seed, j)
+        for blk in range(1, blocks + 1):
+            s = oracle.sweep_replica(L, seed, blk, j, beta, theta, s, update=oracle.HEATBATH)
+            E, _ = oracle.energy_mag(L, s)
+            counts[(E + 32) // 4] += 1
+    p = _exact_level_distribution(beta)
+    n = counts.sum()
+    mask = p * n > 5
+    chi2 = np.sum((counts[mask] - n * p[mask]) ** 2 / (n * p[mask]))
+    dof = mask.sum() - 1
+    assert chi2 < dof + 6 * math.sqrt(2 * dof), (chi2, dof)
+
+
+def test_heatbath_at_beta_zero_is_a_fair_coin_per_site():
+    """At beta = 0 every site flips with probability 1/2 (x < 2^31: the top bit of its
+    uniform), so one sweep flips about half the spins, unlike Metropolis which flips all."""
+    L = 16
+    s = oracle.init_replica(L, 3, 0)
+    flips = 0
+    for step in range(1, 41):
+        t = oracle.sweep_replica(L, 3, step, 0, 0.0, 1, s, update=oracle.HEATBATH)
+        flips += int((t != s).sum())
+    n = 40 * L * L
+    assert abs(flips / n - 0.5) < 5 * math.sqrt(0.25 / n)
