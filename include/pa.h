@@ -55,6 +55,17 @@ typedef enum {
     PA_RESAMPLE_POISSON = 1  /* r_j ~ Poisson(tau_hat_j), fluctuating population size */
 } pa_resample_kind;
 
+/* Spin update of step 3 (Sec. IV).  With a aligned neighbours, dE = 4a - 8 and x the site's
+   uniform 32-bit integer:
+     Metropolis  a <= 2 flips; a = 3, 4 flip iff x < floor(e^{-beta dE} 2^32);
+     heatbath    flip iff x < T_a, T_3 = floor(2^32 / (1 + e^{4 beta})),
+                 T_4 = floor(2^32 / (1 + e^{8 beta})), T_1 = 2^32 - T_3, T_0 = 2^32 - T_4,
+                 T_2 = 2^31 (flip probability 1 / (1 + e^{beta dE}) to 2^-32). */
+typedef enum {
+    PA_UPDATE_METROPOLIS = 0,
+    PA_UPDATE_HEATBATH = 1
+} pa_update_kind;
+
 /* Run configuration.  L must be one of 4, 8, 12, 16, 24, 32, 48, 64, 128.
    1 <= R <= capacity <= 2^31 - 1.  beta_0 is always 0 (simple sampling, Sec. II). */
 typedef struct {
@@ -63,6 +74,8 @@ typedef struct {
     long long R;                 /* target population size R (Eq. taus) */
     long long capacity;          /* replicas each buffer can hold (>= R) */
     unsigned long long seed;     /* Philox key */
+    int update;                  /* pa_update_kind (batches: Metropolis only) */
+    int pad;                     /* 0 */
 } pa_config;
 
 /* Byte sizes of the caller-owned device buffers for a configuration.

@@ -42,16 +42,18 @@ class PopulationAnnealing:
     """One population-annealing run on one GPU (device buffers owned by this object)."""
 
     def __init__(self, L: int, R: int, seed: int, resample: str = "nearest", capacity: int | None = None,
-                 device: str | torch.device | None = None, stream: torch.cuda.Stream | None = None):
+                 device: str | torch.device | None = None, stream: torch.cuda.Stream | None = None,
+                 update: str = "metropolis"):
         self.lib = _lib.lib()
         self.L, self.N, self.R_target = int(L), int(L) * int(L), int(R)
         self.capacity = int(capacity if capacity is not None else default_capacity(R))
         self.seed = int(seed)
         kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON}[resample]
+        upd = {"metropolis": _lib.PA_UPDATE_METROPOLIS, "heatbath": _lib.PA_UPDATE_HEATBATH}[update]
         self.device = torch.device(device if device is not None else "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.cfg = _lib.pa_config(L=self.L, resample=kind, R=self.R_target, capacity=self.capacity,
-                                  seed=self.seed)
+                                  seed=self.seed, update=upd)
         sizes = _lib.pa_sizes()
         _check(self.lib, None, self.lib.pa_query_sizes(ctypes.byref(self.cfg), ctypes.byref(sizes)))
         self.sizes = sizes

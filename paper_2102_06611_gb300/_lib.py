@@ -18,6 +18,7 @@ _lib = None
 STATUS_NAMES = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_STATE", 3: "PA_ERR_CAPACITY",
                 4: "PA_ERR_CUDA", 5: "PA_ERR_TIMEOUT", 6: "PA_ERR_NUMERIC", 7: "PA_ERR_TOO_LARGE"}
 PA_RESAMPLE_NEAREST, PA_RESAMPLE_POISSON = 0, 1
+PA_UPDATE_METROPOLIS, PA_UPDATE_HEATBATH = 0, 1
 
 
 class PAError(RuntimeError):
@@ -28,7 +29,8 @@ class PAError(RuntimeError):
 
 class pa_config(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("resample", ctypes.c_int), ("R", ctypes.c_longlong),
-                ("capacity", ctypes.c_longlong), ("seed", ctypes.c_ulonglong)]
+                ("capacity", ctypes.c_longlong), ("seed", ctypes.c_ulonglong), ("update", ctypes.c_int),
+                ("pad", ctypes.c_int)]
 
 
 class pa_sizes(ctypes.Structure):

@@ -132,6 +132,8 @@ pa_status pa_query_sizes(const pa_config *cfg, pa_sizes *out)
     if (!supported_L(cfg->L) || cfg->R < 1 || cfg->capacity < cfg->R || cfg->capacity > 2147483647LL)
         return PA_ERR_INVALID_ARG;
     if (cfg->resample != PA_RESAMPLE_NEAREST && cfg->resample != PA_RESAMPLE_POISSON) return PA_ERR_INVALID_ARG;
+    if ((cfg->update != PA_UPDATE_METROPOLIS && cfg->update != PA_UPDATE_HEATBATH) || cfg->pad != 0)
+        return PA_ERR_INVALID_ARG;
     const pa::Workspace ws = pa::plan_workspace(cfg->L, cfg->capacity);
     out->bytes_per_replica = (size_t)pa::bytes_per_replica(cfg->L);
     out->spin_bytes = out->bytes_per_replica * (size_t)cfg->capacity;
@@ -174,7 +176,7 @@ pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_
         delete c;
         return PA_ERR_CUDA;
     }
-    e = pa::launch_setup(c->st, cfg->R, at<int>(c, c->ws.hist), c->N, c->stream);
+    e = pa::launch_setup(c->st, cfg->R, at<int>(c, c->ws.hist), c->N, cfg->update, c->stream);
     if (e == cudaSuccess) {
         pa::SweepArgs a{};
         a.spins = buf->spins[0];
@@ -277,6 +279,7 @@ static pa_status sweep_and_measure(pa_ctx *c, int theta)
     a.step = (unsigned int)c->step;
     a.t0 = c->sweeps_in_step;
     a.theta = theta;
+    a.update = c->cfg.update;
     e = pa::launch_sweep(c->cfg.L, false, a, c->num_sms, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->measured = true;
@@ -673,7 +676,7 @@ pa_status pa_save(pa_ctx *c, void *host_buf, size_t n)
     char *p = static_cast<char *>(host_buf);
     CkptHeader h{};
     h.magic = kCkptMagic;
-    h.version = 1;
+    h.version = 2;
     h.cfg = c->cfg;
     h.step = c->step;
     h.R_cur = R;
@@ -713,7 +716,7 @@ pa_status pa_load(pa_ctx *c, const void *host_buf, size_t n)
     if (!host_buf || n < sizeof(CkptHeader)) return PA_ERR_INVALID_ARG;
     CkptHeader h;
     std::memcpy(&h, host_buf, sizeof(h));
-    if (h.magic != kCkptMagic || h.version != 1) return fail(c, PA_ERR_INVALID_ARG, "not a checkpoint");
+    if (h.magic != kCkptMagic || h.version != 2) return fail(c, PA_ERR_INVALID_ARG, "not a checkpoint");
     if (std::memcmp(&h.cfg, &c->cfg, sizeof(pa_config)) != 0)
         return fail(c, PA_ERR_INVALID_ARG, "checkpoint of a different configuration");
     if (h.R_cur < 1 || h.R_cur > c->cfg.capacity || h.R_prev < 0 || h.R_prev > c->cfg.capacity || h.n_log < 0 ||

@@ -79,7 +79,8 @@ Tables layout_tables(int n)
 bool valid_desc(const pa_run_desc &d)
 {
     return batch_supported_L(d.cfg.L) && d.cfg.R >= 1 && d.cfg.capacity >= d.cfg.R &&
-           d.cfg.capacity <= 2147483647LL && (d.cfg.resample == PA_RESAMPLE_NEAREST ||
+           d.cfg.capacity <= 2147483647LL && d.cfg.update == PA_UPDATE_METROPOLIS && d.cfg.pad == 0 &&
+           (d.cfg.resample == PA_RESAMPLE_NEAREST ||
                                               d.cfg.resample == PA_RESAMPLE_POISSON) &&
            d.n_temps >= 2 && d.theta >= 0 && d.theta <= (1 << 26);
 }
@@ -220,7 +221,8 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
         state[(size_t)i].beta = 0.0;
         state[(size_t)i].beta_prev = 0.0;
         // step 1 (simple sampling at beta_0 = 0) and the first measurement
-        e = pa::launch_setup(st, d.cfg.R, reinterpret_cast<int *>(work + L.ws.hist), d.cfg.L * d.cfg.L, b->user);
+        e = pa::launch_setup(st, d.cfg.R, reinterpret_cast<int *>(work + L.ws.hist), d.cfg.L * d.cfg.L,
+                             PA_UPDATE_METROPOLIS, b->user);
         if (e == cudaSuccess) {
             pa::SweepArgs s = r.sw[0];
             s.R_init = d.cfg.R;

@@ -158,6 +158,13 @@ __device__ __forceinline__ unsigned long long metropolis_threshold(double y)
     return (unsigned long long)floor(__dmul_rn(p, 4294967296.0));
 }
 
+// floor(2^32 / (1 + exp(y))): the heatbath thresholds T_3 (y = 4 beta) and T_4 (y = 8 beta).
+__device__ __forceinline__ unsigned long long heatbath_threshold(double y)
+{
+    double p = __ddiv_rn(1.0, __dadd_rn(1.0, det_exp(y)));
+    return (unsigned long long)floor(__dmul_rn(p, 4294967296.0));
+}
+
 // ------------------------------------------------------------------------------------
 // Device state block (first bytes of the workspace).
 // ------------------------------------------------------------------------------------
@@ -188,7 +195,7 @@ struct DevState {
     // after the last sweep call (k1): sum k0, k0^2, k1, k1^2, k0 k1 (exact)
     long long c0, c00, c1, c11, c01;
     int theta;
-    int pad;
+    int update;               // pa_update_kind of the run (selects the thresholds below)
 };
 
 __device__ __forceinline__ void set_error(DevState *st, int code)

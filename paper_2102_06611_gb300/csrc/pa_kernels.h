@@ -59,9 +59,12 @@ struct SweepArgs {
     unsigned int step;      // temperature index i
     int t0;                 // sweeps already done at this step (sweep numbering offset)
     int theta;
+    int update;             // pa_update_kind (the init kernel ignores it)
 };
 
 cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s);
+// the heatbath sweep (pa_sweep_hb.cu); launch_sweep forwards to it for a.update = heatbath
+cudaError_t launch_sweep_hb(int L, const SweepArgs &a, int num_sms, cudaStream_t s);
 
 struct ResampleArgs {
     int L;
@@ -90,7 +93,7 @@ cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s);
 cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s);
 cudaError_t launch_thresholds(DevState *st, double beta, cudaStream_t s);
 cudaError_t launch_zero_measure(DevState *st, int *hist, int N, cudaStream_t s);
-cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, cudaStream_t s);
+cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, int update, cudaStream_t s);
 
 struct ObsArgs {
     int L;

@@ -104,22 +104,29 @@ __device__ __forceinline__ T block_sum(T v)
     return t;  // valid in thread 0
 }
 
+// Thresholds of the run's spin update at beta: Metropolis floor(e^{-4 beta} 2^32),
+// floor(e^{-8 beta} 2^32); heatbath T_3 = floor(2^32 / (1 + e^{4 beta})), T_4 likewise with 8 beta.
 __device__ __forceinline__ void set_thresholds(DevState *st, double beta)
 {
-    const unsigned long long t4 = metropolis_threshold(__dmul_rn(4.0, beta));
-    const unsigned long long t8 = metropolis_threshold(__dmul_rn(8.0, beta));
-    st->T4 = t4;
-    st->T8 = t8;
+    const double y4 = __dmul_rn(4.0, beta), y8 = __dmul_rn(8.0, beta);
+    if (st->update == PA_UPDATE_HEATBATH) {
+        st->T4 = heatbath_threshold(y4);
+        st->T8 = heatbath_threshold(y8);
+    } else {
+        st->T4 = metropolis_threshold(y4);
+        st->T8 = metropolis_threshold(y8);
+    }
 }
 
 // ------------------------------------------------------------------------------ setup
-__global__ void k_setup(DevState *st, long long R, int *hist, int nlev)
+__global__ void k_setup(DevState *st, long long R, int *hist, int nlev, int update)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevState z{};
         *st = z;
         st->R_cur = R;
         st->R_prev = 0;
+        st->update = update;
         set_thresholds(st, 0.0);
     }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlev; k += gridDim.x * blockDim.x) hist[k] = 0;
@@ -152,10 +159,10 @@ cudaError_t launch_thresholds(DevState *st, double beta, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, cudaStream_t s)
+cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, int update, cudaStream_t s)
 {
     const int nlev = N + 1;
-    k_setup<<<(nlev + 1023) / 1024, 1024, 0, s>>>(st, R, hist, nlev);
+    k_setup<<<(nlev + 1023) / 1024, 1024, 0, s>>>(st, R, hist, nlev, update);
     return cudaGetLastError();
 }
 

@@ -110,7 +110,7 @@ extern "C" pa_status pa_copy_numbers_static(int L, long long R_target, long long
     const int N = L * L;
 
     // clears the state block and the histogram, and sets R_{i-1} = R_prev
-    cudaError_t e = launch_setup(st, R_prev, hist, N, s);
+    cudaError_t e = launch_setup(st, R_prev, hist, N, PA_UPDATE_METROPOLIS, s);
     if (e != cudaSuccess) return PA_ERR_CUDA;
     const unsigned int blocks = (unsigned int)((R_prev + 255) / 256 < 4096 ? (R_prev + 255) / 256 : 4096);
     k_static_levels<<<blocks, 256, 0, s>>>(level_dev, R_prev, N, hist, st);

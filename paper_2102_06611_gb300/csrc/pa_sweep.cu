@@ -1,165 +1,17 @@
-// pa_sweep.cu -- the sweep kernels of a single run: step 1 (simple-sampling initialisation)
-// and step 3 (theta checkerboard Metropolis sweeps), each fused with the measurement; the
-// device routines they use are in pa_sweep.cuh.
+// pa_sweep.cu -- the sweep kernels of a single run with the Metropolis update: step 1
+// (simple-sampling initialisation) and step 3 (theta checkerboard sweeps), each fused with
+// the measurement (the kernel template is in pa_sweep.cuh; heatbath instantiations are in
+// pa_sweep_hb.cu), and the persistent sweep kernel of batches.
 #include "pa_sweep.cuh"
 
 namespace pa {
 
-template <int L, bool INIT>
-__global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_sweep(SweepArgs a)
-{
-    using Gm = Geo<L>;
-    using W = typename Gm::W;
-    constexpr int N = Gm::N, G = Gm::G, RPW = Gm::RPW, RPL = Gm::RPL;
-    extern __shared__ int sh_hist[];
-
-    for (int k = threadIdx.x; k <= N; k += blockDim.x) sh_hist[k] = 0;
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31;
-    const int q = lane & (G - 1);
-    const int sub = lane / G;
-    const int r0 = q * RPL;
-    const long long R = INIT ? a.R_init : a.st->R_cur;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-
-    unsigned int rk0[10], rk1[10];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
-        rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
-    }
-    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
-
-    // per-block exact sums: |M|, M^2, and the levels at the step start (0) and now (1):
-    // k0, k0^2, k1, k1^2, k0 k1
-    __shared__ unsigned long long sh_sum[7];
-    if (threadIdx.x < 7) sh_sum[threadIdx.x] = 0;
-    __syncthreads();
-    W *spins = reinterpret_cast<W *>(a.spins);
-    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp; 8 warps per block
-    __shared__ W tq_eq[8 * TQ], tq_a4[8 * TQ];
-    __shared__ unsigned int tq_code[8 * TQ];
-    const int wib = threadIdx.x >> 5;
-    const TieQueue<W> tq{tq_eq + wib * TQ, tq_a4 + wib * TQ, tq_code + wib * TQ};
-
-    for (long long base = warp * RPW; base < R; base += nwarps * RPW) {
-        const long long j = base + sub;
-        const bool active = j < R;
-        W A[RPL], B[RPL];
-        W *rep = spins + (size_t)(active ? j : 0) * (2 * L);
-        if (INIT) {
-            init_rows<L>((unsigned int)j, r0, a.k0, a.k1, A, B);
-        } else {
-            if (active) load_rows<L>(rep, r0, A, B);
-            else {
-#pragma unroll
-                for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
-            }
-        }
-        sweep_rows<L>(A, B, r0, lane, (unsigned int)j, (unsigned int)base, a.t0, a.theta, a.step, rk0, rk1, a.k0,
-                      a.k1, ac, tq);
-        int anti, ups;
-        measure_rows<L>(A, B, r0, lane, anti, ups);
-        anti = group_sum<G>(anti);
-        ups = group_sum<G>(ups);
-        // exact sums of this group of replicas: |M|, M^2, k0, k0^2, k1, k1^2, k0 k1
-        unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
-        int level = -1;
-        if (active) {
-            if (INIT || a.theta > 0) store_rows<L>(rep, r0, A, B);
-            if (q == 0) {
-                level = anti >> 1;
-                const int M = 2 * ups - N;
-                if (!INIT) {
-                    // level at the start of this temperature step (right after resampling),
-                    // kept in level_snap by the step's first call
-                    const unsigned long long k0 = (unsigned long long)(a.t0 == 0 ? a.level[j] : a.level_snap[j]);
-                    const unsigned long long k1 = (unsigned long long)level;
-                    if (a.t0 == 0) a.level_snap[j] = (int)k0;
-                    v[2] = k0;
-                    v[3] = k0 * k0;
-                    v[4] = k1;
-                    v[5] = k1 * k1;
-                    v[6] = k0 * k1;
-                }
-                a.level[j] = level;
-                a.mag[j] = M;
-                if (INIT) a.fam[j] = (int)j;
-                v[0] = (unsigned long long)(M < 0 ? -M : M);
-                v[1] = (unsigned long long)((long long)M * M);
-            }
-        }
-        constexpr int NSUM = INIT ? 2 : 7;
-        if constexpr (RPW >= 8) {
-            // many replicas per warp: reduce over the warp first, and count equal levels once
-            const unsigned int grp = __match_any_sync(0xffffffffu, level);
-            if (level >= 0 && lane == __ffs((int)grp) - 1) atomicAdd(&sh_hist[level], __popc(grp));
-#pragma unroll
-            for (int i = 0; i < NSUM; ++i)
-#pragma unroll
-                for (int o = 16; o >= G; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-            if (lane == 0)
-#pragma unroll
-                for (int i = 0; i < NSUM; ++i) atomicAdd(&sh_sum[i], v[i]);
-        } else if (level >= 0) {
-            atomicAdd(&sh_hist[level], 1);
-#pragma unroll
-            for (int i = 0; i < NSUM; ++i) atomicAdd(&sh_sum[i], v[i]);
-        }
-    }
-
-    // one global atomic per block and sum
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&a.st->sum_absM, sh_sum[0]);
-        atomicAdd(&a.st->sum_M2, sh_sum[1]);
-        if (!INIT) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), sh_sum[2]);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), sh_sum[3]);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), sh_sum[4]);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), sh_sum[5]);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), sh_sum[6]);
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k <= N; k += blockDim.x) {
-        const int v = sh_hist[k];
-        if (v) atomicAdd(&a.hist[k], v);
-    }
-}
-
-template <int L, bool INIT>
-static cudaError_t launch_sweep_t(const SweepArgs &a, int num_sms, cudaStream_t s)
-{
-    constexpr int N = Geo<L>::N;
-    const size_t smem = (size_t)(N + 1) * sizeof(int);
-    static int blocks_per_sm = 0;  // occupancy of this instantiation, queried once
-    if (blocks_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep<L, INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep<L, INIT>, 256, smem);
-        if (e != cudaSuccess) return e;
-        blocks_per_sm = b > 0 ? b : 1;
-    }
-    const long long R = a.R_bound;
-    const long long groups = (R + Geo<L>::RPW - 1) / Geo<L>::RPW;  // warps needed
-    long long blocks = (groups + 7) / 8;
-    const long long cap = (long long)num_sms * blocks_per_sm;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_sweep<L, INIT><<<(unsigned int)blocks, 256, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s)
 {
+    if (!init && a.update == PA_UPDATE_HEATBATH) return launch_sweep_hb(L, a, num_sms, s);
 #define PA_SWEEP_CASE(LL)                                                                      \
     case LL:                                                                                   \
-        return init ? launch_sweep_t<LL, true>(a, num_sms, s) : launch_sweep_t<LL, false>(a, num_sms, s);
+        return init ? launch_sweep_t<LL, true, false>(a, num_sms, s) : launch_sweep_t<LL, false, false>(a, num_sms, s);
     switch (L) {
         PA_SWEEP_CASE(4)
         PA_SWEEP_CASE(8)
@@ -209,8 +61,8 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
 #pragma unroll
         for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
     }
-    const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), tq_code};
-    sweep_rows<L>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, a.k0, a.k1,
+    const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), nullptr, tq_code};
+    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, a.k0, a.k1,
                   ac, tq);
     int anti, ups;
     measure_rows<L>(A, B, r0, lane, anti, ups);

@@ -319,6 +319,45 @@ __device__ __forceinline__ void compare_planes(const W *plane, W all4, W eq3, W 
     eq = e;
 }
 
+// Heatbath (Sec. IV): every site draws; with A = 4 - a antiparallel neighbours the classes
+// are c04 (A = 0 or 4: threshold T_4, x for A = 0 / ~x for A = 4), c13 (A = 1 or 3:
+// threshold T_3), clow (A >= 3, the sites that compare ~x) and c2 (A = 2: flip iff the top
+// bit of x is 0, x < 2^31).  With pair masks z = y_1 | y_2, x = y_1 ^ y_2, d = y_1 & y_2 of
+// y_n = s ^ n: A = 0 is ~z12 & ~z34, A = 4 is d12 & d34, A >= 3 is (d12 & z34) | (x12 & d34),
+// A = 2 is (d12 & ~z34) | (x12 & x34) | (~z12 & d34).
+template <typename W>
+__device__ __forceinline__ void classify_hb(W s, W up, W dn, W ha, W hb, W valid, W &c04, W &clow, W &c2)
+{
+    const W y1 = s ^ up, y2 = s ^ dn, y3 = s ^ ha, y4 = s ^ hb;
+    const W z12 = y1 | y2, x12 = up ^ dn, d12 = y1 & y2;
+    const W z34 = y3 | y4, x34 = ha ^ hb, d34 = y3 & y4;
+    c04 = ((~z12 & ~z34) | (d12 & d34)) & valid;
+    clow = ((d12 & z34) | (x12 & d34)) & valid;
+    c2 = ((d12 & ~z34) | (x12 & x34) | (~z12 & d34)) & valid;
+}
+
+// The heatbath decision from the 8 planes: x' = x (A <= 1) or ~x (A >= 3) against T (T_4 for
+// c04, T_3 otherwise) by the borrow chain; a site flips iff x' < T for A <= 1 and iff
+// x' >= T (~x >= T, i.e. x < 2^32 - T) for A >= 3; A = 2 flips iff plane 0 (bit 31 of x) is 0.
+// flip = the decided flips (for ties x'_top = T_top it holds the decision for x'_low >= T_low,
+// which the tie resolution toggles where x'_low < T_low), eq = the ties.
+template <typename W>
+__device__ __forceinline__ void compare_planes_hb(const W *plane, W c04, W clow, W c2, W valid, const Accept<W> &ac,
+                                                  W &flip, W &eq)
+{
+    W l = 0, e = ~c2 & valid;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        const W tm = (c04 & ac.m8[k]) | (~c04 & ac.m4[k]);
+        const W pp = plane[k] ^ clow;
+        const W np = ~pp;
+        l = (np & tm) | (np & l) | (tm & l);
+        e &= ~(pp ^ tm);
+    }
+    flip = ((c2 & ~plane[0]) | (~c2 & (l ^ clow))) & valid;
+    eq = e;
+}
+
 // ------------------------------------------------------------------------------------
 // Ties x_top = T_top are rare (2^-8 per site) but land on few lanes of a warp, so a loop in
 // which every lane resolves its own ties runs as many Philox passes as the busiest lane has
@@ -330,7 +369,8 @@ __device__ __forceinline__ void compare_planes(const W *plane, W all4, W eq3, W 
 template <typename W>
 struct TieQueue {
     W *eq;              // tie mask of the entry's word (overwritten with the accept mask)
-    W *a4;              // class-4 mask of the word
+    W *a4;              // sites compared with the second threshold (class 4 / heatbath c04)
+    W *inv;             // heatbath: sites that compare the complemented low bits (else unused)
     unsigned int *code; // owner lane << 4 | word index
 };
 
@@ -339,11 +379,14 @@ struct TieSite {
     int r, j;           // row and position within the colour's half-row
 };
 
-template <int NW, typename W, typename SiteOf>
-__device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, int lane, const TieQueue<W> &q,
-                                             SiteOf site_of, unsigned int tag, unsigned int step,
-                                             const unsigned int *rk0, const unsigned int *rk1, unsigned int low4,
-                                             unsigned int low8)
+// For entry t the accept mask has bit b set iff x_low < thr (low8 where a4 is set, else
+// low4), with x_low the low 24 bits of the site's refinement draw, complemented where inv is
+// set (heatbath, HB).  The owners XOR it into `flip` (zero at the ties for Metropolis).
+template <int NW, bool HB, typename W, typename SiteOf>
+__device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, const W *inv, W *flip, int lane,
+                                             const TieQueue<W> &q, SiteOf site_of, unsigned int tag,
+                                             unsigned int step, const unsigned int *rk0, const unsigned int *rk1,
+                                             unsigned int low4, unsigned int low8)
 {
     static_assert(NW <= 15, "word index is 4 bits of the entry code");
     const unsigned int below = (1u << lane) - 1u;
@@ -357,6 +400,7 @@ __device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, in
         if (eq[i] != W(0)) {
             q.eq[pos[i]] = eq[i];
             q.a4[pos[i]] = a4[i];
+            if constexpr (HB) q.inv[pos[i]] = inv[i];
             q.code[pos[i]] = ((unsigned int)lane << 4) | (unsigned int)i;
         }
         total += __popc(b);
@@ -366,6 +410,8 @@ __device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, in
     for (int t = lane; t < total; t += 32) {
         W w = q.eq[t];
         const W a = q.a4[t];
+        W v = 0;
+        if constexpr (HB) v = q.inv[t];
         const unsigned int code = q.code[t];
         W acc = 0;
         while (w) {
@@ -374,7 +420,9 @@ __device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, in
             const uint4 x = philox_rk(make_uint4((unsigned int)(64 * s.r + s.j), s.slot, (kStreamRefine << 28) | tag,
                                                  step), rk0, rk1);
             const unsigned int thr = ((a >> b) & W(1)) ? low8 : low4;
-            if ((x.x & 0xFFFFFFu) < thr) acc |= W(1) << b;
+            unsigned int xl = x.x & 0xFFFFFFu;
+            if (HB && ((v >> b) & W(1))) xl ^= 0xFFFFFFu;
+            if (xl < thr) acc |= W(1) << b;
             w &= w - W(1);
         }
         q.eq[t] = acc;
@@ -382,7 +430,7 @@ __device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, in
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < NW; ++i)
-        if (eq[i] != W(0)) lt[i] |= q.eq[pos[i]];
+        if (eq[i] != W(0)) flip[i] ^= q.eq[pos[i]];
 }
 
 // One colour (compile-time Q) of one sweep over the rows a lane holds (sizes L >= 48).
@@ -394,7 +442,7 @@ __device__ __forceinline__ void resolve_ties(const W *eq, const W *a4, W *lt, in
 // k mod 4 of Philox(ctr = (2 (nh r + h) + k / 4, slot, SWEEP << 28 | tag, i)) for the 32-site
 // chunk h of the half-row (nh = chunks per half-row); the low part of site j is the low 24
 // bits of word 0 of Philox(ctr = (64 r + j, slot, REFINE << 28 | tag, i)), tag = 2t + Q.
-template <int L, int Q>
+template <int L, int Q, bool HB>
 __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L>::W *B, int r0,
                                            int lane, unsigned int slot, unsigned int slot0, unsigned int tag,
                                            unsigned int step, const unsigned int *rk0,
@@ -419,6 +467,7 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
     // the plane stream's calls differ only in c0 (rounds 1 and 2 partly shared)
     const PhiloxC0 pc = philox_c0_setup(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
 
+    // Metropolis: lt = decided accepts, g3 = sites with a >= 3; heatbath: lt = flip, g3 = clow
     W lt[RPL], eq[RPL], a4[RPL], g3[RPL];
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
@@ -428,8 +477,9 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
         // the updated half is the even-column half iff (r + Q) is even
         const bool even_half = ((r + Q) & 1) == 0;
         const W hb = even_half ? rot_up<W, H>(O[i]) : rot_down<W, H>(O[i]);
-        W all4, eq3, ge3;
-        classify<XNOR>(T[i], up, dn, O[i], hb, half_mask<W, H>(), all4, eq3, ge3);
+        W all4, eq3, ge3, c2;
+        if constexpr (HB) classify_hb(T[i], up, dn, O[i], hb, half_mask<W, H>(), all4, ge3, c2);
+        else classify<XNOR>(T[i], up, dn, O[i], hb, half_mask<W, H>(), all4, eq3, ge3);
 
         // bit planes of the top 8 bits of every site's uniform
         W plane[8];
@@ -448,7 +498,8 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
 #pragma unroll
             for (int k = 0; k < 8; ++k) plane[k] = (W)lo[k] | ((W)hi[k] << 32);
         }
-        compare_planes<XNOR>(plane, all4, eq3, ge3, ac, lt[i], eq[i]);
+        if constexpr (HB) compare_planes_hb(plane, all4, ge3, c2, half_mask<W, H>(), ac, lt[i], eq[i]);
+        else compare_planes<XNOR>(plane, all4, eq3, ge3, ac, lt[i], eq[i]);
         a4[i] = all4;
         g3[i] = ge3;
     }
@@ -456,13 +507,16 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
     // rare: the low 24 bits decide the sites whose top 8 bits equal the threshold's
     static_assert(SweepStyle<L>::TIE_QUEUE, "row-wise sizes hold 3 or more words per lane");
     (void)slot;
-    resolve_ties<RPL>(eq, a4, lt, lane, tq,
-                      [&](int src, int i, int b) {
-                          return TieSite{slot0 + (unsigned int)(src / G), (src & (G - 1)) * RPL + i, b};
-                      },
-                      tag, step, rk0, rk1, ac.low4, ac.low8);
+    resolve_ties<RPL, HB>(eq, a4, g3, lt, lane, tq,
+                          [&](int src, int i, int b) {
+                              return TieSite{slot0 + (unsigned int)(src / G), (src & (G - 1)) * RPL + i, b};
+                          },
+                          tag, step, rk0, rk1, ac.low4, ac.low8);
 #pragma unroll
-    for (int i = 0; i < RPL; ++i) T[i] ^= (~g3[i] | lt[i]) & half_mask<W, H>();
+    for (int i = 0; i < RPL; ++i) {
+        if constexpr (HB) T[i] ^= lt[i];
+        else T[i] ^= (~g3[i] | lt[i]) & half_mask<W, H>();
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -550,7 +604,7 @@ __device__ __forceinline__ void packed_planes(int r0, unsigned int slot, unsigne
 //
 // With PRE the planes come in `plane` (drawn by packed_planes); otherwise they are drawn
 // here, chunk by chunk.
-template <int L, int Q, bool PRE>
+template <int L, int Q, bool PRE, bool HB>
 __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB, const unsigned int (*plane)[8],
                                               int r0, int lane, unsigned int slot, unsigned int slot0,
                                               unsigned int tag, unsigned int step, const unsigned int *rk0,
@@ -599,28 +653,35 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
         const unsigned int ru = ((o << 1) & ~LSBF) | ((o >> (H - 1)) & LSBF);  // site j <- j - 1
         const unsigned int rd = ((o >> 1) & ~MSBF) | ((o << (H - 1)) & MSBF);  // site j <- j + 1
         const unsigned int hb = (ru & SEL_UP) | (rd & ~SEL_UP);
-        unsigned int all4, eq3, ge3;
-        classify<XNOR>(T[c], up, dn, o, hb, Mk::VALID, all4, eq3, ge3);
+        // Metropolis: lt = decided accepts, g3 = sites with a >= 3; heatbath: lt = flip,
+        // all4 = c04, g3 = clow
+        unsigned int all4, eq3, ge3, c2;
+        if constexpr (HB) classify_hb(T[c], up, dn, o, hb, Mk::VALID, all4, ge3, c2);
+        else classify<XNOR>(T[c], up, dn, o, hb, Mk::VALID, all4, eq3, ge3);
+        unsigned int pl[8];
         if constexpr (PRE) {
-            compare_planes<XNOR>(plane[c], all4, eq3, ge3, ac, lt[c], eq[c]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) pl[k] = plane[c][k];
         } else {
             const unsigned int ch = (unsigned int)(r0 / P + c);
             const uint4 p0 = philox_c0(2 * ch, pc, rk0, rk1);
             const uint4 p1 = philox_c0(2 * ch + 1, pc, rk0, rk1);
-            const unsigned int pl[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-            compare_planes<XNOR>(pl, all4, eq3, ge3, ac, lt[c], eq[c]);
+            pl[0] = p0.x; pl[1] = p0.y; pl[2] = p0.z; pl[3] = p0.w;
+            pl[4] = p1.x; pl[5] = p1.y; pl[6] = p1.z; pl[7] = p1.w;
         }
+        if constexpr (HB) compare_planes_hb(pl, all4, ge3, c2, Mk::VALID, ac, lt[c], eq[c]);
+        else compare_planes<XNOR>(pl, all4, eq3, ge3, ac, lt[c], eq[c]);
         a4[c] = all4;
         g3[c] = ge3;
     }
 
     if constexpr (SweepStyle<L>::TIE_QUEUE) {
-        resolve_ties<C>(eq, a4, lt, lane, tq,
-                        [&](int src, int c, int b) {
-                            return TieSite{slot0 + (unsigned int)(src / G), (src & (G - 1)) * Gm::RPL + c * P + b / HP,
-                                           b % HP};
-                        },
-                        tag, step, rk0, rk1, ac.low4, ac.low8);
+        resolve_ties<C, HB>(eq, a4, g3, lt, lane, tq,
+                                [&](int src, int c, int b) {
+                                return TieSite{slot0 + (unsigned int)(src / G),
+                                               (src & (G - 1)) * Gm::RPL + c * P + b / HP, b % HP};
+                            },
+                            tag, step, rk0, rk1, ac.low4, ac.low8);
     } else {
         // the lane resolves its own ties, one per iteration over all its words
         unsigned int pending = 0;
@@ -628,13 +689,14 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
         for (int c = 0; c < C; ++c) pending |= eq[c];
         while (pending) {
             int csel = 0;
-            unsigned int w = 0, a4s = 0;
+            unsigned int w = 0, a4s = 0, invs = 0;
 #pragma unroll
             for (int c = C - 1; c >= 0; --c)
                 if (eq[c]) {
                     csel = c;
                     w = eq[c];
                     a4s = a4[c];
+                    if constexpr (HB) invs = g3[c];
                 }
             const int b = __ffs((int)w) - 1;
             const int r = r0 + csel * P + b / HP, j = b % HP;
@@ -642,20 +704,25 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
                                        rk0, rk1);
             const unsigned int thr = ((a4s >> b) & 1u) ? ac.low8 : ac.low4;
             const unsigned int bit = 1u << b;
-            const unsigned int acc = ((xr.x & 0xFFFFFFu) < thr) ? bit : 0u;
+            unsigned int xl = xr.x & 0xFFFFFFu;
+            if (HB && ((invs >> b) & 1u)) xl ^= 0xFFFFFFu;
+            const unsigned int acc = (xl < thr) ? bit : 0u;
             pending = 0;
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 if (c == csel) {
                     eq[c] &= ~bit;
-                    lt[c] |= acc;
+                    lt[c] ^= acc;
                 }
                 pending |= eq[c];
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < C; ++c) T[c] ^= (~g3[c] | lt[c]) & Mk::VALID;
+    for (int c = 0; c < C; ++c) {
+        if constexpr (HB) T[c] ^= lt[c];
+        else T[c] ^= (~g3[c] | lt[c]) & Mk::VALID;
+    }
 }
 
 // theta sweeps (numbered t0 .. t0 + theta - 1 within the temperature step) of the rows a
@@ -665,7 +732,7 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
 //
 // slot = the lane's replica slot, slot0 = the slot of the warp's first replica; tq = the
 // warp's tie queue.
-template <int L>
+template <int L, bool HB>
 __device__ __forceinline__ void sweep_rows(typename Geo<L>::W *A, typename Geo<L>::W *B, int r0, int lane,
                                            unsigned int slot, unsigned int slot0, int t0, int theta,
                                            unsigned int step, const unsigned int *rk0, const unsigned int *rk1,
@@ -685,11 +752,11 @@ __device__ __forceinline__ void sweep_rows(typename Geo<L>::W *A, typename Geo<L
                 unsigned int pl0[C][8], pl1[C][8];
                 packed_planes<L>(r0, slot, tag0, step, rk0, rk1, pl0);
                 packed_planes<L>(r0, slot, tag0 | 1u, step, rk0, rk1, pl1);
-                packed_update<L, 0, true>(PA, PB, pl0, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
-                packed_update<L, 1, true>(PA, PB, pl1, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
+                packed_update<L, 0, true, HB>(PA, PB, pl0, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
+                packed_update<L, 1, true, HB>(PA, PB, pl1, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
             } else {
-                packed_update<L, 0, false>(PA, PB, nullptr, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
-                packed_update<L, 1, false>(PA, PB, nullptr, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
+                packed_update<L, 0, false, HB>(PA, PB, nullptr, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
+                packed_update<L, 1, false, HB>(PA, PB, nullptr, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
             }
         }
         unpack_rows<L>(PA, PB, A, B);
@@ -697,8 +764,8 @@ __device__ __forceinline__ void sweep_rows(typename Geo<L>::W *A, typename Geo<L
 #pragma unroll 1
         for (int t = 0; t < theta; ++t) {
             const unsigned int tag0 = (unsigned int)(2 * (t0 + t));
-            half_sweep<L, 0>(A, B, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
-            half_sweep<L, 1>(A, B, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
+            half_sweep<L, 0, HB>(A, B, r0, lane, slot, slot0, tag0, step, rk0, rk1, k0, k1, ac, tq);
+            half_sweep<L, 1, HB>(A, B, r0, lane, slot, slot0, tag0 | 1u, step, rk0, rk1, k0, k1, ac, tq);
         }
     }
 }
@@ -732,6 +799,160 @@ __device__ __forceinline__ void measure_rows(const typename Geo<L>::W *A, const 
     }
 }
 
-// Fused kernel: (INIT) generate or (!INIT) load each replica, theta sweeps, measure.
+// ------------------------------------------------------------------------------------
+// Fused kernel: (INIT) generate or (!INIT) load each replica, theta sweeps with the
+// Metropolis (!HB) or heatbath (HB) update, measure.
+// ------------------------------------------------------------------------------------
+template <int L, bool INIT, bool HB>
+__global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_sweep(SweepArgs a)
+{
+    using Gm = Geo<L>;
+    using W = typename Gm::W;
+    constexpr int N = Gm::N, G = Gm::G, RPW = Gm::RPW, RPL = Gm::RPL;
+    extern __shared__ int sh_hist[];
+
+    for (int k = threadIdx.x; k <= N; k += blockDim.x) sh_hist[k] = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int q = lane & (G - 1);
+    const int sub = lane / G;
+    const int r0 = q * RPL;
+    const long long R = INIT ? a.R_init : a.st->R_cur;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+
+    unsigned int rk0[10], rk1[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
+        rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
+    }
+    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
+
+    // per-block exact sums: |M|, M^2, and the levels at the step start (0) and now (1):
+    // k0, k0^2, k1, k1^2, k0 k1
+    __shared__ unsigned long long sh_sum[7];
+    if (threadIdx.x < 7) sh_sum[threadIdx.x] = 0;
+    __syncthreads();
+    W *spins = reinterpret_cast<W *>(a.spins);
+    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp; 8 warps per block
+    __shared__ W tq_eq[8 * TQ], tq_a4[8 * TQ], tq_inv[HB ? 8 * TQ : 1];
+    __shared__ unsigned int tq_code[8 * TQ];
+    const int wib = threadIdx.x >> 5;
+    const TieQueue<W> tq{tq_eq + wib * TQ, tq_a4 + wib * TQ, HB ? tq_inv + wib * TQ : nullptr,
+                         tq_code + wib * TQ};
+
+    for (long long base = warp * RPW; base < R; base += nwarps * RPW) {
+        const long long j = base + sub;
+        const bool active = j < R;
+        W A[RPL], B[RPL];
+        W *rep = spins + (size_t)(active ? j : 0) * (2 * L);
+        if (INIT) {
+            init_rows<L>((unsigned int)j, r0, a.k0, a.k1, A, B);
+        } else {
+            if (active) load_rows<L>(rep, r0, A, B);
+            else {
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
+            }
+        }
+        sweep_rows<L, HB>(A, B, r0, lane, (unsigned int)j, (unsigned int)base, a.t0, a.theta, a.step, rk0, rk1, a.k0,
+                      a.k1, ac, tq);
+        int anti, ups;
+        measure_rows<L>(A, B, r0, lane, anti, ups);
+        anti = group_sum<G>(anti);
+        ups = group_sum<G>(ups);
+        // exact sums of this group of replicas: |M|, M^2, k0, k0^2, k1, k1^2, k0 k1
+        unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
+        int level = -1;
+        if (active) {
+            if (INIT || a.theta > 0) store_rows<L>(rep, r0, A, B);
+            if (q == 0) {
+                level = anti >> 1;
+                const int M = 2 * ups - N;
+                if (!INIT) {
+                    // level at the start of this temperature step (right after resampling),
+                    // kept in level_snap by the step's first call
+                    const unsigned long long k0 = (unsigned long long)(a.t0 == 0 ? a.level[j] : a.level_snap[j]);
+                    const unsigned long long k1 = (unsigned long long)level;
+                    if (a.t0 == 0) a.level_snap[j] = (int)k0;
+                    v[2] = k0;
+                    v[3] = k0 * k0;
+                    v[4] = k1;
+                    v[5] = k1 * k1;
+                    v[6] = k0 * k1;
+                }
+                a.level[j] = level;
+                a.mag[j] = M;
+                if (INIT) a.fam[j] = (int)j;
+                v[0] = (unsigned long long)(M < 0 ? -M : M);
+                v[1] = (unsigned long long)((long long)M * M);
+            }
+        }
+        constexpr int NSUM = INIT ? 2 : 7;
+        if constexpr (RPW >= 8) {
+            // many replicas per warp: reduce over the warp first, and count equal levels once
+            const unsigned int grp = __match_any_sync(0xffffffffu, level);
+            if (level >= 0 && lane == __ffs((int)grp) - 1) atomicAdd(&sh_hist[level], __popc(grp));
+#pragma unroll
+            for (int i = 0; i < NSUM; ++i)
+#pragma unroll
+                for (int o = 16; o >= G; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+            if (lane == 0)
+#pragma unroll
+                for (int i = 0; i < NSUM; ++i) atomicAdd(&sh_sum[i], v[i]);
+        } else if (level >= 0) {
+            atomicAdd(&sh_hist[level], 1);
+#pragma unroll
+            for (int i = 0; i < NSUM; ++i) atomicAdd(&sh_sum[i], v[i]);
+        }
+    }
+
+    // one global atomic per block and sum
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.st->sum_absM, sh_sum[0]);
+        atomicAdd(&a.st->sum_M2, sh_sum[1]);
+        if (!INIT) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), sh_sum[2]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), sh_sum[3]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), sh_sum[4]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), sh_sum[5]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), sh_sum[6]);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k <= N; k += blockDim.x) {
+        const int v = sh_hist[k];
+        if (v) atomicAdd(&a.hist[k], v);
+    }
+}
+
+template <int L, bool INIT, bool HB>
+cudaError_t launch_sweep_t(const SweepArgs &a, int num_sms, cudaStream_t s)
+{
+    constexpr int N = Geo<L>::N;
+    const size_t smem = (size_t)(N + 1) * sizeof(int);
+    static int blocks_per_sm = 0;  // occupancy of this instantiation, queried once
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep<L, INIT, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep<L, INIT, HB>, 256, smem);
+        if (e != cudaSuccess) return e;
+        blocks_per_sm = b > 0 ? b : 1;
+    }
+    const long long R = a.R_bound;
+    const long long groups = (R + Geo<L>::RPW - 1) / Geo<L>::RPW;  // warps needed
+    long long blocks = (groups + 7) / 8;
+    const long long cap = (long long)num_sms * blocks_per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_sweep<L, INIT, HB><<<(unsigned int)blocks, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 
 }  // namespace pa

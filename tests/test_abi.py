@@ -49,10 +49,12 @@ def test_query_sizes_is_host_only():
     cfg128 = _lib.pa_config(L=128, resample=0, R=10, capacity=10, seed=1)
     assert lib.pa_query_sizes(ctypes.byref(cfg128), ctypes.byref(sz)) == _lib.PA_OK
     assert sz.bytes_per_replica == 2048
+    hb = _lib.pa_config(L=16, resample=1, R=10, capacity=30, seed=1, update=_lib.PA_UPDATE_HEATBATH)
+    assert lib.pa_query_sizes(ctypes.byref(hb), ctypes.byref(sz)) == _lib.PA_OK
 
 
 @pytest.mark.parametrize("bad", [dict(L=10), dict(L=6), dict(L=256), dict(R=0), dict(capacity=5, R=10),
-                                 dict(resample=2), dict(capacity=2 ** 31)])
+                                 dict(resample=2), dict(capacity=2 ** 31), dict(update=2), dict(pad=1)])
 def test_query_sizes_rejects_bad_configs(bad):
     args = dict(L=8, resample=0, R=10, capacity=20, seed=1)
     args.update(bad)
