@@ -33,7 +33,7 @@ _lock = threading.Lock()
 _lib = None
 
 STREAM_INIT, STREAM_SWEEP, STREAM_RESAMPLE, STREAM_POISSON, STREAM_REFINE = 0, 1, 2, 3, 4
-NEAREST, POISSON = 0, 1
+NEAREST, POISSON, MULTINOMIAL = 0, 1, 2
 
 
 def build(force: bool = False) -> str:

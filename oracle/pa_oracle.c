@@ -239,7 +239,7 @@ void orc_init_replica(int L, uint64_t seed, uint32_t j, int8_t *s)
  *   low 24 bits:  the low 24 bits of word 0 of
  *                 Philox(ctr = (64 r + p, j, (REFINE << 28) | tag, i)).
  * ---------------------------------------------------------------------------------- */
-enum { STREAM_REFINE = 4 };
+enum { STREAM_REFINE = 4, STREAM_MULTINOMIAL = 5 };
 
 uint32_t orc_sweep_uniform(int L, uint64_t seed, uint32_t step, uint32_t slot, int tag, int r, int p)
 {
@@ -415,7 +415,39 @@ int orc_resample_levels(int L, int64_t R_target, int64_t R_prev, const int32_t *
         thr[k] = (uint64_t)floor((tau[k] - f) * 4294967296.0);
     }
     int64_t R_new = 0;
-    for (int64_t j = 0; j < R_prev; ++j) {
+    if (kind == 2) {
+        /* Multinomial resampling at fixed size (Sec. II: R_target children drawn from the
+           parents with probabilities tau_j / R_prev = w_j / sum_l w_l).  Reading: the weights
+           are the integers W_j = floor(w_{k(j)} 2^32) (w <= 1), C_j = W_0 + ... + W_j exactly,
+           T = C_{R_prev - 1}; child c takes X = x1 2^32 + x0 from words 0 and 1 of
+           Philox(ctr = (c, 0, MULTINOMIAL << 28, i)), U = floor(X T / 2^64) in [0, T), and
+           the parent j with C_{j-1} <= U < C_j.  counts_out[j] = children of parent j. */
+        uint64_t *C = (uint64_t *)malloc((size_t)R_prev * sizeof(uint64_t));
+        uint64_t run = 0;
+        for (int64_t j = 0; j < R_prev; ++j) {
+            run += (uint64_t)floor(w[level[j]] * 4294967296.0);
+            C[j] = run;
+            counts_out[j] = 0;
+        }
+        const uint64_t T = run;
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        for (int64_t c = 0; c < R_target; ++c) {
+            uint32_t ctr[4] = {(uint32_t)c, 0, (uint32_t)STREAM_MULTINOMIAL << 28, step}, x[4];
+            orc_philox4x32_10(ctr, key, x);
+            const uint64_t X = ((uint64_t)x[1] << 32) | x[0];
+            const uint64_t U = (uint64_t)(((unsigned __int128)X * T) >> 64);
+            int64_t lo = 0, hi = R_prev - 1;  /* first j with C_j > U */
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (C[mid] > U) hi = mid;
+                else lo = mid + 1;
+            }
+            counts_out[lo] += 1;
+        }
+        free(C);
+        R_new = R_target;
+    }
+    for (int64_t j = 0; kind != 2 && j < R_prev; ++j) {
         int k = level[j];
         int64_t r;
         if (kind == 0) {

@@ -89,6 +89,52 @@ def test_nearest_integer_counts_bounds_and_mean():
     assert abs(extra.sum() - frac.sum()) < 5 * math.sqrt(np.sum(frac * (1 - frac)))
 
 
+def test_multinomial_counts_fixed_size_mean_and_variance():
+    """Multinomial resampling (Sec. II): exactly R children; r_j is Binomial(R, p_j) with
+    p_j = w_j / sum w, so per energy level the total copies have mean R P_k and variance
+    R P_k (1 - P_k), P_k = h_k w_k / S (checked over the levels with P_k > 1e-3)."""
+    L, R = 8, 50000
+    pa = oracle.PA(L, R, seed=9)
+    pa.init()
+    E, _, _ = pa.state()
+    lv = _levels_energy(L, E)
+    db = 0.05
+    w = np.exp(-db * E.astype(float))
+    p = w / w.sum()
+    sums = []
+    for step in range(1, 41):
+        st, counts, lnQ, S, kmin, R_new = oracle.resample_levels(L, R, lv, 0.0, db, step, 9,
+                                                                 oracle.MULTINOMIAL, oracle.default_capacity(R))
+        assert st == 0 and R_new == R and counts.sum() == R
+        sums.append(np.bincount(lv, weights=counts, minlength=L * L + 1))
+    sums = np.array(sums)
+    P = np.bincount(lv, weights=p, minlength=L * L + 1)
+    sel = P > 1e-3
+    mean = sums[:, sel].mean(axis=0)
+    var = sums[:, sel].var(axis=0, ddof=1)
+    expect_var = R * P[sel] * (1 - P[sel])
+    z = (mean - R * P[sel]) / np.sqrt(expect_var / len(sums))
+    assert np.all(np.abs(z) < 5)
+    # variance ratio: chi-square with 39 dof per level, averaged over the levels
+    assert abs(np.mean(var / expect_var) - 1) < 0.25
+
+
+def test_multinomial_uniform_weights_are_binomial_counts():
+    """With dbeta = 0 every parent has probability 1/R: r_j ~ Binomial(R, 1/R), whose
+    frequencies of 0, 1, 2, 3 copies are checked by chi-square."""
+    L, R = 4, 20000
+    pa = oracle.PA(L, R, seed=2)
+    pa.init()
+    E, _, _ = pa.state()
+    st, counts, *_ = oracle.resample_levels(L, R, _levels_energy(L, E), 0.3, 0.3, 1, 2, oracle.MULTINOMIAL,
+                                            oracle.default_capacity(R))
+    assert counts.sum() == R
+    obs = np.bincount(counts, minlength=5)[:4]
+    pk = np.array([math.comb(R, k) * (1 / R) ** k * (1 - 1 / R) ** (R - k) for k in range(4)])
+    chi2 = np.sum((obs - R * pk) ** 2 / (R * pk))
+    assert chi2 < 3 + 6 * math.sqrt(6)
+
+
 @pytest.mark.parametrize("lam", [0.3, 1.0, 2.5, 70.0])
 def test_poisson_sampler_pmf(lam):
     n = 30000
@@ -150,15 +196,17 @@ def test_capacity_overflow_is_reported():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("update", [oracle.METROPOLIS, oracle.HEATBATH])
-def test_full_anneal_L4_matches_enumeration(update):
+@pytest.mark.parametrize("update,kind", [(oracle.METROPOLIS, oracle.NEAREST), (oracle.HEATBATH, oracle.NEAREST),
+                                         (oracle.METROPOLIS, oracle.MULTINOMIAL)])
+def test_full_anneal_L4_matches_enumeration(update, kind):
     """A whole anneal at L=4 reproduces the exact ln Z (Sec. VII estimator), <E> and C
-    within a few standard errors, with the Metropolis and the heatbath update (Sec. IV)."""
+    within a few standard errors, with the Metropolis and the heatbath update (Sec. IV) and
+    with nearest-integer and multinomial resampling (Sec. II)."""
     L, R, theta = 4, 20000, 5
     N = L * L
     g, _, _ = oracle.bruteforce(L)
     Ek = (4 * np.arange(N + 1) - 2 * N).astype(float)
-    pa = oracle.PA(L, R, seed=31, update=update)
+    pa = oracle.PA(L, R, seed=31, kind=kind, update=update)
     pa.init()
     for i in range(1, 21):
         beta = i / 20.0
