@@ -51,8 +51,14 @@ typedef enum {
 } pa_status;
 
 typedef enum {
-    PA_RESAMPLE_NEAREST = 0, /* Eq. (resampling-factors): floor(tau) or floor(tau) + 1 */
-    PA_RESAMPLE_POISSON = 1  /* r_j ~ Poisson(tau_hat_j), fluctuating population size */
+    PA_RESAMPLE_NEAREST = 0,    /* Eq. (resampling-factors): floor(tau) or floor(tau) + 1 */
+    PA_RESAMPLE_POISSON = 1,    /* r_j ~ Poisson(tau_hat_j), fluctuating population size */
+    PA_RESAMPLE_MULTINOMIAL = 2 /* R children drawn from the parents with probabilities
+                                   tau_j / R_{i-1} (Sec. II; fixed size R_i = R): integer
+                                   weights W_j = floor(w_j 2^32), their exact running sum C_j,
+                                   child c takes X = words 1:0 of Philox(ctr = (c, 0,
+                                   MULTINOMIAL << 28, i)), U = floor(X C_last / 2^64), parent
+                                   j with C_{j-1} <= U < C_j.  Single runs only. */
 } pa_resample_kind;
 
 /* Spin update of step 3 (Sec. IV).  With a aligned neighbours, dE = 4a - 8 and x the site's

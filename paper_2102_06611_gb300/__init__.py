@@ -48,7 +48,8 @@ class PopulationAnnealing:
         self.L, self.N, self.R_target = int(L), int(L) * int(L), int(R)
         self.capacity = int(capacity if capacity is not None else default_capacity(R))
         self.seed = int(seed)
-        kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON}[resample]
+        kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON,
+                "multinomial": _lib.PA_RESAMPLE_MULTINOMIAL}[resample]
         upd = {"metropolis": _lib.PA_UPDATE_METROPOLIS, "heatbath": _lib.PA_UPDATE_HEATBATH}[update]
         self.device = torch.device(device if device is not None else "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -17,7 +17,7 @@ _lib = None
  PA_ERR_TOO_LARGE) = range(8)
 STATUS_NAMES = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_STATE", 3: "PA_ERR_CAPACITY",
                 4: "PA_ERR_CUDA", 5: "PA_ERR_TIMEOUT", 6: "PA_ERR_NUMERIC", 7: "PA_ERR_TOO_LARGE"}
-PA_RESAMPLE_NEAREST, PA_RESAMPLE_POISSON = 0, 1
+PA_RESAMPLE_NEAREST, PA_RESAMPLE_POISSON, PA_RESAMPLE_MULTINOMIAL = 0, 1, 2
 PA_UPDATE_METROPOLIS, PA_UPDATE_HEATBATH = 0, 1
 
 

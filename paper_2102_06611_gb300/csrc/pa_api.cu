@@ -131,7 +131,9 @@ pa_status pa_query_sizes(const pa_config *cfg, pa_sizes *out)
     if (!cfg || !out) return PA_ERR_INVALID_ARG;
     if (!supported_L(cfg->L) || cfg->R < 1 || cfg->capacity < cfg->R || cfg->capacity > 2147483647LL)
         return PA_ERR_INVALID_ARG;
-    if (cfg->resample != PA_RESAMPLE_NEAREST && cfg->resample != PA_RESAMPLE_POISSON) return PA_ERR_INVALID_ARG;
+    if (cfg->resample != PA_RESAMPLE_NEAREST && cfg->resample != PA_RESAMPLE_POISSON &&
+        cfg->resample != PA_RESAMPLE_MULTINOMIAL)
+        return PA_ERR_INVALID_ARG;
     if ((cfg->update != PA_UPDATE_METROPOLIS && cfg->update != PA_UPDATE_HEATBATH) || cfg->pad != 0)
         return PA_ERR_INVALID_ARG;
     const pa::Workspace ws = pa::plan_workspace(cfg->L, cfg->capacity);
@@ -229,6 +231,8 @@ pa_status pa_resample(pa_ctx *c, double beta_new)
     a.counts = at<int>(c, c->ws.counts);
     a.blocksum = at<long long>(c, c->ws.blocksum);
     a.nblk = c->ws.nblk;
+    a.wint = at<unsigned long long>(c, c->ws.wint);
+    a.cdf = at<unsigned long long>(c, c->ws.cdf);
     a.spins_src = c->buf.spins[c->cur];
     a.spins_dst = c->buf.spins[nxt];
     a.level_src = static_cast<const int *>(c->buf.level[c->cur]);

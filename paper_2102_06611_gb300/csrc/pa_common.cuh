@@ -94,7 +94,8 @@ enum : unsigned int {
     kStreamSweep = 1u,
     kStreamResample = 2u,
     kStreamPoisson = 3u,
-    kStreamRefine = 4u
+    kStreamRefine = 4u,
+    kStreamMultinomial = 5u
 };
 
 __device__ __forceinline__ void mulhilo(unsigned int a, unsigned int b, unsigned int &hi, unsigned int &lo)
@@ -196,6 +197,7 @@ struct DevState {
     long long c0, c00, c1, c11, c01;
     int theta;
     int update;               // pa_update_kind of the run (selects the thresholds below)
+    unsigned long long mn_total;  // multinomial resampling: sum of the integer parent weights
 };
 
 __device__ __forceinline__ void set_error(DevState *st, int code)

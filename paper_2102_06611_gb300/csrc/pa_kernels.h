@@ -32,6 +32,8 @@ struct Workspace {
     size_t ana_blk;     // int64[4 * kMaxAnaBlocks] analysis block sums
     size_t ana_sizes;   // int32[capacity + 1]     family-size histogram (entry 0: largest size)
     size_t ana_out;     // pa_analysis
+    size_t wint;        // uint64[N + 1]  multinomial: integer weights floor(w_k 2^32)
+    size_t cdf;         // uint64[capacity] multinomial: running sum of the parents' weights
     size_t total;
     long long nblk;     // blocks of the copy-count / copy kernels
 };
@@ -83,6 +85,8 @@ struct ResampleArgs {
     int *counts;
     long long *blocksum;
     long long nblk;
+    unsigned long long *wint;  // multinomial only
+    unsigned long long *cdf;   // multinomial only
     const void *spins_src;
     void *spins_dst;
     const int *level_src, *mag_src, *fam_src;

@@ -53,6 +53,8 @@ Workspace plan_workspace(int L, long long capacity)
     w.ana_blk = off;  off = align256(off + (size_t)kMaxAnaBlocks * 4 * 8);
     w.ana_sizes = off; off = align256(off + ((size_t)capacity + 1) * 4);
     w.ana_out = off;  off = align256(off + sizeof(pa_analysis));
+    w.wint = off;     off = align256(off + nlev * 8);
+    w.cdf = off;      off = align256(off + (size_t)capacity * 8);
     w.total = off;
     w.nblk = nblk;
     return w;
@@ -230,6 +232,8 @@ __device__ __forceinline__ void table_body(const ResampleArgs &a)
             a.tau[k] = tau;
             a.fl[k] = (int)f;
             a.thr[k] = (unsigned int)floor(__dmul_rn(__dsub_rn(tau, f), 4294967296.0));
+            if (a.kind == PA_RESAMPLE_MULTINOMIAL)
+                a.wint[k] = (unsigned long long)floor(__dmul_rn(a.w[k], 4294967296.0));
         }
     }
     if (tid == 0) {
@@ -305,6 +309,110 @@ __device__ __forceinline__ void counts_body(const ResampleArgs &a)
 }
 
 __global__ void __launch_bounds__(kCountThreads) k_counts(ResampleArgs a) { counts_body(a); }
+
+// ------------------------------------------------------------------------------ multinomial
+// Fixed-size multinomial resampling (Sec. II): R_target children pick parents with
+// probabilities proportional to the integer weights W_j = floor(w_{k(j)} 2^32).
+//   k_mn_wsum   per-block sums of W_j (blocks of kCountBlockItems parents)
+//   k_mn_wscan  exclusive scan of the block sums, total T into DevState::mn_total
+//   k_mn_cdf    C_j = W_0 + ... + W_j (exact uint64), counts zeroed
+//   k_mn_draw   child c: X = Philox words 1:0, U = floor(X T / 2^64), parent = first j with
+//               C_j > U (binary search), counts[j] += 1
+//   k_mn_csum   per-block sums of the counts, for k_scan and k_copy
+__global__ void __launch_bounds__(kCountThreads) k_mn_wsum(ResampleArgs a)
+{
+    if (a.st->error) return;
+    const long long Rp = a.st->R_prev;
+    const long long base = (long long)blockIdx.x * kCountBlockItems;
+    long long sum = 0;
+#pragma unroll
+    for (int it = 0; it < kCountItems; ++it) {
+        const long long j = base + it * kCountThreads + threadIdx.x;
+        if (j < Rp) sum += (long long)a.wint[a.level_src[j]];
+    }
+    const long long t = block_sum<long long, kCountThreads>(sum);
+    if (threadIdx.x == 0) a.blocksum[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_mn_wscan(ResampleArgs a)
+{
+    DevState *st = a.st;
+    if (st->error) return;
+    const long long nb = (st->R_prev + kCountBlockItems - 1) / kCountBlockItems;
+    long long carry = 0;
+    for (long long start = 0; start < nb; start += 1024) {
+        const long long b = start + threadIdx.x;
+        const long long v = b < nb ? a.blocksum[b] : 0;
+        long long tot;
+        const long long ex = block_exclusive_scan<long long, 1024>(v, &tot);
+        if (b < nb) a.blocksum[b] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) st->mn_total = (unsigned long long)carry;
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_mn_cdf(ResampleArgs a)
+{
+    if (a.st->error) return;
+    const long long Rp = a.st->R_prev;
+    const long long base = (long long)blockIdx.x * kCountBlockItems;
+    // thread t owns parents base + 4t .. base + 4t + 3
+    long long wv[kCountItems];
+    long long local = 0;
+#pragma unroll
+    for (int it = 0; it < kCountItems; ++it) {
+        const long long j = base + threadIdx.x * kCountItems + it;
+        wv[it] = j < Rp ? (long long)a.wint[a.level_src[j]] : 0;
+        local += wv[it];
+    }
+    long long tot;
+    long long run = block_exclusive_scan<long long, kCountThreads>(local, &tot) + a.blocksum[blockIdx.x];
+#pragma unroll
+    for (int it = 0; it < kCountItems; ++it) {
+        const long long j = base + threadIdx.x * kCountItems + it;
+        run += wv[it];
+        if (j < Rp) {
+            a.cdf[j] = (unsigned long long)run;
+            a.counts[j] = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_mn_draw(ResampleArgs a)
+{
+    const DevState *st = a.st;
+    if (st->error) return;
+    const long long Rp = st->R_prev;
+    const unsigned long long T = st->mn_total;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < a.R_target;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint4 x = philox(make_uint4((unsigned int)c, 0u, kStreamMultinomial << 28, a.step), a.k0, a.k1);
+        const unsigned long long X = ((unsigned long long)x.y << 32) | x.x;
+        const unsigned long long U = __umul64hi(X, T);
+        long long lo = 0, hi = Rp - 1;  // first j with C_j > U
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (a.cdf[mid] > U) hi = mid;
+            else lo = mid + 1;
+        }
+        atomicAdd(&a.counts[lo], 1);
+    }
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_mn_csum(ResampleArgs a)
+{
+    if (a.st->error) return;
+    const long long Rp = a.st->R_prev;
+    const long long base = (long long)blockIdx.x * kCountBlockItems;
+    long long sum = 0;
+#pragma unroll
+    for (int it = 0; it < kCountItems; ++it) {
+        const long long j = base + it * kCountThreads + threadIdx.x;
+        if (j < Rp) sum += a.counts[j];
+    }
+    const long long t = block_sum<long long, kCountThreads>(sum);
+    if (threadIdx.x == 0) a.blocksum[blockIdx.x] = t;
+}
 
 // ------------------------------------------------------------------------------ scan
 constexpr int kScanThreads = 1024;
@@ -400,7 +508,16 @@ cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned int nblk = (unsigned int)a.nblk;
-    k_counts<<<nblk, kCountThreads, 0, s>>>(a);
+    if (a.kind == PA_RESAMPLE_MULTINOMIAL) {
+        k_mn_wsum<<<nblk, kCountThreads, 0, s>>>(a);
+        k_mn_wscan<<<1, 1024, 0, s>>>(a);
+        k_mn_cdf<<<nblk, kCountThreads, 0, s>>>(a);
+        const long long dblk = (a.R_target + kCountThreads - 1) / kCountThreads;
+        k_mn_draw<<<(unsigned int)(dblk < 4096 ? dblk : 4096), kCountThreads, 0, s>>>(a);
+        k_mn_csum<<<nblk, kCountThreads, 0, s>>>(a);
+    } else {
+        k_counts<<<nblk, kCountThreads, 0, s>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scan<<<1, kScanThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

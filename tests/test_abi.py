@@ -54,7 +54,7 @@ def test_query_sizes_is_host_only():
 
 
 @pytest.mark.parametrize("bad", [dict(L=10), dict(L=6), dict(L=256), dict(R=0), dict(capacity=5, R=10),
-                                 dict(resample=2), dict(capacity=2 ** 31), dict(update=2), dict(pad=1)])
+                                 dict(resample=3), dict(capacity=2 ** 31), dict(update=2), dict(pad=1)])
 def test_query_sizes_rejects_bad_configs(bad):
     args = dict(L=8, resample=0, R=10, capacity=20, seed=1)
     args.update(bad)
