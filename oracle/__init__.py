@@ -127,6 +127,7 @@ def lib():
                 "orc_analysis": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int64, i32p, i32p,
                                                 i32p, ctypes.c_int, dp]),
                 "orc_pa_analysis": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+                "orc_weighted_average": (None, [ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_int, dp]),
                 "orc_bruteforce": (ctypes.c_int, [ctypes.c_int, i64p, i64p, i64p]),
                 "orc_transfer_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
                 "orc_kaufman_lnZ": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
@@ -294,7 +295,7 @@ def kaufman_thermo(L: int, beta: float, h: float = 2e-4):
 
 # ----------------------------------------------------------------------------- full PA
 OBS_FIELDS = ["beta", "dbeta", "R", "e", "C", "m", "m2", "chi", "lnQ", "minus_betaF",
-              "families", "rho_t", "step", "theta"]
+              "families", "rho_t", "step", "theta", "sum_lnRratio"]
 
 
 ANALYSIS_FIELDS = ["n_blocks", "mean_E", "var_E", "var_mean_E_jack", "var_mean_E_blocked", "R_eff_E",
@@ -315,6 +316,22 @@ def analysis(N: int, beta: float, E, M, fam, n_blocks: int = 100) -> dict:
     if st != 0:
         raise ValueError("need 2 <= n_blocks <= R")
     return dict(zip(ANALYSIS_FIELDS, out.tolist()))
+
+
+WEIGHTED_FIELDS = ["M_eff", "max_weight", "var_minus_betaF", "minus_betaF_combined", "e", "C", "m", "m2", "chi",
+                   "e_plain", "C_plain", "m_plain", "m2_plain", "chi_plain"]
+
+
+def weighted_average(R_i, R_target, minus_betaF, sum_lnRratio, obs, mode: int = 1) -> dict:
+    """Weighted average over independent runs at one temperature (Sec. VIII, Eq.
+    weighted-averages for mode 0, Eq. modified-weights2 for mode 1); obs is M x 5
+    (e, C, m, m2, chi)."""
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (R_i, R_target, minus_betaF, sum_lnRratio)]
+    o = np.ascontiguousarray(obs, np.float64).reshape(-1, 5)
+    out = np.zeros(14)
+    lib().orc_weighted_average(len(arrs[0]), *[_ptr(a, ctypes.c_double) for a in arrs], _ptr(o, ctypes.c_double),
+                               int(mode), _ptr(out, ctypes.c_double))
+    return dict(zip(WEIGHTED_FIELDS, out.tolist()))
 
 
 class PA:
@@ -354,7 +371,7 @@ class PA:
         return int(lib().orc_pa_R_prev(self._h))
 
     def observables(self) -> dict:
-        out = np.zeros(14)
+        out = np.zeros(15)
         isums = np.zeros(6, np.int64)
         lib().orc_pa_observables(self._h, _ptr(out, ctypes.c_double), _ptr(isums, ctypes.c_int64))
         d = dict(zip(OBS_FIELDS, out.tolist()))

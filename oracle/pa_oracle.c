@@ -479,6 +479,7 @@ typedef struct {
     uint64_t seed;
     uint32_t step;          /* index i of the current temperature beta_i */
     double beta, dbeta, lnQ, sum_lnQ;
+    double sum_lnR;         /* sum_k ln(R_{k-1} / R) over the resamplings so far */
     int theta_last;
     int t_done;             /* sweeps already done at the current step */
     int8_t *s;              /* capacity * N */
@@ -533,7 +534,7 @@ void orc_pa_init(orc_pa *p)
     p->R = p->R_target;
     p->R_prev = 0;
     p->step = 0;
-    p->beta = 0.0; p->dbeta = 0.0; p->lnQ = 0.0; p->sum_lnQ = 0.0;
+    p->beta = 0.0; p->dbeta = 0.0; p->lnQ = 0.0; p->sum_lnQ = 0.0; p->sum_lnR = 0.0;
     p->theta_last = 0;
     p->t_done = 0;
     p->status = 0;
@@ -579,6 +580,7 @@ int orc_pa_resample(orc_pa *p, double beta_new)
     p->t_done = 0;
     p->lnQ = info.lnQ;
     p->sum_lnQ = p->sum_lnQ + info.lnQ;
+    p->sum_lnR = p->sum_lnR + log((double)p->R_prev / (double)p->R_target);
     return 0;
 }
 
@@ -599,7 +601,8 @@ void orc_pa_sweep(orc_pa *p, int theta)
 /* Step 4: population averages (Sec. III) and the free energy (Sec. VII), all from exact
    integer sums; formula order fixed.
    out[0] beta, [1] dbeta, [2] R_i, [3] e, [4] C, [5] m, [6] m2, [7] chi, [8] lnQ,
-   [9] -beta F, [10] families f, [11] rho_t, [12] step, [13] theta.
+   [9] -beta F, [10] families f, [11] rho_t, [12] step, [13] theta,
+   [14] sum_k ln(R_{k-1} / R) (the population-size factor of Eq. modified-weights2).
    isums[0] sum E, [1] sum E^2, [2] sum |M|, [3] sum M^2, [4] f, [5] sum size^2. */
 void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
 {
@@ -635,6 +638,7 @@ void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
     out[5] = m; out[6] = m2; out[7] = chi; out[8] = p->lnQ; out[9] = mbF;
     out[10] = (double)f; out[11] = rho_t; out[12] = (double)p->step;
     out[13] = (double)p->theta_last;
+    out[14] = p->sum_lnR;
     if (isums) {
         isums[0] = sE; isums[1] = sE2; isums[2] = sAM; isums[3] = sM2; isums[4] = f;
         isums[5] = s2;
@@ -815,4 +819,56 @@ int orc_analysis(int N, double beta, int64_t R, const int32_t *E, const int32_t 
 int orc_pa_analysis(const orc_pa *p, int n, double *out)
 {
     return orc_analysis(p->N, p->beta, p->R, p->E, p->M, p->fam, n, out);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Weighted averages over M independent runs at the same temperature step (Sec. VIII,
+ * Eqs. weighted-averages and modified-weights2).  Run m has population R_i^m, target R^m,
+ * -beta F^m = N ln 2 + sum_k ln Q_k^m and s^m = sum_{k<=i} ln(R_{k-1}^m / R^m):
+ *   log w_m = ln R_i^m - beta F^m (+ s^m for mode 1, the fluctuating-size form),
+ *   omega_m = exp(log w_m - max) / sum_l exp(log w_l - max)      (runs in order),
+ *   O = sum_m omega_m O_m for O in (e, C, m, m2, chi), and the plain means (1/M) sum_m O_m.
+ * Also M_eff = 1 / sum omega_m^2, the largest omega, the unbiased variance of -beta F^m over
+ * the runs (weighted averaging is sound only while it is well below 1, Sec. VIII), and the
+ * combined free energy ln(sum_m R^m exp(-beta F^m) / sum_m R^m) (reading: the R-weighted
+ * mean of the runs' partition-function estimates).
+ * obs is M x 5 (e, C, m, m2, chi).  out: [0] M_eff, [1] max omega, [2] var(-beta F),
+ * [3] combined -beta F, [4..8] weighted e C m m2 chi, [9..13] plain means. */
+void orc_weighted_average(int M, const double *R_i, const double *R_t, const double *mbF, const double *slnR,
+                          const double *obs, int mode, double *out)
+{
+    double mx = -INFINITY, mz = -INFINITY, sR = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double lw = log(R_i[m]) + mbF[m] + (mode == 1 ? slnR[m] : 0.0);
+        const double lz = log(R_t[m]) + mbF[m];
+        if (lw > mx) mx = lw;
+        if (lz > mz) mz = lz;
+        sR += R_t[m];
+    }
+    double s = 0.0, sz = 0.0;
+    for (int m = 0; m < M; ++m) {
+        s += exp(log(R_i[m]) + mbF[m] + (mode == 1 ? slnR[m] : 0.0) - mx);
+        sz += exp(log(R_t[m]) + mbF[m] - mz);
+    }
+    double w2 = 0.0, wmax = 0.0, meanF = 0.0;
+    for (int q = 0; q < 5; ++q) { out[4 + q] = 0.0; out[9 + q] = 0.0; }
+    for (int m = 0; m < M; ++m) {
+        const double om = exp(log(R_i[m]) + mbF[m] + (mode == 1 ? slnR[m] : 0.0) - mx) / s;
+        w2 += om * om;
+        if (om > wmax) wmax = om;
+        for (int q = 0; q < 5; ++q) {
+            out[4 + q] += om * obs[5 * m + q];
+            out[9 + q] += obs[5 * m + q];
+        }
+        meanF += mbF[m];
+    }
+    meanF /= (double)M;
+    double vF = 0.0;
+    for (int m = 0; m < M; ++m) vF += (mbF[m] - meanF) * (mbF[m] - meanF);
+    vF = M > 1 ? vF / (double)(M - 1) : 0.0;
+    for (int q = 0; q < 5; ++q) out[9 + q] /= (double)M;
+    out[0] = 1.0 / w2;
+    out[1] = wmax;
+    out[2] = vF;
+    out[3] = mz + log(sz) - log(sR);
 }
