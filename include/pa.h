@@ -129,6 +129,9 @@ typedef struct {
     long long sum_size2;   /* sum over families of (family size)^2 */
     int theta;             /* sweeps of the last pa_anneal_step */
     int status;            /* sticky device error word (pa_status) */
+    double sum_lnRratio;   /* sum_{k<=i} ln(R_{k-1} / R): the population-size factor of
+                              Eq. modified-weights2 (0 at fixed population size) */
+    long long R_target;    /* target population size R */
 } pa_obs;
 
 /* One temperature step of the schedule a context actually ran (see pa_schedule_log). */
@@ -204,6 +207,33 @@ typedef struct {
     double C, var_C_jack;
     double S_f, rho_s;
 } pa_analysis;
+
+/* Weighted average over M independent runs at one temperature step (Sec. VIII).  Run m's
+   record gives R_i^m, R^m, -beta F^m and s^m = sum_k ln(R_{k-1}^m / R^m); the weights are
+   omega_m proportional to R_i^m exp(-beta F^m) (mode 0, Eq. weighted-averages) or to
+   R_i^m exp(s^m) exp(-beta F^m) (mode 1, Eq. modified-weights2), normalised in binary64 with
+   the largest exponent taken out, runs in order.  Fields: the weighted and the plain means
+   of e, C, m, m2, chi; M_eff = 1 / sum omega^2; the largest omega; the unbiased variance of
+   -beta F^m over the runs (weighting is sound only while it is well below 1, Sec. VIII);
+   and ln(sum_m R^m exp(-beta F^m) / sum_m R^m), the R-weighted mean of the runs' partition
+   function estimates.  status = PA_ERR_INVALID_ARG if the records are not all at the same
+   step and beta, else the first non-zero record status. */
+typedef struct {
+    long long step;
+    int M;
+    int mode;
+    double beta;
+    double M_eff, max_weight, var_minus_betaF, minus_betaF_combined;
+    double e, C, m, m2, chi;                            /* weighted */
+    double e_plain, C_plain, m_plain, m2_plain, chi_plain;
+    int status;
+    int pad;
+} pa_weighted;
+
+/* Form the weighted average of M >= 1 pa_obs records (device memory, contiguous, as written
+   by pa_record or pa_batch_record) into *out_dev (device memory, sizeof(pa_weighted) bytes,
+   8-byte aligned).  Asynchronous on `stream`; one block of one thread per call's result. */
+pa_status pa_weighted_average(const void *records_dev, int M, int mode, void *out_dev, void *stream);
 
 /* Analyse the current population (measured first if a resampling came since) in n_blocks
    blocks, 2 <= n_blocks <= min(R_i, 1024), and copy the result to host memory.

@@ -20,7 +20,8 @@ import torch
 from . import _lib
 from ._lib import PAError, pa_obs
 
-__all__ = ["PopulationAnnealing", "PAError", "pa_obs", "default_capacity", "SUPPORTED_L", "OBS_BYTES"]
+__all__ = ["PopulationAnnealing", "PAError", "pa_obs", "default_capacity", "SUPPORTED_L", "OBS_BYTES",
+           "weighted_average"]
 
 SUPPORTED_L = (4, 8, 12, 16, 24, 32, 48, 64, 128)
 OBS_BYTES = ctypes.sizeof(pa_obs)
@@ -36,6 +37,25 @@ def _check(lib, ctx, status: int):
     if status != _lib.PA_OK:
         msg = lib.pa_last_error(ctx) if ctx else b""
         raise PAError(status, (msg or b"").decode(errors="replace"))
+
+
+def weighted_average(records: torch.Tensor, mode: str = "modified", stream: torch.cuda.Stream | None = None) -> dict:
+    """Weighted average over independent runs at one temperature step (Sec. VIII):
+    `records` is a device tensor holding M pa_obs records back to back (pa_record /
+    Batch.record output for one step); mode "standard" is Eq. weighted-averages, "modified"
+    Eq. modified-weights2.  Synchronises `stream` (default: the current stream)."""
+    if not records.is_cuda or records.numel() * records.element_size() % OBS_BYTES:
+        raise ValueError("records must be a device tensor of whole pa_obs records")
+    M = records.numel() * records.element_size() // OBS_BYTES
+    lib = _lib.lib()
+    stream = stream if stream is not None else torch.cuda.current_stream(records.device)
+    out = torch.zeros((ctypes.sizeof(_lib.pa_weighted) + 7) // 8, dtype=torch.int64, device=records.device)
+    st = lib.pa_weighted_average(ctypes.c_void_p(records.data_ptr()), M, {"standard": 0, "modified": 1}[mode],
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    _check(lib, None, st)
+    stream.synchronize()
+    w = _lib.pa_weighted.from_buffer_copy(out.cpu().numpy().tobytes()[: ctypes.sizeof(_lib.pa_weighted)])
+    return w.as_dict()
 
 
 class PopulationAnnealing:

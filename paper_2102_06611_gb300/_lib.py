@@ -50,7 +50,8 @@ class pa_obs(ctypes.Structure):
                 ("lnQ", ctypes.c_double), ("minus_betaF", ctypes.c_double), ("rho_t", ctypes.c_double),
                 ("families", ctypes.c_longlong), ("sum_E", ctypes.c_longlong), ("sum_E2", ctypes.c_longlong),
                 ("sum_absM", ctypes.c_longlong), ("sum_M2", ctypes.c_longlong),
-                ("sum_size2", ctypes.c_longlong), ("theta", ctypes.c_int), ("status", ctypes.c_int)]
+                ("sum_size2", ctypes.c_longlong), ("theta", ctypes.c_int), ("status", ctypes.c_int),
+                ("sum_lnRratio", ctypes.c_double), ("R_target", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -65,6 +66,19 @@ class pa_analysis(ctypes.Structure):
                 ("var_mean_absM_jack", ctypes.c_double), ("var_mean_absM_blocked", ctypes.c_double),
                 ("R_eff_M", ctypes.c_double), ("C", ctypes.c_double), ("var_C_jack", ctypes.c_double),
                 ("S_f", ctypes.c_double), ("rho_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+
+
+class pa_weighted(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("M", ctypes.c_int), ("mode", ctypes.c_int), ("beta", ctypes.c_double),
+                ("M_eff", ctypes.c_double), ("max_weight", ctypes.c_double), ("var_minus_betaF", ctypes.c_double),
+                ("minus_betaF_combined", ctypes.c_double), ("e", ctypes.c_double), ("C", ctypes.c_double),
+                ("m", ctypes.c_double), ("m2", ctypes.c_double), ("chi", ctypes.c_double),
+                ("e_plain", ctypes.c_double), ("C_plain", ctypes.c_double), ("m_plain", ctypes.c_double),
+                ("m2_plain", ctypes.c_double), ("chi_plain", ctypes.c_double), ("status", ctypes.c_int),
+                ("pad", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
@@ -101,6 +115,7 @@ SIGNATURES = {
     "pa_record": (ctypes.c_int, [_vp, _vp]),
     "pa_observables": (ctypes.c_int, [_vp, _P(pa_obs)]),
     "pa_analyze": (ctypes.c_int, [_vp, ctypes.c_int, _P(pa_analysis)]),
+    "pa_weighted_average": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "pa_propose_schedule": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            _P(ctypes.c_double), _P(ctypes.c_double)]),
     "pa_schedule_log": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, _P(ctypes.c_longlong)]),

@@ -2,9 +2,10 @@
 // and jackknife errors of the mean over the tree-ordered population and the effective
 // population size R_eff (Sec. IV, Eqs. neff, blocks, blocked_variance, jackknife-blocks,
 // jackknife-variance), and the family entropy S_f with rho_s = R / exp(S_f) (Sec. V,
-// Eq. rhos).
+// Eq. rhos); and the weighted average of independent runs' records (Sec. VIII, Eqs.
+// weighted-averages, modified-weights2: k_weighted, one thread, runs in order).
 //
-// Three launches on the context's stream:
+// The analysis is three launches on the context's stream:
 //   k_ana_blocks    one CUDA block per analysis block: exact int64 sums of E, E^2, |M|, M^2
 //                   over the block's slot range [floor(b R / n), floor((b + 1) R / n));
 //   k_ana_families  family sizes (runs of equal ids in slot order) into a size histogram;
@@ -214,7 +215,74 @@ __global__ void __launch_bounds__(kAnaFinalThreads) k_ana_final(const DevState *
     *out = o;
 }
 
+__global__ void k_weighted(const pa_obs *rec, int M, int mode, pa_weighted *out)
+{
+    if (threadIdx.x != 0) return;
+    pa_weighted o{};
+    o.M = M;
+    o.mode = mode;
+    o.step = rec[0].step;
+    o.beta = rec[0].beta;
+    int status = 0;
+    for (int m = 0; m < M; ++m) {
+        if (rec[m].step != o.step || rec[m].beta != o.beta) status = PA_ERR_INVALID_ARG;
+        if (!status && rec[m].status) status = rec[m].status;
+    }
+    o.status = status;
+    auto lw = [&](int m) {
+        return __dadd_rn(__dadd_rn(log((double)rec[m].R), rec[m].minus_betaF), mode == 1 ? rec[m].sum_lnRratio : 0.0);
+    };
+    auto lz = [&](int m) { return __dadd_rn(log((double)rec[m].R_target), rec[m].minus_betaF); };
+    double mx = -INFINITY, mz = -INFINITY, sR = 0.0;
+    for (int m = 0; m < M; ++m) {
+        mx = fmax(mx, lw(m));
+        mz = fmax(mz, lz(m));
+        sR = __dadd_rn(sR, (double)rec[m].R_target);
+    }
+    double s = 0.0, sz = 0.0;
+    for (int m = 0; m < M; ++m) {
+        s = __dadd_rn(s, exp(__dsub_rn(lw(m), mx)));
+        sz = __dadd_rn(sz, exp(__dsub_rn(lz(m), mz)));
+    }
+    double w2 = 0.0, wmax = 0.0, meanF = 0.0;
+    double acc[5] = {0, 0, 0, 0, 0}, pl[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m < M; ++m) {
+        const double om = __ddiv_rn(exp(__dsub_rn(lw(m), mx)), s);
+        w2 = __dadd_rn(w2, __dmul_rn(om, om));
+        wmax = fmax(wmax, om);
+        const double v[5] = {rec[m].e, rec[m].C, rec[m].m, rec[m].m2, rec[m].chi};
+        for (int q = 0; q < 5; ++q) {
+            acc[q] = __dadd_rn(acc[q], __dmul_rn(om, v[q]));
+            pl[q] = __dadd_rn(pl[q], v[q]);
+        }
+        meanF = __dadd_rn(meanF, rec[m].minus_betaF);
+    }
+    meanF = __ddiv_rn(meanF, (double)M);
+    double vF = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double d = __dsub_rn(rec[m].minus_betaF, meanF);
+        vF = __dadd_rn(vF, __dmul_rn(d, d));
+    }
+    o.var_minus_betaF = M > 1 ? __ddiv_rn(vF, (double)(M - 1)) : 0.0;
+    o.M_eff = __ddiv_rn(1.0, w2);
+    o.max_weight = wmax;
+    o.minus_betaF_combined = __dsub_rn(__dadd_rn(mz, log(sz)), log(sR));
+    o.e = acc[0]; o.C = acc[1]; o.m = acc[2]; o.m2 = acc[3]; o.chi = acc[4];
+    o.e_plain = __ddiv_rn(pl[0], (double)M);
+    o.C_plain = __ddiv_rn(pl[1], (double)M);
+    o.m_plain = __ddiv_rn(pl[2], (double)M);
+    o.m2_plain = __ddiv_rn(pl[3], (double)M);
+    o.chi_plain = __ddiv_rn(pl[4], (double)M);
+    *out = o;
+}
+
 }  // namespace
+
+cudaError_t launch_weighted(const pa_obs *rec, int M, int mode, pa_weighted *out, cudaStream_t s)
+{
+    k_weighted<<<1, 32, 0, s>>>(rec, M, mode, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_analysis(const DevState *st, const int *level, const int *mag, const int *fam, int N,
                             double beta, int n, long long capacity, long long *blk, int *sizes, pa_analysis *out,

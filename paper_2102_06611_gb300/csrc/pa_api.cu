@@ -478,6 +478,7 @@ pa_status pa_record(pa_ctx *c, void *device_dst)
     if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
     pa::ObsArgs a{};
     a.L = c->cfg.L;
+    a.R_target = c->cfg.R;
     a.step = c->step;
     a.beta = c->beta;
     a.dbeta = c->dbeta;
@@ -502,6 +503,16 @@ pa_status pa_observables(pa_ctx *c, pa_obs *host_out)
                                     c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "observables copy");
     return sync_and_check(c);
+}
+
+pa_status pa_weighted_average(const void *records_dev, int M, int mode, void *out_dev, void *stream)
+{
+    if (!records_dev || !out_dev || M < 1 || (mode != 0 && mode != 1) ||
+        (reinterpret_cast<uintptr_t>(records_dev) & 7u) || (reinterpret_cast<uintptr_t>(out_dev) & 7u))
+        return PA_ERR_INVALID_ARG;
+    cudaError_t e = pa::launch_weighted(static_cast<const pa_obs *>(records_dev), M, mode,
+                                        static_cast<pa_weighted *>(out_dev), static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PA_OK : PA_ERR_CUDA;
 }
 
 pa_status pa_analyze(pa_ctx *c, int n_blocks, pa_analysis *host_out)

@@ -209,6 +209,7 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
             s.theta = d.theta;
             pa::ObsArgs &o = r.obs[cur];
             o.L = d.cfg.L;
+            o.R_target = d.cfg.R;
             o.st = st;
             o.hist = reinterpret_cast<int *>(work + L.ws.hist);
             o.fam = reinterpret_cast<int *>(base + L.fam[cur]);

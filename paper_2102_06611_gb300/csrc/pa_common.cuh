@@ -198,6 +198,7 @@ struct DevState {
     int theta;
     int update;               // pa_update_kind of the run (selects the thresholds below)
     unsigned long long mn_total;  // multinomial resampling: sum of the integer parent weights
+    double sum_lnR;           // sum_k ln(R_{k-1} / R) over the resamplings so far
 };
 
 __device__ __forceinline__ void set_error(DevState *st, int code)

@@ -101,6 +101,7 @@ cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, int update
 
 struct ObsArgs {
     int L;
+    long long R_target;
     long long step;
     double beta, dbeta;
     int theta;
@@ -112,6 +113,9 @@ struct ObsArgs {
 };
 
 cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s);
+
+// Weighted average over independent runs' records (pa_analysis.cu).
+cudaError_t launch_weighted(const pa_obs *rec, int M, int mode, pa_weighted *out, cudaStream_t s);
 
 // Population analysis (pa_analysis.cu): block sums, family-size histogram, binary64 results.
 cudaError_t launch_analysis(const DevState *st, const int *level, const int *mag, const int *fam, int N,

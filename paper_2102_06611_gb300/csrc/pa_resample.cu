@@ -241,6 +241,7 @@ __device__ __forceinline__ void table_body(const ResampleArgs &a)
         const double lnQ = __dadd_rn(-__dmul_rn(dbeta, (double)Eref), log(__ddiv_rn(S, (double)Rp)));
         st->lnQ = lnQ;
         st->sum_lnQ = __dadd_rn(st->sum_lnQ, lnQ);
+        st->sum_lnR = __dadd_rn(st->sum_lnR, log(__ddiv_rn((double)Rp, (double)a.R_target)));
         st->S = S;
         st->kmin = kmin;
         st->R_prev = Rp;
@@ -627,6 +628,8 @@ __device__ __forceinline__ void obs_body(const ObsArgs &a)
     o.sum_size2 = f2;
     o.theta = a.theta;
     o.status = st->error;
+    o.sum_lnRratio = st->sum_lnR;
+    o.R_target = a.R_target;
     *a.dst = o;
 }
 

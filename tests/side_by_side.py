@@ -8,7 +8,7 @@ import numpy as np
 
 import oracle
 
-FLOAT_KEYS = ("e", "C", "m", "m2", "chi", "lnQ", "minus_betaF", "rho_t")
+FLOAT_KEYS = ("e", "C", "m", "m2", "chi", "lnQ", "minus_betaF", "rho_t", "sum_lnRratio")
 REL_TOL = 1e-12
 
 
