@@ -31,6 +31,16 @@ int rpw_for(int L)
     return 32 / (L / pa::rows_per_lane(L));
 }
 
+// Replica groups per work item: runs whose groups are small (below 2^14 attempts: small L or
+// few sweeps) take 4 to 16 groups per item so that an item holds about 2^16 attempts and the
+// per-item cost (work counter, run lookup, sums) stays small; other runs take one.
+int ipw_for(int L, int theta)
+{
+    const long long per_group = (long long)L * L * rpw_for(L) * (theta > 1 ? theta : 1);
+    const long long g = (65536 + per_group - 1) / per_group;
+    return g < 4 ? 1 : (int)(g > 16 ? 16 : g);
+}
+
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct RunLayout {
@@ -167,6 +177,7 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
         r.theta = d.theta;
         r.n_temps = d.n_temps;
         r.rpw = rpw_for(d.cfg.L);
+        r.ipw = ipw_for(d.cfg.L, d.theta);
         r.chunks16 = pa::bytes_per_replica(d.cfg.L) / 16;
         const unsigned int k0 = (unsigned int)(d.cfg.seed & 0xffffffffu), k1 = (unsigned int)(d.cfg.seed >> 32);
         for (int cur = 0; cur < 2; ++cur) {
@@ -239,8 +250,10 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     std::vector<int> order((size_t)n_runs);
     for (int i = 0; i < n_runs; ++i) order[(size_t)i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        const double cx = (double)runs[x].cfg.L * runs[x].cfg.L * rpw_for(runs[x].cfg.L) * std::max(1, runs[x].theta);
-        const double cy = (double)runs[y].cfg.L * runs[y].cfg.L * rpw_for(runs[y].cfg.L) * std::max(1, runs[y].theta);
+        const double cx = (double)runs[x].cfg.L * runs[x].cfg.L * rpw_for(runs[x].cfg.L) *
+                          ipw_for(runs[x].cfg.L, runs[x].theta) * std::max(1, runs[x].theta);
+        const double cy = (double)runs[y].cfg.L * runs[y].cfg.L * rpw_for(runs[y].cfg.L) *
+                          ipw_for(runs[y].cfg.L, runs[y].theta) * std::max(1, runs[y].theta);
         return cx > cy;
     });
     pa::BatchCtl ctl{};

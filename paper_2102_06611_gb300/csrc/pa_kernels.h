@@ -167,7 +167,7 @@ struct BatchRun {
     SweepArgs sw[2];      // sweep arguments with `cur` = 0 / 1
     int L, theta, n_temps, rpw;
     int chunks16;
-    int pad;
+    int ipw;              // replica groups (of rpw replicas) per work item
 };
 
 struct BatchState {       // per run, mutable

@@ -876,7 +876,8 @@ __global__ void k_b_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl
         if (dst->error) continue;
         if (flip) s.cur ^= 1;
         const long long R = dst->R_cur;
-        total += (R + runs[r].rpw - 1) / runs[r].rpw;
+        const long long per_item = (long long)runs[r].rpw * runs[r].ipw;
+        total += (R + per_item - 1) / per_item;
     }
     item_start[n] = total;
     ctl->total_items = total;

@@ -29,12 +29,78 @@ cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cuda
 }
 
 // ------------------------------------------------------------------------------ batches
-// One persistent launch sweeps every active run of a batch: warps take work items (one
-// replica group of one run) from a global counter, largest items first (runs are ordered by
-// cost), and dispatch on the run's lattice size.  The per-replica arithmetic is exactly the
-// single-run kernel's, with the histogram and sums going to the run's own workspace.
+// One persistent launch sweeps every active run of a batch: warps take work items (ipw
+// consecutive replica groups of one run) from a global counter, largest items first (runs
+// are ordered by cost), and dispatch on the run's lattice size.  The per-replica arithmetic
+// is exactly the single-run kernel's, with the histogram and sums going to the run's own
+// workspace: level counts aggregated over the warp, the seven exact sums once per item.
 template <int L>
-__device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
+__device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
+                                            unsigned long long *tq_eq, unsigned long long *tq_a4,
+                                            unsigned int *tq_code, const unsigned int *rk0, const unsigned int *rk1,
+                                            unsigned long long *v)
+{
+    using Gm = Geo<L>;
+    using W = typename Gm::W;
+    constexpr int N = Gm::N, G = Gm::G, RPW = Gm::RPW, RPL = Gm::RPL;
+    const int q = lane & (G - 1);
+    const int sub = lane / G;
+    const int r0 = q * RPL;
+    const long long R = a.st->R_cur;
+    const long long j = g * RPW + sub;
+    const bool active = j < R;
+    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
+    W A[RPL], B[RPL];
+    W *rep = reinterpret_cast<W *>(a.spins) + (size_t)(active ? j : 0) * (2 * L);
+    if (active) load_rows<L>(rep, r0, A, B);
+    else {
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
+    }
+    const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), nullptr, tq_code};
+    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1,
+                         a.k0, a.k1, ac, tq);
+    int anti, ups;
+    measure_rows<L>(A, B, r0, lane, anti, ups);
+    anti = group_sum<G>(anti);
+    ups = group_sum<G>(ups);
+    int level = -1;
+    if (active) {
+        if (dry) {
+            store_rows<L>(reinterpret_cast<W *>(const_cast<void *>(spare)) + (size_t)j * (2 * L), r0, A, B);
+        } else {
+            if (a.theta > 0) store_rows<L>(rep, r0, A, B);
+            if (q == 0) {
+                level = anti >> 1;
+                const int M = 2 * ups - N;
+                const unsigned long long k0 = (unsigned long long)a.level[j];
+                const unsigned long long k1 = (unsigned long long)level;
+                a.level_snap[j] = (int)k0;
+                a.level[j] = level;
+                a.mag[j] = M;
+                v[0] += (unsigned long long)(M < 0 ? -M : M);
+                v[1] += (unsigned long long)((long long)M * M);
+                v[2] += k0;
+                v[3] += k0 * k0;
+                v[4] += k1;
+                v[5] += k1 * k1;
+                v[6] += k0 * k1;
+            }
+        }
+    }
+    if constexpr (RPW >= 8) {
+        // many replicas per warp: one atomic per distinct level
+        const unsigned int grp = __match_any_sync(0xffffffffu, level);
+        if (level >= 0 && lane == __ffs((int)grp) - 1) atomicAdd(&a.hist[level], __popc(grp));
+    } else if (level >= 0) {
+        atomicAdd(&a.hist[level], 1);
+    }
+}
+
+// Items of one group (ipw = 1) take this form, which nvcc compiles to faster code for them
+// than the general loop below (measured).
+template <int L>
+__device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
                                            unsigned long long *tq_eq, unsigned long long *tq_a4,
                                            unsigned int *tq_code)
 {
@@ -107,6 +173,44 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
     }
 }
 
+template <int L>
+__device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare, long long item, int ipw, int lane,
+                                           int dry, unsigned long long *tq_eq, unsigned long long *tq_a4,
+                                           unsigned int *tq_code)
+{
+    constexpr int RPW = Geo<L>::RPW;
+    if (ipw == 1) {  // uniform over the warp
+        batch_item_single<L>(a, spare, item, lane, dry, tq_eq, tq_a4, tq_code);
+        return;
+    }
+    unsigned int rk0[10], rk1[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
+        rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
+    }
+    const long long R = a.st->R_cur;
+    unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 1
+    for (int k = 0; k < ipw; ++k) {
+        const long long g = item * ipw + k;
+        if (g * RPW >= R) break;  // uniform over the warp
+        batch_group<L>(a, spare, g, lane, dry, tq_eq, tq_a4, tq_code, rk0, rk1, v);
+    }
+    // every replica of the item belongs to one run: one atomic per sum and item
+#pragma unroll
+    for (int i = 0; i < 7; ++i) v[i] = group_sum<32>(v[i]);
+    if (lane == 0 && !dry) {
+        atomicAdd(&a.st->sum_absM, v[0]);
+        atomicAdd(&a.st->sum_M2, v[1]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), v[2]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), v[3]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), v[4]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), v[5]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), v[6]);
+    }
+}
+
 __global__ void __launch_bounds__(256, 2) k_b_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl,
                                                      const int *order, const long long *item_start, int n)
 {
@@ -138,17 +242,18 @@ __global__ void __launch_bounds__(256, 2) k_b_sweep(const BatchRun *runs, const 
         a.t0 = 0;
         a.theta = run.theta;
         const void *spare = run.sw[s.cur ^ 1].spins;
-        const long long g = item - item_start[lo];
+        const long long it = item - item_start[lo];
+        const int ipw = run.ipw;
         switch (run.L) {
-            case 4: batch_item<4>(a, spare, g, lane, dry, qe, qa, qc); break;
-            case 8: batch_item<8>(a, spare, g, lane, dry, qe, qa, qc); break;
-            case 12: batch_item<12>(a, spare, g, lane, dry, qe, qa, qc); break;
-            case 16: batch_item<16>(a, spare, g, lane, dry, qe, qa, qc); break;
-            case 24: batch_item<24>(a, spare, g, lane, dry, qe, qa, qc); break;
-            case 32: batch_item<32>(a, spare, g, lane, dry, qe, qa, qc); break;
-            case 48: batch_item<48>(a, spare, g, lane, dry, qe, qa, qc); break;
-            case 64: batch_item<64>(a, spare, g, lane, dry, qe, qa, qc); break;
-            case 128: batch_item<128>(a, spare, g, lane, dry, qe, qa, qc); break;
+            case 4: batch_item<4>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
+            case 8: batch_item<8>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
+            case 12: batch_item<12>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
+            case 16: batch_item<16>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
+            case 24: batch_item<24>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
+            case 32: batch_item<32>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
+            case 48: batch_item<48>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
+            case 64: batch_item<64>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
+            case 128: batch_item<128>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
             default: break;
         }
     }
