@@ -862,26 +862,37 @@ __global__ void __launch_bounds__(kCountThreads) k_b_copy(const BatchRun *runs, 
 
 // Switch each resampled run to its new buffers (unless resampling failed) and lay out the
 // persistent sweep's work items: ceil(R_i / replicas-per-item) per run, runs in `order`.
-__global__ void k_b_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
-                          long long *item_start, int n, int flip)
+__global__ void __launch_bounds__(1024) k_b_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl,
+                                                  const int *order, long long *item_start, int n, int flip)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    long long total = 0;
-    for (int p = 0; p < n; ++p) {
-        const int r = order[p];
-        BatchState &s = state[r];
-        item_start[p] = total;
-        if (!s.active) continue;
-        const DevState *dst = runs[r].rs[s.cur].st;
-        if (dst->error) continue;
-        if (flip) s.cur ^= 1;
-        const long long R = dst->R_cur;
-        const long long per_item = (long long)runs[r].rpw * runs[r].ipw;
-        total += (R + per_item - 1) / per_item;
+    // one thread per run position (chunks of 1024), work items per run, exclusive scan
+    long long carry = 0;
+    for (int base = 0; base < n; base += 1024) {
+        const int p = base + (int)threadIdx.x;
+        long long items = 0;
+        if (p < n) {
+            const int r = order[p];
+            BatchState &s = state[r];
+            if (s.active) {
+                const DevState *dst = runs[r].rs[s.cur].st;
+                if (!dst->error) {
+                    if (flip) s.cur ^= 1;
+                    const long long R = dst->R_cur;
+                    const long long per_item = (long long)runs[r].rpw * runs[r].ipw;
+                    items = (R + per_item - 1) / per_item;
+                }
+            }
+        }
+        long long tot;
+        const long long ex = block_exclusive_scan<long long, 1024>(items, &tot);
+        if (p < n) item_start[p] = carry + ex;
+        carry += tot;
     }
-    item_start[n] = total;
-    ctl->total_items = total;
-    ctl->next_item = 0;
+    if (threadIdx.x == 0) {
+        item_start[n] = carry;
+        ctl->total_items = carry;
+        ctl->next_item = 0;
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_b_zero(const BatchRun *runs, const BatchState *state)
@@ -919,7 +930,7 @@ __global__ void __launch_bounds__(1024) k_b_obs(const BatchRun *runs, BatchState
 cudaError_t launch_batch_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
                                long long *item_start, int n, int flip, cudaStream_t s)
 {
-    k_b_items<<<1, 32, 0, s>>>(runs, state, ctl, order, item_start, n, flip);
+    k_b_items<<<1, 1024, 0, s>>>(runs, state, ctl, order, item_start, n, flip);
     return cudaGetLastError();
 }
 
