@@ -111,7 +111,18 @@ struct pa_batch {
     int nblk_max, nlev_max;
     int sweep_grid;
     pa_batch_tuning tuning;
+    pa::BatchSweepPlan plan;
 };
+
+static void destroy_plan(pa::BatchSweepPlan &p)
+{
+    for (int i = 0; i < p.ngroups; ++i) {
+        if (p.side[i]) cudaStreamDestroy(p.side[i]);
+        if (p.join[i]) cudaEventDestroy(p.join[i]);
+    }
+    if (p.fork) cudaEventDestroy(p.fork);
+    p = pa::BatchSweepPlan{};
+}
 
 extern "C" {
 
@@ -246,10 +257,13 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
         }
         if (e != cudaSuccess) break;
     }
-    // work items of the largest per-item cost first (longest-processing-time order)
+    // runs grouped by lattice size, and within a size the largest per-item cost first
+    // (longest-processing-time order)
     std::vector<int> order((size_t)n_runs);
     for (int i = 0; i < n_runs; ++i) order[(size_t)i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const int gx = pa::batch_group_of(runs[x].cfg.L), gy = pa::batch_group_of(runs[y].cfg.L);
+        if (gx != gy) return gx < gy;
         const double cx = (double)runs[x].cfg.L * runs[x].cfg.L * rpw_for(runs[x].cfg.L) *
                           ipw_for(runs[x].cfg.L, runs[x].theta) * std::max(1, runs[x].theta);
         const double cy = (double)runs[y].cfg.L * runs[y].cfg.L * rpw_for(runs[y].cfg.L) *
@@ -258,6 +272,22 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     });
     pa::BatchCtl ctl{};
     ctl.n = n_runs;
+    for (int g = 0; g < pa::kBatchGroups; ++g) ctl.pbeg[g] = ctl.pend[g] = 0;
+    for (int p = 0; p < n_runs; ++p) {
+        const int g = pa::batch_group_of(runs[order[(size_t)p]].cfg.L);
+        if (p == 0 || pa::batch_group_of(runs[order[(size_t)p - 1]].cfg.L) != g) ctl.pbeg[g] = p;
+        ctl.pend[g] = p + 1;
+    }
+    // one persistent sweep kernel per size present, on its own side stream
+    b->plan = pa::BatchSweepPlan{};
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->plan.fork, cudaEventDisableTiming);
+    for (int g = 0; g < pa::kBatchGroups && e == cudaSuccess; ++g) {
+        if (ctl.pend[g] == ctl.pbeg[g]) continue;
+        const int i = b->plan.ngroups++;
+        b->plan.L[i] = runs[order[(size_t)ctl.pbeg[g]]].cfg.L;
+        e = cudaStreamCreateWithFlags(&b->plan.side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->plan.join[i], cudaEventDisableTiming);
+    }
     char *tb = b->arena;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tb + b->t.runs, table.data(), sizeof(pa::BatchRun) * table.size(), cudaMemcpyHostToDevice,
@@ -279,10 +309,20 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     if (e == cudaSuccess) e = pa::launch_batch_record(d_runs, d_state, d_records, n_runs, b->user);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->user);  // host tables must outlive the copies
 
-    // autotune the persistent sweep grid on dry sweeps (spare buffers only)
-    const int max_bps = pa::batch_sweep_max_blocks_per_sm();
+    // autotune the blocks per SM of the persistent sweeps on dry sweeps (spare buffers
+    // only); each size's kernel gets min(candidate, its occupancy) blocks per SM
+    int occ[pa::kBatchGroups];
+    int max_bps = 1;
+    for (int i = 0; i < b->plan.ngroups; ++i) {
+        occ[i] = pa::batch_sweep_max_blocks_per_sm(b->plan.L[i]);
+        max_bps = std::max(max_bps, occ[i]);
+    }
+    auto set_grids = [&](int bps) {
+        for (int i = 0; i < b->plan.ngroups; ++i) b->plan.grid[i] = b->num_sms * std::min(bps, occ[i]);
+    };
     std::memset(&b->tuning, 0, sizeof(b->tuning));
     b->sweep_grid = b->num_sms * max_bps;
+    set_grids(max_bps);
     if (e == cudaSuccess) {
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
@@ -293,11 +333,12 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
         int nc = 0;
         for (int bps = 1; bps <= max_bps && nc < 4 && e == cudaSuccess; ++bps, ++nc) {
             const int grid = b->num_sms * bps;
+            set_grids(bps);
             float ms = 0.f;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                 e = pa::launch_batch_items(d_runs, d_state, d_ctl, d_order, d_items, n_runs, 0, b->user);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, b->user);
-                if (e == cudaSuccess) e = pa::launch_batch_sweep(d_runs, d_state, d_ctl, d_order, d_items, n_runs, grid, b->user);
+                if (e == cudaSuccess) e = pa::launch_batch_sweep(d_runs, d_state, d_ctl, d_order, d_items, b->plan, b->user);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, b->user);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -311,6 +352,7 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
         }
         b->tuning.n_candidates = nc;
         b->tuning.chosen_grid = b->sweep_grid;
+        set_grids(b->sweep_grid / b->num_sms);
         dry = 0;
         if (e == cudaSuccess)
             e = cudaMemcpy(&reinterpret_cast<pa::BatchCtl *>(tb + b->t.ctl)->dry, &dry, sizeof(int), cudaMemcpyHostToDevice);
@@ -322,12 +364,13 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = pa::launch_batch_step(d_runs, d_state, d_ctl, d_order, d_items, d_records, n_runs,
-                                               b->nblk_max, b->nlev_max, b->sweep_grid, b->num_sms, b->cs);
+                                               b->nblk_max, b->nlev_max, b->plan, b->cs);
         e = cudaStreamEndCapture(b->cs, &b->graph);
         if (le != cudaSuccess) e = le;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     if (e != cudaSuccess) {
+        destroy_plan(b->plan);
         cudaEventDestroy(b->ev_in);
         cudaEventDestroy(b->ev_out);
         cudaStreamDestroy(b->cs);
@@ -417,6 +460,7 @@ void pa_batch_destroy(pa_batch *b)
     cudaStreamSynchronize(b->cs);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    destroy_plan(b->plan);
     cudaEventDestroy(b->ev_in);
     cudaEventDestroy(b->ev_out);
     cudaStreamDestroy(b->cs);

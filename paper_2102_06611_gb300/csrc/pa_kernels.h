@@ -178,23 +178,46 @@ struct BatchState {       // per run, mutable
     double beta, beta_prev;
 };
 
+// Lattice sizes of batches, one persistent sweep kernel each.
+constexpr int kBatchGroups = 9;
+__host__ __device__ constexpr int batch_group_of(int L)
+{
+    return L == 4 ? 0 : L == 8 ? 1 : L == 12 ? 2 : L == 16 ? 3 : L == 24 ? 4 : L == 32 ? 5 : L == 48 ? 6
+           : L == 64 ? 7 : L == 128 ? 8 : -1;
+}
+
 struct BatchCtl {
-    unsigned long long next_item;  // work counter of the persistent sweep
+    unsigned long long next_item;  // work counter (unused by the per-size kernels)
     long long total_items;
     int n;
     int dry;              // autotuning: sweep into the spare buffer, measure nothing
+    // per lattice-size group g: runs at order positions [pbeg[g], pend[g]) (fixed at
+    // initialisation), their work items [begin[g], end[g]) and the group's work counter
+    int pbeg[kBatchGroups], pend[kBatchGroups];
+    long long begin[kBatchGroups], end[kBatchGroups];
+    unsigned long long next[kBatchGroups];
+};
+
+// Host plan of the sweep phase: one persistent kernel per lattice size present, launched on
+// side streams forked from (and joined back into) the step's stream.
+struct BatchSweepPlan {
+    int ngroups;
+    int L[kBatchGroups];
+    int grid[kBatchGroups];
+    cudaStream_t side[kBatchGroups];
+    cudaEvent_t fork, join[kBatchGroups];
 };
 
 cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
                               long long *item_start, pa_obs *records, int n, int nblk_max, int nlev_max,
-                              int sweep_grid, int num_sms, cudaStream_t s);
+                              const BatchSweepPlan &plan, cudaStream_t s);
 cudaError_t launch_batch_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
                                long long *item_start, int n, int dry, cudaStream_t s);
 cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
-                               const long long *item_start, int n, int grid, cudaStream_t s);
+                               const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s);
 cudaError_t launch_batch_record(const BatchRun *runs, BatchState *state, pa_obs *records, int n,
                                 cudaStream_t s);
-int batch_sweep_max_blocks_per_sm();
+int batch_sweep_max_blocks_per_sm(int L);
 
 cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
                           unsigned long long *out, cudaStream_t s);

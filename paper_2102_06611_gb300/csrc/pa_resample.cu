@@ -888,10 +888,19 @@ __global__ void __launch_bounds__(1024) k_b_items(const BatchRun *runs, BatchSta
         if (p < n) item_start[p] = carry + ex;
         carry += tot;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         item_start[n] = carry;
         ctl->total_items = carry;
         ctl->next_item = 0;
+    }
+    if (threadIdx.x < kBatchGroups) {
+        const int g = threadIdx.x;
+        const long long b0 = ctl->pbeg[g] < ctl->pend[g] ? item_start[ctl->pbeg[g]] : 0;
+        const long long b1 = ctl->pbeg[g] < ctl->pend[g] ? (ctl->pend[g] == n ? carry : item_start[ctl->pend[g]]) : 0;
+        ctl->begin[g] = b0;
+        ctl->end[g] = b1;
+        ctl->next[g] = (unsigned long long)b0;
     }
 }
 
@@ -946,9 +955,8 @@ cudaError_t launch_batch_record(const BatchRun *runs, BatchState *state, pa_obs 
 
 cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
                               long long *item_start, pa_obs *records, int n, int nblk_max, int nlev_max,
-                              int sweep_grid, int num_sms, cudaStream_t s)
+                              const BatchSweepPlan &plan, cudaStream_t s)
 {
-    (void)num_sms;
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_b_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -970,7 +978,7 @@ cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl 
     if ((e = launch_batch_items(runs, state, ctl, order, item_start, n, 1, s)) != cudaSuccess) return e;
     k_b_zero<<<dim3((nlev_max + 1023) / 1024, n), 1024, 0, s>>>(runs, state);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_batch_sweep(runs, state, ctl, order, item_start, n, sweep_grid, s)) != cudaSuccess) return e;
+    if ((e = launch_batch_sweep(runs, state, ctl, order, item_start, plan, s)) != cudaSuccess) return e;
     return launch_batch_record(runs, state, records, n, s);
 }
 

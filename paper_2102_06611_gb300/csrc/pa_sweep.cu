@@ -29,9 +29,10 @@ cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cuda
 }
 
 // ------------------------------------------------------------------------------ batches
-// One persistent launch sweeps every active run of a batch: warps take work items (ipw
-// consecutive replica groups of one run) from a global counter, largest items first (runs
-// are ordered by cost), and dispatch on the run's lattice size.  The per-replica arithmetic
+// One persistent launch per lattice size present sweeps the active runs of that size (the
+// launches run concurrently on side streams): warps take work items (ipw consecutive
+// replica groups of one run) from the size's counter, largest items first (runs are
+// ordered by cost within a size).  The per-replica arithmetic
 // is exactly the single-run kernel's, with the histogram and sums going to the run's own
 // workspace: level counts aggregated over the warp, the seven exact sums once per item.
 template <int L>
@@ -211,24 +212,30 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
     }
 }
 
+// Persistent sweep over the work items of the runs with lattice size L (group g): warps
+// take items from the group's counter; the item's run is found by bisection over the
+// group's order positions.
+template <int L>
 __global__ void __launch_bounds__(256, 2) k_b_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl,
-                                                     const int *order, const long long *item_start, int n)
+                                                     const int *order, const long long *item_start)
 {
+    constexpr int g = batch_group_of(L);
     const int lane = threadIdx.x & 31;
     const int dry = ctl->dry;
-    constexpr int TQ = batch_tie_queue_len();  // per warp; 8 warps per block
+    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp; 8 warps per block
     __shared__ unsigned long long tq_eq[8 * TQ], tq_a4[8 * TQ];
     __shared__ unsigned int tq_code[8 * TQ];
     const int wib = threadIdx.x >> 5;
     unsigned long long *qe = tq_eq + wib * TQ, *qa = tq_a4 + wib * TQ;
     unsigned int *qc = tq_code + wib * TQ;
-    const long long total = ctl->total_items;
+    const long long end = ctl->end[g];
+    const int p0 = ctl->pbeg[g], p1 = ctl->pend[g];
     for (;;) {
         long long item = 0;
-        if (lane == 0) item = (long long)atomicAdd(&ctl->next_item, 1ull);
+        if (lane == 0) item = (long long)atomicAdd(&ctl->next[g], 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total) break;
-        int lo = 0, hi = n;  // largest lo with item_start[lo] <= item
+        if (item >= end) break;
+        int lo = p0, hi = p1;  // largest lo with item_start[lo] <= item
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (item_start[mid] <= item) lo = mid;
@@ -242,35 +249,65 @@ __global__ void __launch_bounds__(256, 2) k_b_sweep(const BatchRun *runs, const 
         a.t0 = 0;
         a.theta = run.theta;
         const void *spare = run.sw[s.cur ^ 1].spins;
-        const long long it = item - item_start[lo];
-        const int ipw = run.ipw;
-        switch (run.L) {
-            case 4: batch_item<4>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            case 8: batch_item<8>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            case 12: batch_item<12>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            case 16: batch_item<16>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            case 24: batch_item<24>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            case 32: batch_item<32>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            case 48: batch_item<48>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            case 64: batch_item<64>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            case 128: batch_item<128>(a, spare, it, ipw, lane, dry, qe, qa, qc); break;
-            default: break;
-        }
+        batch_item<L>(a, spare, item - item_start[lo], run.ipw, lane, dry, qe, qa, qc);
     }
 }
 
-cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
-                               const long long *item_start, int n, int grid, cudaStream_t s)
+template <int L>
+static cudaError_t launch_b_sweep_t(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
+                                    const long long *item_start, int grid, cudaStream_t s)
 {
-    k_b_sweep<<<grid, 256, 0, s>>>(runs, state, ctl, order, item_start, n);
+    k_b_sweep<L><<<grid, 256, 0, s>>>(runs, state, ctl, order, item_start);
     return cudaGetLastError();
 }
 
-int batch_sweep_max_blocks_per_sm()
+cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
+                               const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s)
+{
+    cudaError_t e = cudaEventRecord(plan.fork, s);
+    for (int i = 0; i < plan.ngroups && e == cudaSuccess; ++i) {
+        cudaStream_t t = plan.side[i];
+        if ((e = cudaStreamWaitEvent(t, plan.fork, 0)) != cudaSuccess) break;
+        switch (plan.L[i]) {
+            case 4: e = launch_b_sweep_t<4>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 8: e = launch_b_sweep_t<8>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 12: e = launch_b_sweep_t<12>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 16: e = launch_b_sweep_t<16>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 24: e = launch_b_sweep_t<24>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 32: e = launch_b_sweep_t<32>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 48: e = launch_b_sweep_t<48>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 64: e = launch_b_sweep_t<64>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 128: e = launch_b_sweep_t<128>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            default: e = cudaErrorInvalidValue; break;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(plan.join[i], t);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan.join[i], 0);
+    }
+    return e;
+}
+
+template <int L>
+static int b_sweep_occupancy()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep, 256, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep<L>, 256, 0) != cudaSuccess) return 1;
     return b > 0 ? b : 1;
+}
+
+int batch_sweep_max_blocks_per_sm(int L)
+{
+    switch (L) {
+        case 4: return b_sweep_occupancy<4>();
+        case 8: return b_sweep_occupancy<8>();
+        case 12: return b_sweep_occupancy<12>();
+        case 16: return b_sweep_occupancy<16>();
+        case 24: return b_sweep_occupancy<24>();
+        case 32: return b_sweep_occupancy<32>();
+        case 48: return b_sweep_occupancy<48>();
+        case 64: return b_sweep_occupancy<64>();
+        case 128: return b_sweep_occupancy<128>();
+        default: return 1;
+    }
 }
 
 }  // namespace pa

@@ -223,16 +223,6 @@ struct SweepStyle {
     static constexpr int TQ_LEN = TIE_QUEUE ? 32 * WORDS : 1;  // queue entries per warp
 };
 
-// tie queue entries per warp that serve every lattice size (persistent batch kernel)
-constexpr int batch_tie_queue_len()
-{
-    const int v[] = {SweepStyle<4>::TQ_LEN,  SweepStyle<8>::TQ_LEN,  SweepStyle<12>::TQ_LEN,
-                     SweepStyle<16>::TQ_LEN, SweepStyle<24>::TQ_LEN, SweepStyle<32>::TQ_LEN,
-                     SweepStyle<48>::TQ_LEN, SweepStyle<64>::TQ_LEN, SweepStyle<128>::TQ_LEN};
-    int m = 1;
-    for (int x : v) m = x > m ? x : m;
-    return m;
-}
 
 // Per-launch constants.  T = floor(e^{-4 beta} 2^32) (class a = 3) or floor(e^{-8 beta} 2^32)
 // (a = 4), T in [0, 2^32], split as T = top 2^24 + low: m[k] = all ones iff bit 7 - k of top
