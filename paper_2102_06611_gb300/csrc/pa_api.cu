@@ -120,6 +120,40 @@ long long read_R(pa_ctx *c, bool prev, pa_status *st)
     return R;
 }
 
+// The acceptance thresholds of the sweep kernel's parameters, in the same binary64
+// arithmetic as the device (pa_common.cuh: det_exp, metropolis_threshold, heatbath_threshold;
+// host code is compiled without FMA contraction): Cody-Waite reduction with ln 2 split into
+// a 32-bit head and a tail, degree-13 Taylor polynomial in Horner form, every operation
+// rounded on its own.
+double host_det_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.5) return HUGE_VAL;
+    if (x < -745.5) return 0.0;
+    const double kLn2Hi = 0x1.62e42feep-1;
+    const double kLn2Lo = 0x1.a39ef35793c76p-33;
+    const double kInvLn2 = 0x1.71547652b82fep+0;
+    const double k = std::rint(x * kInvLn2);
+    const double r = (x + -(k * kLn2Hi)) + -(k * kLn2Lo);
+    const double c[14] = {1.0 / 6227020800.0, 1.0 / 479001600.0, 1.0 / 39916800.0, 1.0 / 3628800.0, 1.0 / 362880.0,
+                          1.0 / 40320.0, 1.0 / 5040.0, 1.0 / 720.0, 1.0 / 120.0, 1.0 / 24.0, 1.0 / 6.0, 0.5, 1.0, 1.0};
+    double p = c[0];
+    for (int i = 1; i < 14; ++i) p = p * r + c[i];
+    return std::ldexp(p, (int)k);
+}
+
+void host_thresholds(int update, double beta, unsigned long long *T4, unsigned long long *T8)
+{
+    const double y4 = 4.0 * beta, y8 = 8.0 * beta;
+    if (update == PA_UPDATE_HEATBATH) {
+        *T4 = (unsigned long long)std::floor((1.0 / (1.0 + host_det_exp(y4))) * 4294967296.0);
+        *T8 = (unsigned long long)std::floor((1.0 / (1.0 + host_det_exp(y8))) * 4294967296.0);
+    } else {
+        *T4 = (unsigned long long)std::floor(host_det_exp(-y4) * 4294967296.0);
+        *T8 = (unsigned long long)std::floor(host_det_exp(-y8) * 4294967296.0);
+    }
+}
+
 bool aligned256(const void *p) { return p && ((reinterpret_cast<uintptr_t>(p) & 255u) == 0); }
 
 }  // namespace
@@ -194,6 +228,7 @@ pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_
         a.step = 0;
         a.t0 = 0;
         a.theta = 0;
+        host_thresholds(cfg->update, 0.0, &a.T4, &a.T8);
         e = pa::launch_sweep(cfg->L, true, a, c->num_sms, c->stream);
     }
     if (e != cudaSuccess) {
@@ -284,6 +319,7 @@ static pa_status sweep_and_measure(pa_ctx *c, int theta)
     a.t0 = c->sweeps_in_step;
     a.theta = theta;
     a.update = c->cfg.update;
+    host_thresholds(c->cfg.update, c->beta, &a.T4, &a.T8);
     e = pa::launch_sweep(c->cfg.L, false, a, c->num_sms, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->measured = true;

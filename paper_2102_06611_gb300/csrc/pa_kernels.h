@@ -62,6 +62,10 @@ struct SweepArgs {
     int t0;                 // sweeps already done at this step (sweep numbering offset)
     int theta;
     int update;             // pa_update_kind (the init kernel ignores it)
+    // the run's acceptance thresholds at the current beta, computed on the host with the
+    // same binary64 arithmetic as DevState::T4 / T8 (k_sweep reads them from its
+    // parameters, where they are warp-uniform operands, and checks them against DevState)
+    unsigned long long T4, T8;
 };
 
 cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s);

@@ -818,7 +818,9 @@ __global__ void __launch_bounds__(256, (L == 128 ? 2 : PA_SWEEP_MIN_BLOCKS)) k_s
         rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
         rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
     }
-    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
+    const Accept<W> ac = make_accept<L>(a.T4, a.T8);
+    if (!INIT && blockIdx.x == 0 && threadIdx.x == 0 && (a.T4 != a.st->T4 || a.T8 != a.st->T8))
+        set_error(a.st, PA_ERR_NUMERIC);  // host and device thresholds disagree (never expected)
 
     // per-block exact sums: |M|, M^2, and the levels at the step start (0) and now (1):
     // k0, k0^2, k1, k1^2, k0 k1
