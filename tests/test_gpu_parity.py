@@ -168,10 +168,10 @@ def test_call_order_errors():
 
 
 # ------------------------------------------------------------------------------ full size
-def _replay_steps(L, R, kind, seed, betas, theta, n_sample):
+def _replay_steps(L, R, kind, seed, betas, theta, n_sample, update="metropolis"):
     """Run the device at full size; replay every resampling in full and a sample of the
     sweeps in the oracle."""
-    gpu = _pa(L, R, seed=seed, resample=kind)
+    gpu = _pa(L, R, seed=seed, resample=kind, update=update)
     N = L * L
     rng = np.random.default_rng(seed)
     # init: sampled slots against the oracle's init
@@ -204,7 +204,8 @@ def _replay_steps(L, R, kind, seed, betas, theta, n_sample):
         assert abs(obs["lnQ"] - lnQ) <= 1e-12 * max(1.0, abs(lnQ))
         for j, w in pre.items():
             s = spins_from_canonical(L, w)[0]
-            s2 = oracle.sweep_replica(L, seed, i, j, beta, theta, s)
+            s2 = oracle.sweep_replica(L, seed, i, j, beta, theta, s,
+                                      update=oracle.HEATBATH if update == "heatbath" else oracle.METROPOLIS)
             post = gpu.export_spins(j, 1)[0].reshape(-1)
             assert np.array_equal(post, oracle.pack(L, s2)), f"slot {j} step {i}"
         # observables at full size from the exact integer sums
@@ -230,3 +231,7 @@ def test_full_size_L32_R1e5_replay(kind):
 
 def test_full_size_L64_R1e6_replay():
     _replay_steps(64, 1_000_000, "nearest", seed=7, betas=[1 / 300, 2 / 300], theta=10, n_sample=24)
+
+
+def test_full_size_L64_R1e6_heatbath_replay():
+    _replay_steps(64, 1_000_000, "nearest", seed=7, betas=[0.3, 0.7], theta=10, n_sample=24, update="heatbath")
