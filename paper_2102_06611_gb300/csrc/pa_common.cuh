@@ -11,10 +11,16 @@
 // Rows of a replica held by one lane in the sweep kernel (tuning knobs; lanes per replica =
 // L / rows, a power of two <= 32).
 #ifndef PA_RPL_16
-#define PA_RPL_16 8
+#define PA_RPL_16 16
+#endif
+#ifndef PA_RPL_24
+#define PA_RPL_24 12
 #endif
 #ifndef PA_RPL_32
 #define PA_RPL_32 8
+#endif
+#ifndef PA_RPL_48
+#define PA_RPL_48 6
 #endif
 #ifndef PA_RPL_64
 #define PA_RPL_64 4
@@ -44,8 +50,8 @@ namespace pa {
 // ------------------------------------------------------------------------------------
 __host__ __device__ constexpr int rows_per_lane(int L)
 {
-    return L == 4 ? 4 : L == 8 ? 8 : L == 12 ? 12 : L == 16 ? PA_RPL_16 : L == 24 ? 6 : L == 32 ? PA_RPL_32
-           : L == 48 ? 3 : L == 64 ? PA_RPL_64 : PA_RPL_128;
+    return L == 4 ? 4 : L == 8 ? 8 : L == 12 ? 12 : L == 16 ? PA_RPL_16 : L == 24 ? PA_RPL_24 : L == 32 ? PA_RPL_32
+           : L == 48 ? PA_RPL_48 : L == 64 ? PA_RPL_64 : PA_RPL_128;
 }
 
 __host__ __device__ constexpr int padded_half(int L)
