@@ -168,7 +168,6 @@ __global__ void k_mlp_round(const float *master, unsigned short *P)
 __global__ void __launch_bounds__(1024) k_features(FeatureArgs a)
 {
     __shared__ double red[32];
-    __shared__ double sh_mean;
     const int N = a.L * a.L, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     auto block_sum_d = [&](double v) -> double {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

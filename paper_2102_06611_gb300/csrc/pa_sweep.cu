@@ -59,8 +59,7 @@ __device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spar
         for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
     }
     const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), nullptr, tq_code};
-    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1,
-                         a.k0, a.k1, ac, tq);
+    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, ac, tq);
     int anti, ups;
     measure_rows<L>(A, B, r0, lane, anti, ups);
     anti = group_sum<G>(anti);
@@ -129,8 +128,7 @@ __device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void
         for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
     }
     const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), nullptr, tq_code};
-    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, a.k0, a.k1,
-                  ac, tq);
+    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, ac, tq);
     int anti, ups;
     measure_rows<L>(A, B, r0, lane, anti, ups);
     anti = group_sum<G>(anti);
