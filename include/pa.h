@@ -72,7 +72,10 @@ typedef enum {
     PA_UPDATE_HEATBATH = 1
 } pa_update_kind;
 
-/* Run configuration.  L must be one of 4, 8, 12, 16, 24, 32, 48, 64, 128.
+/* Run configuration.  L even, 4 <= L <= 128 (periodic L x L lattice).  The sizes 4, 8, 12,
+   16, 24, 32, 48, 64 and 128 run kernels that hold a replica in registers; every other even
+   L runs a kernel that stages it in shared memory (same random numbers and decisions,
+   slower).  Batches (pa_batch_create) take the nine register sizes only.
    1 <= R <= capacity <= 2^31 - 1.  beta_0 is always 0 (simple sampling, Sec. II). */
 typedef struct {
     int L;
@@ -358,8 +361,8 @@ pa_status pa_export_spins(pa_ctx *ctx, long long first, long long count, unsigne
    pa_resample would draw them for the same (seed, step i, beta_prev -> beta_new, R_target,
    kind); *lnQ_out gets ln Q_i and *R_new_out the new population size.  The scratch (histogram,
    level tables, block sums) is one fixed array of 493,056 bytes in the library image, present
-   on every GPU that loads the library until the process exits.  Limits: L one of the supported
-   sizes (so at most 16385 levels) and 1 <= R_prev <= 4,194,304; a larger R_prev returns
+   on every GPU that loads the library until the process exits.  Limits: L even, 4 <= L <= 128
+   (so at most 16385 levels) and 1 <= R_prev <= 4,194,304; a larger R_prev returns
    PA_ERR_TOO_LARGE.  Allocates nothing.  The first call on a device also looks up the array's
    device address (once per device); make that first call before any stream capture.  All calls
    share the array and each clears what it needs first; calls that overlap on the GPU (e.g. on

@@ -20,10 +20,11 @@ import torch
 from . import _lib
 from ._lib import PAError, pa_obs
 
-__all__ = ["PopulationAnnealing", "PAError", "pa_obs", "default_capacity", "SUPPORTED_L", "OBS_BYTES",
+__all__ = ["PopulationAnnealing", "PAError", "pa_obs", "default_capacity", "SUPPORTED_L", "REGISTER_L", "OBS_BYTES",
            "weighted_average"]
 
-SUPPORTED_L = (4, 8, 12, 16, 24, 32, 48, 64, 128)
+SUPPORTED_L = tuple(range(4, 129, 2))              # even 4 <= L <= 128
+REGISTER_L = (4, 8, 12, 16, 24, 32, 48, 64, 128)   # sizes with register-resident sweep kernels
 OBS_BYTES = ctypes.sizeof(pa_obs)
 
 

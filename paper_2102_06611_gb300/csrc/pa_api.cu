@@ -37,13 +37,7 @@ struct pa_ctx {
 
 namespace {
 
-bool supported_L(int L)
-{
-    switch (L) {
-        case 4: case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 128: return true;
-        default: return false;
-    }
-}
+bool supported_L(int L) { return L >= 4 && L <= 128 && (L % 2) == 0; }
 
 pa_status fail(pa_ctx *c, pa_status s, const char *fmt, ...)
 {

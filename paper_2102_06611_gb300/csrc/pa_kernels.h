@@ -69,6 +69,10 @@ struct SweepArgs {
 };
 
 cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s);
+// the sizes with a register-resident kernel template (pa_sweep.cuh); launch_sweep forwards
+// every other even 4 <= L <= 128 to the shared-memory kernel of pa_sweep_any.cu
+bool sweep_has_template(int L);
+cudaError_t launch_sweep_any(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s);
 // the heatbath sweep (pa_sweep_hb.cu); launch_sweep forwards to it for a.update = heatbath
 cudaError_t launch_sweep_hb(int L, const SweepArgs &a, int num_sms, cudaStream_t s);
 

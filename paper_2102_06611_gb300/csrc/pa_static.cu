@@ -79,13 +79,7 @@ __global__ void k_static_levels(const int *level, long long R, int N, int *hist,
     }
 }
 
-bool static_supported_L(int L)
-{
-    switch (L) {
-        case 4: case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 128: return true;
-        default: return false;
-    }
-}
+bool static_supported_L(int L) { return L >= 4 && L <= 128 && (L % 2) == 0; }
 
 }  // namespace
 }  // namespace pa

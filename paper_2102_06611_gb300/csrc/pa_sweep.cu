@@ -6,8 +6,17 @@
 
 namespace pa {
 
+bool sweep_has_template(int L)
+{
+    switch (L) {
+        case 4: case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 128: return true;
+        default: return false;
+    }
+}
+
 cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s)
 {
+    if (!sweep_has_template(L)) return launch_sweep_any(L, init, a, num_sms, s);
     if (!init && a.update == PA_UPDATE_HEATBATH) return launch_sweep_hb(L, a, num_sms, s);
 #define PA_SWEEP_CASE(LL)                                                                      \
     case LL:                                                                                   \

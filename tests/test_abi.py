@@ -53,7 +53,27 @@ def test_query_sizes_is_host_only():
     assert lib.pa_query_sizes(ctypes.byref(hb), ctypes.byref(sz)) == _lib.PA_OK
 
 
-@pytest.mark.parametrize("bad", [dict(L=10), dict(L=6), dict(L=256), dict(R=0), dict(capacity=5, R=10),
+@pytest.mark.parametrize("L,bpr", [(6, 48), (20, 160), (66, 1056), (126, 2016)])
+def test_query_sizes_any_even_L(L, bpr):
+    """Every even 4 <= L <= 128 is accepted; a replica is L rows of two half-row words
+    (32-bit for L <= 64, 64-bit above)."""
+    cfg = _lib.pa_config(L=L, resample=0, R=10, capacity=20, seed=1)
+    sz = _lib.pa_sizes()
+    assert _lib.lib().pa_query_sizes(ctypes.byref(cfg), ctypes.byref(sz)) == _lib.PA_OK
+    assert sz.bytes_per_replica == bpr
+
+
+def test_batches_take_register_sizes_only():
+    """Batches run the per-size register kernels: an even L without one is rejected."""
+    lib = _lib.lib()
+    n = ctypes.c_size_t()
+    for L, st in ((16, _lib.PA_OK), (20, _lib.PA_ERR_INVALID_ARG), (100, _lib.PA_ERR_INVALID_ARG)):
+        d = (_lib.pa_run_desc * 1)(_lib.pa_run_desc(_lib.pa_config(L=L, resample=0, R=100, capacity=200, seed=1),
+                                                    5, 1))
+        assert lib.pa_batch_query_sizes(1, d, ctypes.byref(n)) == st
+
+
+@pytest.mark.parametrize("bad", [dict(L=2), dict(L=7), dict(L=130), dict(L=256), dict(R=0), dict(capacity=5, R=10),
                                  dict(resample=3), dict(capacity=2 ** 31), dict(update=2), dict(pad=1)])
 def test_query_sizes_rejects_bad_configs(bad):
     args = dict(L=8, resample=0, R=10, capacity=20, seed=1)

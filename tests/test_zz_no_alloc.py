@@ -61,7 +61,7 @@ def test_static_entry_point_rejects_sizes_beyond_its_maximum():
                                     ctypes.c_void_p(dummy.data_ptr()), ctypes.byref(lnQ), ctypes.byref(R_new),
                                     None)
     assert st == _lib.PA_ERR_TOO_LARGE
-    st = lib.pa_copy_numbers_static(10, 1000, 10, ctypes.c_void_p(dummy.data_ptr()), 0.0, 0.1, 1, 1, 0,
+    st = lib.pa_copy_numbers_static(130, 1000, 10, ctypes.c_void_p(dummy.data_ptr()), 0.0, 0.1, 1, 1, 0,
                                     ctypes.c_void_p(dummy.data_ptr()), ctypes.byref(lnQ), ctypes.byref(R_new),
                                     None)
     assert st == _lib.PA_ERR_INVALID_ARG
