@@ -3,13 +3,13 @@
 // any even lattice size 4 <= L <= 128 that has no kernel template of its own (the sizes
 // 4, 8, 12, 16, 24, 32, 48, 64 and 128 run the register-resident kernels of pa_sweep.cuh).
 //
-// One warp owns one replica at a time and stages it in shared memory in its HBM layout
-// (per row the even-column half-row word, then the odd-column one, bit p = column 2p or
-// 2p + 1, here widened to 64 bits).  For one colour the lanes update rows lane, lane + 32,
-// ... : a row's colour-q sites are its half (r + q) & 1, whose vertical neighbours are the
-// same half of rows r -/+ 1 and whose horizontal neighbours are the other half of row r at
-// positions p and p -/+ 1, all of the other colour, so the lanes of one colour never
-// write what another lane reads.
+// A warp stages its replicas in shared memory in their HBM layout (per row the even-column
+// half-row word, then the odd-column one, bit p = column 2p or 2p + 1, widened to 64 bits).
+// A row's colour-q sites are its half (r + q) & 1, whose vertical neighbours are the same
+// half of rows r -/+ 1 and whose horizontal neighbours are the other half of row r at
+// positions p and p -/+ 1, all of the other colour, so the lanes updating one colour never
+// write what another lane reads.  For L <= 64 a lane updates one 32-site random-number chunk
+// at a time (the P rows of the chunk packed into one word); for L > 64 one row (two chunks).
 //
 // The random numbers and decisions are those of the register kernels, written for a
 // run-time size: the uniform x of site p of row r, colour q, sweep t has its top 8 bits from
@@ -30,7 +30,7 @@ namespace {
 
 using u64 = unsigned long long;
 
-constexpr int kAnyWarps = 8;  // warps per block, one replica each at a time
+constexpr int kAnyWarps = 8;  // warps per block
 
 // Class thresholds T_a, a = 0..4 aligned neighbours, split into top 8 and low 24 bits;
 // always has bit a set iff T_a = 2^32 (every site of class a flips).
@@ -68,92 +68,171 @@ __device__ ClassThr class_thresholds(int update, u64 T4, u64 T8)
     return c;
 }
 
-// bit p <- bit p - 1 and bit p <- bit p + 1, periodic in H bits (m = the H-bit mask)
-__device__ __forceinline__ u64 rot_from_below(u64 x, int H, u64 m) { return ((x << 1) | (x >> (H - 1))) & m; }
-__device__ __forceinline__ u64 rot_from_above(u64 x, int H, u64 m) { return ((x >> 1) | (x << (H - 1))) & m; }
+// Geometry of a run-time size.  Narrow sizes (H' <= 32, L <= 64): the P = 32 / H' rows of
+// one chunk are packed into one 32-bit word (field i = bits i H' .. i H' + H - 1 = row cP + i),
+// so a chunk's two Philox calls serve all its rows; nch chunks per colour, Gc lanes per
+// replica and k = 32 / Gc replicas per warp.  Wide sizes (L > 64): a row is two chunks, one
+// 64-bit word; a lane takes rows, one replica per warp.
+struct AnyGeo {
+    int L, H, HP, P, nch, Gc, k;
+    bool wide;
+    u64 hmask;
+};
 
-// The 8 bit planes of row r (bit p of plane k = bit 31 - k of site p's uniform).
-__device__ void row_planes(int r, int HP, u64 m, unsigned int slot, unsigned int tag, unsigned int step,
-                           unsigned int k0, unsigned int k1, u64 *pl)
+__host__ __device__ AnyGeo any_geo(int L)
 {
-    const unsigned int c2 = (kStreamSweep << 28) | tag;
-    if (HP <= 32) {
-        // the row's sites are bits off .. off + H - 1 of chunk n / 32, n = r H'
-        const unsigned int n = (unsigned int)(r * HP);
-        const unsigned int chunk = n >> 5, off = n & 31u;
-        const uint4 a = philox(make_uint4(2 * chunk, slot, c2, step), k0, k1);
-        const uint4 b = philox(make_uint4(2 * chunk + 1, slot, c2, step), k0, k1);
-        const unsigned int w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        for (int k = 0; k < 8; ++k) pl[k] = (u64)(w[k] >> off) & m;
+    AnyGeo g;
+    g.L = L;
+    g.H = L / 2;
+    g.HP = 1;
+    while (g.HP < g.H) g.HP *= 2;
+    g.wide = g.HP > 32;
+    g.hmask = (g.H == 64) ? ~0ull : ((1ull << g.H) - 1ull);
+    if (g.wide) {
+        g.P = 1;
+        g.nch = L;
+        g.Gc = 32;
     } else {
-        // H' = 64: sites 0..31 are chunk 2r, sites 32..63 chunk 2r + 1
-        const unsigned int c0 = (unsigned int)(4 * r);
-        const uint4 a0 = philox(make_uint4(c0, slot, c2, step), k0, k1);
-        const uint4 a1 = philox(make_uint4(c0 + 1, slot, c2, step), k0, k1);
-        const uint4 b0 = philox(make_uint4(c0 + 2, slot, c2, step), k0, k1);
-        const uint4 b1 = philox(make_uint4(c0 + 3, slot, c2, step), k0, k1);
-        const unsigned int lo[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const unsigned int hi[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-        for (int k = 0; k < 8; ++k) pl[k] = ((u64)lo[k] | ((u64)hi[k] << 32)) & m;
+        g.P = 32 / g.HP;
+        g.nch = (L + g.P - 1) / g.P;
+        int n = 1;
+        while (n < g.nch && n < 32) n *= 2;
+        g.Gc = n;
+    }
+    g.k = 32 / g.Gc;
+    return g;
+}
+
+// Classes and the top-8-bit decision of one word: returns the decided flips; eq = the
+// sites whose top bits tie with their class threshold, cls = the class masks (a aligned
+// neighbours, a = 0..4).  Sites outside V stay clear.
+template <typename W>
+__device__ __forceinline__ W decide(W s, W up, W dn, W o, W side, W V, const W *pl, const ClassThr &th, W &eq,
+                                    W *cls)
+{
+    // aligned-neighbour count a = x1 + x2 + x3 + x4 in three bit slices
+    const W x1 = ~(s ^ up) & V, x2 = ~(s ^ dn) & V, x3 = ~(s ^ o) & V, x4 = ~(s ^ side) & V;
+    const W s12 = x1 ^ x2, c12 = x1 & x2, s34 = x3 ^ x4, c34 = x3 & x4;
+    const W b0 = s12 ^ s34, cr = s12 & s34;
+    const W b1 = c12 ^ c34 ^ cr;
+    const W b2 = (c12 & c34) | ((c12 ^ c34) & cr);
+    cls[0] = ~b2 & ~b1 & ~b0 & V;
+    cls[1] = ~b2 & ~b1 & b0 & V;
+    cls[2] = ~b2 & b1 & ~b0 & V;
+    cls[3] = ~b2 & b1 & b0 & V;
+    cls[4] = b2 & V;
+    W alw = 0;
+    for (int a = 0; a < 5; ++a)
+        if ((th.always >> a) & 1u) alw |= cls[a];
+    // borrow chain from the least significant plane: lt = x_top < T_top, e = x_top == T_top
+    W lt = 0, e = V & ~alw;
+    for (int k = 7; k >= 0; --k) {
+        W tm = 0;  // bit 7 - k of each site's class threshold
+        for (int a = 0; a < 5; ++a)
+            if ((th.top[a] >> (7 - k)) & 1u) tm |= cls[a];
+        const W np = ~pl[k];
+        lt = (np & tm) | (np & lt) | (tm & lt);
+        e &= ~(pl[k] ^ tm);
+    }
+    eq = e;
+    return alw | (lt & ~alw);
+}
+
+// The low 24 bits decide a tie: site p of row r, class a.
+__device__ __forceinline__ bool tie_accept(int r, int p, int a, unsigned int slot, unsigned int tag, unsigned int step,
+                                           unsigned int k0, unsigned int k1, const ClassThr &th)
+{
+    const uint4 x = philox(make_uint4((unsigned int)(64 * r + p), slot, (kStreamRefine << 28) | tag, step), k0, k1);
+    return (x.x & 0xFFFFFFu) < th.low[a];
+}
+
+template <typename W>
+__device__ __forceinline__ int class_of(const W *cls, W bit)
+{
+    int a = 0;
+    for (int c = 1; c < 5; ++c)
+        if (cls[c] & bit) a = c;
+    return a;
+}
+
+// One colour q of one sweep, narrow sizes: the lane updates chunks c0, c0 + Gc, ... of the
+// replica S (S[2r] = even-column half of row r, S[2r + 1] = odd-column half).
+__device__ void half_sweep_chunks(u64 *S, const AnyGeo &g, int q, unsigned int slot, unsigned int tag,
+                                  unsigned int step, unsigned int k0, unsigned int k1, const ClassThr &th, int c0)
+{
+    const int L = g.L, H = g.H, HP = g.HP, P = g.P;
+    const unsigned int hm = (unsigned int)g.hmask;
+    const unsigned int c2 = (kStreamSweep << 28) | tag;
+    for (int c = c0; c < g.nch; c += g.Gc) {
+        // pack the chunk's rows: T = colour-q sites, O = the other half of the same rows,
+        // U / D = the same half of the rows above / below, Sd = O shifted to the second
+        // horizontal neighbour (even-column sites see p - 1, odd-column sites p + 1)
+        unsigned int T = 0, O = 0, U = 0, D = 0, Sd = 0, V = 0;
+        for (int i = 0; i < P; ++i) {
+            const int r = c * P + i;
+            if (r >= L) break;
+            const int h = (r + q) & 1;
+            const int ru = (r == 0) ? L - 1 : r - 1, rd = (r == L - 1) ? 0 : r + 1;
+            const unsigned int o = (unsigned int)S[2 * r + (h ^ 1)];
+            const int sh = i * HP;
+            T |= (unsigned int)S[2 * r + h] << sh;
+            O |= o << sh;
+            U |= (unsigned int)S[2 * ru + h] << sh;
+            D |= (unsigned int)S[2 * rd + h] << sh;
+            const unsigned int side = h == 0 ? ((o << 1) | (o >> (H - 1))) & hm : ((o >> 1) | (o << (H - 1))) & hm;
+            Sd |= side << sh;
+            V |= hm << sh;
+        }
+        // the chunk's 8 bit planes: bit n mod 32 = bit i H' + p
+        const uint4 a0 = philox(make_uint4(2 * (unsigned int)c, slot, c2, step), k0, k1);
+        const uint4 a1 = philox(make_uint4(2 * (unsigned int)c + 1, slot, c2, step), k0, k1);
+        const unsigned int pl[8] = {a0.x & V, a0.y & V, a0.z & V, a0.w & V, a1.x & V, a1.y & V, a1.z & V, a1.w & V};
+        unsigned int eq, cls[5];
+        unsigned int flip = decide<unsigned int>(T, U, D, O, Sd, V, pl, th, eq, cls);
+        while (eq) {
+            const int b = __ffs((int)eq) - 1;
+            const unsigned int bit = 1u << b;
+            if (tie_accept(c * P + b / HP, b % HP, class_of(cls, bit), slot, tag, step, k0, k1, th)) flip |= bit;
+            eq &= eq - 1u;
+        }
+        const unsigned int Tn = T ^ flip;
+        for (int i = 0; i < P; ++i) {
+            const int r = c * P + i;
+            if (r >= L) break;
+            S[2 * r + ((r + q) & 1)] = (Tn >> (i * HP)) & hm;
+        }
     }
 }
 
-// One colour q of one sweep over the rows lane, lane + 32, ... of the warp's replica S
-// (S[2r] = even-column half of row r, S[2r + 1] = odd-column half).
-__device__ void half_sweep_any(u64 *S, int L, int q, unsigned int slot, unsigned int tag, unsigned int step,
-                               unsigned int k0, unsigned int k1, const ClassThr &th, int lane)
+// One colour q of one sweep, wide sizes: the lane updates rows c0, c0 + 32, ... (one row =
+// chunks 2r and 2r + 1, four Philox calls for its planes).
+__device__ void half_sweep_rows(u64 *S, const AnyGeo &g, int q, unsigned int slot, unsigned int tag,
+                                unsigned int step, unsigned int k0, unsigned int k1, const ClassThr &th, int c0)
 {
-    const int H = L / 2;
-    int HP = 1;
-    while (HP < H) HP *= 2;
-    const u64 m = (H == 64) ? ~0ull : ((1ull << H) - 1ull);
-    for (int r = lane; r < L; r += 32) {
+    const int L = g.L, H = g.H;
+    const u64 m = g.hmask;
+    const unsigned int c2 = (kStreamSweep << 28) | tag;
+    for (int r = c0; r < L; r += g.Gc) {
         const int h = (r + q) & 1;  // the half holding colour q in row r
         const int ru = (r == 0) ? L - 1 : r - 1, rd = (r == L - 1) ? 0 : r + 1;
         const u64 s = S[2 * r + h];
         const u64 o = S[2 * r + (h ^ 1)];
-        const u64 up = S[2 * ru + h], dn = S[2 * rd + h];
-        // even-column sites (h = 0) see odd columns p - 1 and p; odd-column sites see p and p + 1
-        const u64 side = h == 0 ? rot_from_below(o, H, m) : rot_from_above(o, H, m);
-        // aligned-neighbour count a = x1 + x2 + x3 + x4 in three bit slices
-        const u64 x1 = ~(s ^ up) & m, x2 = ~(s ^ dn) & m, x3 = ~(s ^ o) & m, x4 = ~(s ^ side) & m;
-        const u64 s12 = x1 ^ x2, c12 = x1 & x2, s34 = x3 ^ x4, c34 = x3 & x4;
-        const u64 b0 = s12 ^ s34, cr = s12 & s34;
-        const u64 b1 = c12 ^ c34 ^ cr;
-        const u64 b2 = (c12 & c34) | ((c12 ^ c34) & cr);
-        u64 cls[5];
-        cls[0] = ~b2 & ~b1 & ~b0 & m;
-        cls[1] = ~b2 & ~b1 & b0 & m;
-        cls[2] = ~b2 & b1 & ~b0 & m;
-        cls[3] = ~b2 & b1 & b0 & m;
-        cls[4] = b2 & m;
-        u64 alw = 0;
-        for (int a = 0; a < 5; ++a)
-            if ((th.always >> a) & 1u) alw |= cls[a];
-
+        const u64 side = h == 0 ? ((o << 1) | (o >> (H - 1))) & m : ((o >> 1) | (o << (H - 1))) & m;
+        const unsigned int ch = (unsigned int)(4 * r);
+        const uint4 a0 = philox(make_uint4(ch, slot, c2, step), k0, k1);
+        const uint4 a1 = philox(make_uint4(ch + 1, slot, c2, step), k0, k1);
+        const uint4 b0 = philox(make_uint4(ch + 2, slot, c2, step), k0, k1);
+        const uint4 b1 = philox(make_uint4(ch + 3, slot, c2, step), k0, k1);
+        const unsigned int lo[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const unsigned int hi[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
         u64 pl[8];
-        row_planes(r, HP, m, slot, tag, step, k0, k1, pl);
-        // borrow chain from the least significant plane: lt = x_top < T_top, eq = x_top == T_top
-        u64 lt = 0, eq = m & ~alw;
-        for (int k = 7; k >= 0; --k) {
-            u64 tm = 0;  // bit 7 - k of each site's class threshold
-            for (int a = 0; a < 5; ++a)
-                if ((th.top[a] >> (7 - k)) & 1u) tm |= cls[a];
-            const u64 np = ~pl[k];
-            lt = (np & tm) | (np & lt) | (tm & lt);
-            eq &= ~(pl[k] ^ tm);
-        }
-        u64 flip = alw | (lt & ~alw);
-        // ties: the low 24 bits decide
+        for (int k = 0; k < 8; ++k) pl[k] = ((u64)lo[k] | ((u64)hi[k] << 32)) & m;
+        u64 eq, cls[5];
+        u64 flip = decide<u64>(s, S[2 * ru + h], S[2 * rd + h], o, side, m, pl, th, eq, cls);
         while (eq) {
             const int p = __ffsll((long long)eq) - 1;
             const u64 bit = 1ull << p;
-            int a = 0;
-            for (int c = 1; c < 5; ++c)
-                if (cls[c] & bit) a = c;
-            const uint4 x = philox(make_uint4((unsigned int)(64 * r + p), slot, (kStreamRefine << 28) | tag, step),
-                                   k0, k1);
-            if ((x.x & 0xFFFFFFu) < th.low[a]) flip |= bit;
+            if (tie_accept(r, p, class_of(cls, bit), slot, tag, step, k0, k1, th)) flip |= bit;
             eq &= eq - 1ull;
         }
         S[2 * r + h] = s ^ flip;
@@ -161,10 +240,12 @@ __device__ void half_sweep_any(u64 *S, int L, int q, unsigned int slot, unsigned
 }
 
 // Simple sampling (step 1): site n = r L + c takes bit n mod 32 of word n / 32 of the INIT
-// stream, word w being lane w mod 4 of Philox(ctr = (w / 4, slot, INIT << 28, 0)).
-__device__ void init_any(u64 *S, int L, unsigned int slot, unsigned int k0, unsigned int k1, int lane)
+// stream, word w being lane w mod 4 of Philox(ctr = (w / 4, slot, INIT << 28, 0)).  The lane
+// fills rows c0, c0 + Gc, ...
+__device__ void init_any(u64 *S, const AnyGeo &g, unsigned int slot, unsigned int k0, unsigned int k1, int c0)
 {
-    for (int r = lane; r < L; r += 32) {
+    const int L = g.L;
+    for (int r = c0; r < L; r += g.Gc) {
         u64 E = 0, O = 0;
         unsigned int cached = 0xffffffffu;
         uint4 x = make_uint4(0, 0, 0, 0);
@@ -187,64 +268,74 @@ __device__ void init_any(u64 *S, int L, unsigned int slot, unsigned int k0, unsi
 template <bool INIT>
 __global__ void __launch_bounds__(32 * kAnyWarps) k_sweep_any(SweepArgs a, int L)
 {
+    const AnyGeo g = any_geo(L);
     extern __shared__ u64 sh_dyn[];
-    const int N = L * L, H = L / 2;
-    u64 *S = sh_dyn + (threadIdx.x >> 5) * (2 * L);  // this warp's replica
-    int *sh_hist = reinterpret_cast<int *>(sh_dyn + kAnyWarps * 2 * L);
+    const int N = L * L, W2 = 2 * L;  // words per replica
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / g.Gc, c0 = lane % g.Gc;  // replica within the warp, lane within its group
+    u64 *Sw = sh_dyn + (size_t)(threadIdx.x >> 5) * g.k * W2;  // the warp's k replicas
+    u64 *S = Sw + sub * W2;
+    int *sh_hist = reinterpret_cast<int *>(sh_dyn + (size_t)kAnyWarps * g.k * W2);
     __shared__ unsigned long long sh_sum[7];
     for (int k = threadIdx.x; k <= N; k += blockDim.x) sh_hist[k] = 0;
     if (threadIdx.x < 7) sh_sum[threadIdx.x] = 0;
     __syncthreads();
 
-    const int lane = threadIdx.x & 31;
     const long long R = INIT ? a.R_init : a.st->R_cur;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const ClassThr th = class_thresholds(a.update, a.T4, a.T8);
     if (!INIT && blockIdx.x == 0 && threadIdx.x == 0 && (a.T4 != a.st->T4 || a.T8 != a.st->T8))
         set_error(a.st, PA_ERR_NUMERIC);  // host and device thresholds disagree (never expected)
-    const bool wide = H > 32;
-    const u64 m = (H == 64) ? ~0ull : ((1ull << H) - 1ull);
+    const int KW = g.k * W2;  // words of the warp's replicas
 
-    for (long long j = warp; j < R; j += nwarps) {
+    for (long long base = warp * g.k; base < R; base += nwarps * g.k) {
+        const long long j = base + sub;
+        const bool active = j < R;
+        // the warp's k replicas are consecutive in HBM; slots past R read as zero
         if (INIT) {
-            init_any(S, L, (unsigned int)j, a.k0, a.k1, lane);
-        } else if (wide) {
-            const u64 *src = reinterpret_cast<const u64 *>(a.spins) + (size_t)j * (2 * L);
-            for (int w = lane; w < 2 * L; w += 32) S[w] = src[w];
+            init_any(S, g, (unsigned int)j, a.k0, a.k1, c0);
+        } else if (g.wide) {
+            const u64 *src = reinterpret_cast<const u64 *>(a.spins) + (size_t)base * W2;
+            for (int w = lane; w < KW; w += 32) Sw[w] = (base + w / W2 < R) ? src[w] : 0ull;
         } else {
-            const unsigned int *src = reinterpret_cast<const unsigned int *>(a.spins) + (size_t)j * (2 * L);
-            for (int w = lane; w < 2 * L; w += 32) S[w] = src[w];
+            const unsigned int *src = reinterpret_cast<const unsigned int *>(a.spins) + (size_t)base * W2;
+            for (int w = lane; w < KW; w += 32) Sw[w] = (base + w / W2 < R) ? src[w] : 0u;
         }
         __syncwarp();
         for (int t = 0; t < a.theta; ++t)
             for (int q = 0; q < 2; ++q) {
-                half_sweep_any(S, L, q, (unsigned int)j, (unsigned int)(2 * (a.t0 + t) + q), a.step, a.k0, a.k1, th,
-                               lane);
+                const unsigned int tag = (unsigned int)(2 * (a.t0 + t) + q);
+                if (g.wide) half_sweep_rows(S, g, q, (unsigned int)j, tag, a.step, a.k0, a.k1, th, c0);
+                else half_sweep_chunks(S, g, q, (unsigned int)j, tag, a.step, a.k0, a.k1, th, c0);
                 __syncwarp();
             }
         // measurement: antiparallel bonds (row r: (2p, 2p+1), (2p+1, 2p+2); column: r, r+1)
         int anti = 0, ups = 0;
-        for (int r = lane; r < L; r += 32) {
+        for (int r = c0; r < L; r += g.Gc) {
             const int rn = (r == L - 1) ? 0 : r + 1;
             const u64 E = S[2 * r], O = S[2 * r + 1];
-            anti += __popcll(E ^ O) + __popcll(O ^ rot_from_above(E, H, m)) + __popcll(E ^ S[2 * rn]) +
-                    __popcll(O ^ S[2 * rn + 1]);
+            const u64 En = ((E >> 1) | (E << (g.H - 1))) & g.hmask;
+            anti += __popcll(E ^ O) + __popcll(O ^ En) + __popcll(E ^ S[2 * rn]) + __popcll(O ^ S[2 * rn + 1]);
             ups += __popcll(E) + __popcll(O);
         }
-        anti = group_sum<32>(anti);
-        ups = group_sum<32>(ups);
+        for (int o = g.Gc / 2; o > 0; o >>= 1) {  // sum over the replica's lane group
+            anti += __shfl_xor_sync(0xffffffffu, anti, o);
+            ups += __shfl_xor_sync(0xffffffffu, ups, o);
+        }
         if (INIT || a.theta > 0) {
-            if (wide) {
-                u64 *dst = reinterpret_cast<u64 *>(a.spins) + (size_t)j * (2 * L);
-                for (int w = lane; w < 2 * L; w += 32) dst[w] = S[w];
+            if (g.wide) {
+                u64 *dst = reinterpret_cast<u64 *>(a.spins) + (size_t)base * W2;
+                for (int w = lane; w < KW; w += 32)
+                    if (base + w / W2 < R) dst[w] = Sw[w];
             } else {
-                unsigned int *dst = reinterpret_cast<unsigned int *>(a.spins) + (size_t)j * (2 * L);
-                for (int w = lane; w < 2 * L; w += 32) dst[w] = (unsigned int)S[w];
+                unsigned int *dst = reinterpret_cast<unsigned int *>(a.spins) + (size_t)base * W2;
+                for (int w = lane; w < KW; w += 32)
+                    if (base + w / W2 < R) dst[w] = (unsigned int)Sw[w];
             }
         }
-        __syncwarp();  // the stores have read S before the next replica overwrites it
-        if (lane == 0) {
+        __syncwarp();  // the stores have read S before the next replicas overwrite it
+        if (c0 == 0 && active) {
             const int level = anti >> 1;
             const int M = 2 * ups - N;
             unsigned long long v[7] = {(unsigned long long)(M < 0 ? -M : M), (unsigned long long)((long long)M * M),
@@ -286,17 +377,21 @@ __global__ void __launch_bounds__(32 * kAnyWarps) k_sweep_any(SweepArgs a, int L
 }
 
 // shared memory of a block: the replicas of its warps, then the level histogram
-size_t any_smem_bytes(int L) { return (size_t)kAnyWarps * 2 * L * sizeof(u64) + (size_t)(L * L + 1) * sizeof(int); }
+size_t any_smem_bytes(int L)
+{
+    return (size_t)kAnyWarps * any_geo(L).k * 2 * L * sizeof(u64) + (size_t)(L * L + 1) * sizeof(int);
+}
 
 template <bool INIT>
 cudaError_t launch_any_t(int L, const SweepArgs &a, int num_sms, cudaStream_t s)
 {
     const size_t smem = any_smem_bytes(L);
-    static bool attr_set = false;  // the limit is set once, for the largest L
+    static bool attr_set = false;  // the limit is set once, for the largest need
     cudaError_t e = cudaSuccess;
     if (!attr_set) {
-        e = cudaFuncSetAttribute(k_sweep_any<INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)any_smem_bytes(128));
+        size_t most = 0;
+        for (int l = 4; l <= 128; l += 2) most = any_smem_bytes(l) > most ? any_smem_bytes(l) : most;
+        e = cudaFuncSetAttribute(k_sweep_any<INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -304,7 +399,8 @@ cudaError_t launch_any_t(int L, const SweepArgs &a, int num_sms, cudaStream_t s)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_any<INIT>, 32 * kAnyWarps, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    long long blocks = (a.R_bound + kAnyWarps - 1) / kAnyWarps;
+    const long long per_block = (long long)kAnyWarps * any_geo(L).k;  // replicas per block and pass
+    long long blocks = (a.R_bound + per_block - 1) / per_block;
     const long long cap = (long long)num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
