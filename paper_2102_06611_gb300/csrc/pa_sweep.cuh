@@ -27,6 +27,9 @@
 #define PA_SWEEP_MIN_BLOCKS 2
 #endif
 constexpr int sweep_min_blocks(int L) { return (L == 8 || L == 128) ? 1 : PA_SWEEP_MIN_BLOCKS; }
+#ifndef PA_TM_IMAD
+#define PA_TM_IMAD 1   // threshold bits by multiply-add (see Accept)
+#endif
 #ifndef PA_PREFETCH_MAX_C
 #define PA_PREFETCH_MAX_C 3
 #endif
@@ -231,12 +234,35 @@ struct SweepStyle {
 // is set (k = 0 most significant).  T = 2^32 (beta = 0) is either the always-accept mask alw
 // (XNOR style, top = low = 0) or top = 255, low = 2^24 (x < 2^32 holds, and so does the
 // split test: x_top < 255, or x_top = 255 and x_low < 2^24).
+//
+// The threshold bit of a site, tm = m8[k] where all4 is set, else m4[k], is also
+// all4 * sel[k] + m4[k] (mod 2^32) with sel[k] = 0 where m4[k] = m8[k], +1 where only m8[k]
+// is set and -1 where only m4[k] is (then tm = -all4 - 1 = ~all4): one integer multiply-add,
+// which issues on the FMA pipe and leaves the logic pipe (the busiest unit of the sweep) to
+// the borrow chain (64-bit words: one per 32-bit half).
 template <typename W>
 struct Accept {
     W m4[8], m8[8];
     W alw4, alw8;
     unsigned int low4, low8;
+    unsigned int sel[8];
 };
+
+template <typename W>
+__device__ __forceinline__ W threshold_bits(W cls, const Accept<W> &ac, int k)
+{
+#if PA_TM_IMAD
+    if constexpr (sizeof(W) == 4) {
+        return cls * ac.sel[k] + ac.m4[k];
+    } else {  // two 32-bit halves
+        const unsigned int m = (unsigned int)ac.m4[k];
+        const unsigned int lo = (unsigned int)cls * ac.sel[k] + m, hi = (unsigned int)(cls >> 32) * ac.sel[k] + m;
+        return ((W)hi << 32) | (W)lo;
+    }
+#else
+    return (cls & ac.m8[k]) | (~cls & ac.m4[k]);
+#endif
+}
 
 template <int L>
 __device__ __forceinline__ Accept<typename Geo<L>::W> make_accept(unsigned long long T4, unsigned long long T8)
@@ -263,8 +289,10 @@ __device__ __forceinline__ Accept<typename Geo<L>::W> make_accept(unsigned long 
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        c.m4[k] = ((top4 >> (7 - k)) & 1u) ? ~W(0) : W(0);
-        c.m8[k] = ((top8 >> (7 - k)) & 1u) ? ~W(0) : W(0);
+        const unsigned int b4 = (top4 >> (7 - k)) & 1u, b8 = (top8 >> (7 - k)) & 1u;
+        c.m4[k] = b4 ? ~W(0) : W(0);
+        c.m8[k] = b8 ? ~W(0) : W(0);
+        c.sel[k] = (b4 == b8) ? 0u : (b8 ? 1u : 0xFFFFFFFFu);
     }
     return c;
 }
@@ -302,7 +330,7 @@ __device__ __forceinline__ void compare_planes(const W *plane, W all4, W eq3, W 
     W l = 0, e = XNOR ? (ge3 & ~dec) : ge3;
 #pragma unroll
     for (int k = 7; k >= 0; --k) {
-        const W tm = (all4 & ac.m8[k]) | (~all4 & ac.m4[k]);  // threshold bit of each site
+        const W tm = threshold_bits(all4, ac, k);  // threshold bit of each site
         const W np = ~plane[k];
         l = (np & tm) | (np & l) | (tm & l);
         e &= ~(plane[k] ^ tm);
@@ -340,7 +368,7 @@ __device__ __forceinline__ void compare_planes_hb(const W *plane, W c04, W clow,
     W l = 0, e = ~c2 & valid;
 #pragma unroll
     for (int k = 7; k >= 0; --k) {
-        const W tm = (c04 & ac.m8[k]) | (~c04 & ac.m4[k]);
+        const W tm = threshold_bits(c04, ac, k);
         const W pp = plane[k] ^ clow;
         const W np = ~pp;
         l = (np & tm) | (np & l) | (tm & l);

@@ -17,7 +17,7 @@ def _pa(*a, **k):
     return PopulationAnnealing(*a, **k)
 
 
-@pytest.mark.parametrize("L,R,target", [(8, 1500, 0.8), (16, 2000, 0.8), (32, 800, 0.5)])
+@pytest.mark.parametrize("L,R,target", [(8, 1500, 0.8), (16, 2000, 0.8), (32, 800, 0.5), (20, 600, 0.8)])
 def test_adaptive_anneal_parity(L, R, target):
     from paper_2102_06611_gb300 import _lib
     seed, theta, dmax, bf = 21, 3, 0.1, 1.0
