@@ -23,10 +23,17 @@
 // Minimum resident blocks of 256 threads per SM the sweep kernel is compiled for (caps its
 // registers at 65536 / (256 * n)): 2, except L = 8 and 128, where one block of up to 255
 // registers per thread is faster (measured: +2.5 % and +8 %).
+#ifndef PA_SWEEP_THREADS
+#define PA_SWEEP_THREADS 256
+#endif
 #ifndef PA_SWEEP_MIN_BLOCKS
 #define PA_SWEEP_MIN_BLOCKS 2
 #endif
-constexpr int sweep_min_blocks(int L) { return (L == 8 || L == 128) ? 1 : PA_SWEEP_MIN_BLOCKS; }
+constexpr int kSweepWarps = PA_SWEEP_THREADS / 32;  // warps per block of the sweep kernel
+constexpr int sweep_min_blocks(int L)
+{
+    return (L == 8 || L == 128) ? (256 / PA_SWEEP_THREADS > 0 ? 256 / PA_SWEEP_THREADS : 1) : PA_SWEEP_MIN_BLOCKS;
+}
 #ifndef PA_TM_IMAD
 #define PA_TM_IMAD 1   // threshold bits by multiply-add (see Accept)
 #endif
@@ -823,7 +830,7 @@ __device__ __forceinline__ void measure_rows(const typename Geo<L>::W *A, const 
 // Metropolis (!HB) or heatbath (HB) update, measure.
 // ------------------------------------------------------------------------------------
 template <int L, bool INIT, bool HB>
-__global__ void __launch_bounds__(256, sweep_min_blocks(L)) k_sweep(SweepArgs a)
+__global__ void __launch_bounds__(PA_SWEEP_THREADS, sweep_min_blocks(L)) k_sweep(SweepArgs a)
 {
     using Gm = Geo<L>;
     using W = typename Gm::W;
@@ -857,9 +864,9 @@ __global__ void __launch_bounds__(256, sweep_min_blocks(L)) k_sweep(SweepArgs a)
     if (threadIdx.x < 7) sh_sum[threadIdx.x] = 0;
     __syncthreads();
     W *spins = reinterpret_cast<W *>(a.spins);
-    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp; 8 warps per block
-    __shared__ W tq_eq[8 * TQ], tq_a4[8 * TQ], tq_inv[HB ? 8 * TQ : 1];
-    __shared__ unsigned int tq_code[8 * TQ];
+    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp
+    __shared__ W tq_eq[kSweepWarps * TQ], tq_a4[kSweepWarps * TQ], tq_inv[HB ? kSweepWarps * TQ : 1];
+    __shared__ unsigned int tq_code[kSweepWarps * TQ];
     const int wib = threadIdx.x >> 5;
     const TieQueue<W> tq{tq_eq + wib * TQ, tq_a4 + wib * TQ, HB ? tq_inv + wib * TQ : nullptr,
                          tq_code + wib * TQ};
@@ -960,17 +967,17 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int num_sms, cudaStream_t s)
                                              (int)smem);
         if (e != cudaSuccess) return e;
         int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep<L, INIT, HB>, 256, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep<L, INIT, HB>, PA_SWEEP_THREADS, smem);
         if (e != cudaSuccess) return e;
         blocks_per_sm = b > 0 ? b : 1;
     }
     const long long R = a.R_bound;
     const long long groups = (R + Geo<L>::RPW - 1) / Geo<L>::RPW;  // warps needed
-    long long blocks = (groups + 7) / 8;
+    long long blocks = (groups + kSweepWarps - 1) / kSweepWarps;
     const long long cap = (long long)num_sms * blocks_per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_sweep<L, INIT, HB><<<(unsigned int)blocks, 256, smem, s>>>(a);
+    k_sweep<L, INIT, HB><<<(unsigned int)blocks, PA_SWEEP_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
