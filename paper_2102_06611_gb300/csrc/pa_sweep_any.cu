@@ -17,11 +17,12 @@
 // SWEEP << 28 | 2t + q, i)), n = r H' + p, chunk = n / 32, H' = the smallest power of two
 // >= L / 2) and its low 24 bits from Philox(ctr = (64 r + p, slot, REFINE << 28 | 2t + q, i))
 // word 0, drawn only when the top bits tie with the threshold.  A site with a aligned
-// neighbours flips iff x < T_a: Metropolis (Sec. IV) T_0 = T_1 = T_2 = 2^32, T_3 =
-// floor(e^{-4 beta} 2^32), T_4 = floor(e^{-8 beta} 2^32); heatbath T_a ~ 2^32 / (1 + e^{beta dE})
-// with dE = 4a - 8, i.e. T_3, T_4 = floor(2^32 / (1 + e^{4 beta})), floor(2^32 / (1 +
-// e^{8 beta})) from the host and T_1 = 2^32 - T_3, T_0 = 2^32 - T_4, T_2 = 2^31.  x < T_a is decided over a whole half-row at once by a borrow chain
-// over the planes against each site's class threshold bits.
+// neighbours flips iff x < T_a.  Metropolis (Sec. IV): T_0 = T_1 = T_2 = 2^32,
+// T_3 = floor(e^{-4 beta} 2^32), T_4 = floor(e^{-8 beta} 2^32).  Heatbath: T_a ~ 2^32 /
+// (1 + e^{beta dE}) with dE = 4a - 8, i.e. T_3 = floor(2^32 / (1 + e^{4 beta})) and
+// T_4 = floor(2^32 / (1 + e^{8 beta})) from the host, T_1 = 2^32 - T_3, T_0 = 2^32 - T_4,
+// T_2 = 2^31.  x < T_a is decided over a whole word at once by a borrow chain over the
+// planes against each site's class threshold bits.
 #include "pa_common.cuh"
 #include "pa_kernels.h"
 
