@@ -471,15 +471,35 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
         off += c[it];
     }
     __syncthreads();
-    // a group of S lanes (the smallest power of two >= the replica's 16-byte chunks, at most
-    // 32) copies one parent, so a warp serves 32 / S parents at a time
-    int S = 1;
-    while (S < chunks16 && S < 32) S <<= 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int sub = lane / S, li = lane % S, per_warp = 32 / S;
     const uint4 *src = reinterpret_cast<const uint4 *>(a.spins_src);
     uint4 *dst = reinterpret_cast<uint4 *>(a.spins_dst);
     const int nloc = (int)min((long long)kCountBlockItems, Rp - base);
+    if (chunks16 >= 32) {
+        // a warp per parent
+        for (int p = wid; p < nloc; p += kCountThreads / 32) {
+            const int cnt = sh_cnt[p];
+            if (cnt == 0) continue;
+            const long long j = base + p;
+            const long long o = sh_off[p];
+            for (int ch = lane; ch < chunks16; ch += 32) {
+                const uint4 v = src[(size_t)j * chunks16 + ch];
+                for (int k = 0; k < cnt; ++k) dst[(size_t)(o + k) * chunks16 + ch] = v;
+            }
+            const int lv = a.level_src[j], mg = a.mag_src[j], fm = a.fam_src[j];
+            for (int k = lane; k < cnt; k += 32) {
+                a.level_dst[o + k] = lv;
+                a.mag_dst[o + k] = mg;
+                a.fam_dst[o + k] = fm;
+            }
+        }
+        return;
+    }
+    // small replicas: a group of 2^gs lanes (the smallest power of two >= the replica's
+    // 16-byte vectors) per parent, 32 / 2^gs parents per warp at a time
+    int gs = 0;
+    while ((1 << gs) < chunks16) ++gs;
+    const int S = 1 << gs, sub = lane >> gs, li = lane & (S - 1), per_warp = 32 >> gs;
     for (int p0 = wid * per_warp; p0 < nloc; p0 += (kCountThreads / 32) * per_warp) {
         const int p = p0 + sub;
         if (p >= nloc) continue;
@@ -487,9 +507,9 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
         if (cnt == 0) continue;
         const long long j = base + p;
         const long long o = sh_off[p];
-        for (int ch = li; ch < chunks16; ch += S) {
-            const uint4 v = src[(size_t)j * chunks16 + ch];
-            for (int k = 0; k < cnt; ++k) dst[(size_t)(o + k) * chunks16 + ch] = v;
+        if (li < chunks16) {
+            const uint4 v = src[(size_t)j * chunks16 + li];
+            for (int k = 0; k < cnt; ++k) dst[(size_t)(o + k) * chunks16 + li] = v;
         }
         const int lv = a.level_src[j], mg = a.mag_src[j], fm = a.fam_src[j];
         for (int k = li; k < cnt; k += S) {
