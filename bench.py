@@ -44,7 +44,7 @@ INT_OPS_PER_SM_CLK = 128.0
 OPS_PER_ATTEMPT = (2 * 60 + 8 * 3 + 15) / 32 + 62 / 256
 # DRAM bytes per attempt of k_sweep<64> from one ncu capture; None until the current kernel
 # has been captured.
-SWEEP64_DRAM_BYTES_PER_ATTEMPT = (135.470848e6 + 76.445696e6) / (262144 * 4096 * 10)
+SWEEP64_DRAM_BYTES_PER_ATTEMPT = (135.497472e6 + 76.767744e6) / (262144 * 4096 * 10)
 
 
 def _parse_args():
