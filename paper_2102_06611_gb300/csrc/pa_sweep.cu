@@ -4,6 +4,11 @@
 // pa_sweep_hb.cu), and the persistent sweep kernel of batches.
 #include "pa_sweep.cuh"
 
+// Minimum resident blocks of 256 threads per SM of the batched sweep kernels.
+#ifndef PA_BATCH_MIN_BLOCKS
+#define PA_BATCH_MIN_BLOCKS 2
+#endif
+
 namespace pa {
 
 bool sweep_has_template(int L)
@@ -223,7 +228,7 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
 // take items from the group's counter; the item's run is found by bisection over the
 // group's order positions.
 template <int L>
-__global__ void __launch_bounds__(256, 2) k_b_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl,
+__global__ void __launch_bounds__(256, PA_BATCH_MIN_BLOCKS) k_b_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl,
                                                      const int *order, const long long *item_start)
 {
     constexpr int g = batch_group_of(L);
