@@ -328,6 +328,10 @@ def run_ours(args):
             "gpu_launches": KERNELS_PER_STEP * K,
             "wall_s": wall,
         }
+        if world == 1:
+            pc = philox_ceiling(dev, stream)
+            pc["sweep_frac"] = sweep_rate / pc["attempts_per_ns"]
+            line["roofline"]["philox_ceiling"] = pc
         if e2e:
             line["e2e"] = e2e
         if not args.no_schedule_eval and world == 1:
@@ -337,6 +341,35 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def philox_ceiling(dev, stream) -> dict:
+    """The rate of Philox4x32-10 calls alone on this GPU (pa_philox_xor: the sweep's round code,
+    every SM filled), and the sweep rate it allows: 2 calls give the bit planes of 32 attempts."""
+    import ctypes
+
+    import torch
+
+    from paper_2102_06611_gb300 import _lib
+    lib = _lib.lib()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    n, calls = sms * 2048, 2048
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    ms = []
+    for rep in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        assert lib.pa_philox_xor(7, n, calls, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(stream.cuda_stream)) == _lib.PA_OK
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep > 0:
+            ms.append(e0.elapsed_time(e1))
+    best = min(ms)
+    rate = n * calls / (best * 1e6)
+    return {"kernel": "pa_philox_xor", "calls_per_ns": rate, "attempts_per_ns": 16 * rate,
+            "basis": f"{n} threads x {calls} Philox4x32-10 calls, best of 5 (CUDA events); "
+                     "2 calls = the 8 bit planes of 32 attempts"}
 
 
 # ------------------------------------------------------------------------------ reference arm

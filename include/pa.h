@@ -437,6 +437,14 @@ pa_status pa_checkpoint_size(pa_ctx *ctx, size_t *bytes);
 pa_status pa_save(pa_ctx *ctx, void *host_buf, size_t n);
 pa_status pa_load(pa_ctx *ctx, const void *host_buf, size_t n);
 
+/* Measurement utility, not a step of the method: the rate of Philox4x32-10 alone (Salmon et
+   al., SC'11, the generator of every random number above), computed as the sweep computes its
+   bit planes.  Thread t of n_threads writes out_dev[t] (device uint32[n_threads], caller-owned)
+   = XOR over i < calls of the four words of Philox(key = seed, ctr = (i, t, 15 << 28, 0)).
+   Asynchronous on `stream` (the caller times it, e.g. with CUDA events); PA_ERR_INVALID_ARG for
+   n_threads < 1, calls < 0 or a null pointer, PA_ERR_CUDA if the launch fails. */
+pa_status pa_philox_xor(unsigned long long seed, int n_threads, int calls, unsigned int *out_dev, void *stream);
+
 /* Message for the last failing call on ctx (static storage owned by the context). */
 const char *pa_last_error(const pa_ctx *ctx);
 

@@ -137,6 +137,7 @@ SIGNATURES = {
     "pa_copy_counts": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_longlong)]),
     "pa_hashes": (ctypes.c_int, [_vp, _vp]),
     "pa_export_spins": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_longlong, _vp]),
+    "pa_philox_xor": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "pa_copy_numbers_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong, _vp,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_uint,
                                               ctypes.c_ulonglong, ctypes.c_int, _vp, _P(ctypes.c_double),

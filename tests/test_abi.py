@@ -63,6 +63,13 @@ def test_query_sizes_any_even_L(L, bpr):
     assert sz.bytes_per_replica == bpr
 
 
+def test_philox_rate_rejects_bad_arguments():
+    lib = _lib.lib()
+    assert lib.pa_philox_xor(1, 0, 4, ctypes.c_void_p(256), None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_philox_xor(1, 10, -1, ctypes.c_void_p(256), None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_philox_xor(1, 10, 4, None, None) == _lib.PA_ERR_INVALID_ARG
+
+
 def test_batches_take_register_sizes_only():
     """Batches run the per-size register kernels: an even L without one is rejected."""
     lib = _lib.lib()
