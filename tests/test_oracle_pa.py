@@ -241,3 +241,26 @@ def test_anneal_L8_against_kaufman(update):
     e_ex, c_ex, lnZ = oracle.kaufman_thermo(L, 1.0)
     assert abs(o["e"] - e_ex / N) < 0.01
     assert abs(o["minus_betaF"] - lnZ) / N < 2e-3
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("L,update", [(6, oracle.HEATBATH), (10, oracle.METROPOLIS)])
+def test_anneal_padded_rows_against_exact(L, update):
+    """Sizes whose half-rows are padded in the random-number chunks (L/2 = 3, 5 sites in
+    H' = 4, 8 bit positions, several rows per chunk, the last chunk partial): whole anneals
+    reproduce Kaufman's exact free energy along the way and the energy at beta = 1."""
+    R, theta, n = 800, 5, 20
+    N = L * L
+    pa = oracle.PA(L, R, seed=5, update=update)
+    pa.init()
+    for i in range(1, n + 1):
+        beta = i / n
+        assert pa.resample(beta) == 0
+        pa.sweep(theta)
+        if i in (8, 12, 16):
+            o = pa.observables()
+            assert abs(o["minus_betaF"] - oracle.kaufman_lnZ(L, beta)) / N < 5e-3, (L, beta)
+    o = pa.observables()
+    e_ex, _, lnZ = oracle.kaufman_thermo(L, 1.0)
+    assert abs(o["e"] - e_ex / N) < 0.01
+    assert abs(o["minus_betaF"] - lnZ) / N < 5e-3
