@@ -80,3 +80,28 @@ def test_failing_run_is_isolated():
     assert status[0] == 3 and status[1] == 0 and step[1] == 7
     pa = _single(good)
     assert np.array_equal(b.hashes(1), pa.hashes())
+
+
+def test_full_mixed_batch_first_steps_match_single_runs():
+    """The 64-run mixed workload at full size (L in {8, ..., 64}, R up to 2e5, theta in {1, 5,
+    10}): after three batched temperature steps every run is bit-identical to its single run
+    (spin hashes and records)."""
+    from paper_2102_06611_gb300 import PopulationAnnealing
+    from paper_2102_06611_gb300.batch import Batch, mixed_runs
+    specs = mixed_runs()
+    b = Batch(specs)
+    k = 3
+    for _ in range(k):
+        b.step()
+    recs = b.observables()
+    for i, s in enumerate(specs):
+        pa = PopulationAnnealing(s.L, s.R, s.seed, resample=s.resample, capacity=s.capacity)
+        for j in range(1, k + 1):
+            pa.resample(j / (s.n_temps - 1))
+            pa.anneal_step(s.theta)
+        assert np.array_equal(b.hashes(i), pa.hashes()), i
+        o = pa.observables()
+        for key in ("step", "R", "beta", "lnQ", "minus_betaF", "sum_E", "sum_E2", "sum_absM", "sum_M2", "families"):
+            assert recs[i][key] == o[key], (i, key)
+        pa.close()
+    b.close()

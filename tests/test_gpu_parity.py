@@ -235,3 +235,9 @@ def test_full_size_L64_R1e6_replay():
 
 def test_full_size_L64_R1e6_heatbath_replay():
     _replay_steps(64, 1_000_000, "nearest", seed=7, betas=[0.3, 0.7], theta=10, n_sample=24, update="heatbath")
+
+
+def test_full_size_L128_R2e5_replay():
+    """The size on which the learned and the plain schedule are compared (L = 128, R = 2e5),
+    64-bit half-row words, one block per SM."""
+    _replay_steps(128, 200_000, "nearest", seed=1, betas=[0.44, 0.9], theta=10, n_sample=10)
