@@ -20,9 +20,11 @@
 #include "pa_common.cuh"
 #include "pa_kernels.h"
 
-// Minimum resident blocks of 256 threads per SM the sweep kernel is compiled for (caps its
-// registers at 65536 / (256 * n)): 2, except L = 8 and 128, where one block of up to 255
-// registers per thread is faster (measured: +2.5 % and +8 %).
+// Build knobs of the sweep kernel, set to the measured best.  PA_SWEEP_THREADS: threads per
+// block (256; blocks of 128 or 192 were slower).  PA_SWEEP_MIN_BLOCKS: minimum resident
+// blocks per SM it is compiled for, which caps its registers at 65536 / (threads * n): 2,
+// except at L = 8 and 128, where one block of up to 255 registers per thread is faster
+// (L = 128: +3 % over two blocks of 128 registers).
 #ifndef PA_SWEEP_THREADS
 #define PA_SWEEP_THREADS 256
 #endif
