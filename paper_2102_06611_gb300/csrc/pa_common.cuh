@@ -104,21 +104,23 @@ enum : unsigned int {
     kStreamMultinomial = 5u
 };
 
-// The 64-bit product of a Philox round as two separate multiplies (low word, high word):
-// the same values as one widening multiply, and measured 1-2 % faster in the sweep kernels.
+// The 64-bit product of a Philox round as two separate multiplies (low word, high word) or
+// as one widening multiply: the same values; the split form is measured 1-2 % faster in the
+// sweep kernels of L >= 32 and 1-2 % slower below.
 #ifndef PA_MULHI_SPLIT
 #define PA_MULHI_SPLIT 1
 #endif
+template <bool SPLIT = (PA_MULHI_SPLIT != 0)>
 __device__ __forceinline__ void mulhilo(unsigned int a, unsigned int b, unsigned int &hi, unsigned int &lo)
 {
-#if PA_MULHI_SPLIT
-    lo = a * b;
-    hi = __umulhi(a, b);
-#else
-    unsigned long long p = (unsigned long long)a * (unsigned long long)b;
-    hi = (unsigned int)(p >> 32);
-    lo = (unsigned int)p;
-#endif
+    if constexpr (SPLIT) {
+        lo = a * b;
+        hi = __umulhi(a, b);
+    } else {
+        unsigned long long p = (unsigned long long)a * (unsigned long long)b;
+        hi = (unsigned int)(p >> 32);
+        lo = (unsigned int)p;
+    }
 }
 
 __device__ __forceinline__ uint4 philox(uint4 c, unsigned int k0, unsigned int k1)

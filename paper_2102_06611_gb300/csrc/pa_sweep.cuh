@@ -79,35 +79,37 @@ struct PhiloxC0 {
     unsigned int u1k;  // u1 ^ (round-2 key word 0)
 };
 
+template <bool SPLIT = (PA_MULHI_SPLIT != 0)>
 __device__ __forceinline__ PhiloxC0 philox_c0_setup(unsigned int c1, unsigned int c2, unsigned int c3,
                                                     const unsigned int *rk0, const unsigned int *rk1)
 {
     PhiloxC0 p;
     unsigned int h1, l1;
-    mulhilo(kPhiloxM1, c2, h1, l1);
+    mulhilo<SPLIT>(kPhiloxM1, c2, h1, l1);
     p.u0 = h1 ^ c1 ^ rk0[0];
     p.u1 = l1;
     p.u2 = c3 ^ rk1[0];
-    mulhilo(kPhiloxM0, p.u0, p.v_hi, p.v_lo);
+    mulhilo<SPLIT>(kPhiloxM0, p.u0, p.v_hi, p.v_lo);
     p.u1k = p.u1 ^ rk0[1];
     return p;
 }
 
+template <bool SPLIT = (PA_MULHI_SPLIT != 0)>
 __device__ __forceinline__ uint4 philox_c0(unsigned int c0, const PhiloxC0 &p, const unsigned int *rk0,
                                            const unsigned int *rk1)
 {
     unsigned int hi0, lo0;
-    mulhilo(kPhiloxM0, c0, hi0, lo0);
+    mulhilo<SPLIT>(kPhiloxM0, c0, hi0, lo0);
     // round 1: (u0, u1, hi0 ^ c3 ^ k1, lo0); round 2 with the shared M0 * u0
     const unsigned int z2 = hi0 ^ p.u2, z3 = lo0;
     unsigned int h1, l1;
-    mulhilo(kPhiloxM1, z2, h1, l1);
+    mulhilo<SPLIT>(kPhiloxM1, z2, h1, l1);
     uint4 c = make_uint4(h1 ^ p.u1k, l1, p.v_hi ^ z3 ^ rk1[1], p.v_lo);
 #pragma unroll
     for (int i = 2; i < 10; ++i) {
         unsigned int h0, l0, h1, l1;
-        mulhilo(kPhiloxM0, c.x, h0, l0);
-        mulhilo(kPhiloxM1, c.z, h1, l1);
+        mulhilo<SPLIT>(kPhiloxM0, c.x, h0, l0);
+        mulhilo<SPLIT>(kPhiloxM1, c.z, h1, l1);
         c = make_uint4(h1 ^ c.y ^ rk0[i], l1, h0 ^ c.w ^ rk1[i], l0);
     }
     return c;
@@ -235,6 +237,9 @@ struct SweepStyle {
     static constexpr int WORDS = Geo<L>::PACK ? Geo<L>::C : Geo<L>::RPL;
     static constexpr bool TIE_QUEUE = WORDS >= 3;
     static constexpr int TQ_LEN = TIE_QUEUE ? 32 * WORDS : 1;  // queue entries per warp
+    // Philox products of the bit planes as separate low/high multiplies (faster from L = 32
+    // up, measured) or one widening multiply
+    static constexpr bool SPLIT_MUL = (PA_MULHI_SPLIT != 0) && L >= 32;
 };
 
 
@@ -610,13 +615,14 @@ __device__ __forceinline__ void packed_planes(int r0, unsigned int slot, unsigne
                                               unsigned int (*plane)[8])
 {
     using Gm = Geo<L>;
-    const PhiloxC0 pc = philox_c0_setup(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
+    constexpr bool SM = SweepStyle<L>::SPLIT_MUL;
+    const PhiloxC0 pc = philox_c0_setup<SM>(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
     const unsigned int chunk0 = (unsigned int)(r0 / Gm::P);
 #pragma unroll
     for (int c = 0; c < Gm::C; ++c) {
         const unsigned int ch = chunk0 + (unsigned int)c;
-        const uint4 p0 = philox_c0(2 * ch, pc, rk0, rk1);
-        const uint4 p1 = philox_c0(2 * ch + 1, pc, rk0, rk1);
+        const uint4 p0 = philox_c0<SM>(2 * ch, pc, rk0, rk1);
+        const uint4 p1 = philox_c0<SM>(2 * ch + 1, pc, rk0, rk1);
         plane[c][0] = p0.x; plane[c][1] = p0.y; plane[c][2] = p0.z; plane[c][3] = p0.w;
         plane[c][4] = p1.x; plane[c][5] = p1.y; plane[c][6] = p1.z; plane[c][7] = p1.w;
     }
@@ -661,7 +667,8 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
     }
 
     PhiloxC0 pc;
-    if constexpr (!PRE) pc = philox_c0_setup(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
+    if constexpr (!PRE)
+        pc = philox_c0_setup<SweepStyle<L>::SPLIT_MUL>(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
 
     unsigned int lt[C], eq[C], a4[C], g3[C];
 #pragma unroll
@@ -692,8 +699,8 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
             for (int k = 0; k < 8; ++k) pl[k] = plane[c][k];
         } else {
             const unsigned int ch = (unsigned int)(r0 / P + c);
-            const uint4 p0 = philox_c0(2 * ch, pc, rk0, rk1);
-            const uint4 p1 = philox_c0(2 * ch + 1, pc, rk0, rk1);
+            const uint4 p0 = philox_c0<SweepStyle<L>::SPLIT_MUL>(2 * ch, pc, rk0, rk1);
+            const uint4 p1 = philox_c0<SweepStyle<L>::SPLIT_MUL>(2 * ch + 1, pc, rk0, rk1);
             pl[0] = p0.x; pl[1] = p0.y; pl[2] = p0.z; pl[3] = p0.w;
             pl[4] = p1.x; pl[5] = p1.y; pl[6] = p1.z; pl[7] = p1.w;
         }
