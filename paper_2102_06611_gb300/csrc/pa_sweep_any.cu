@@ -34,11 +34,16 @@ using u64 = unsigned long long;
 constexpr int kAnyWarps = 8;  // warps per block
 
 // Class thresholds T_a, a = 0..4 aligned neighbours, split into top 8 and low 24 bits;
-// always has bit a set iff T_a = 2^32 (every site of class a flips).
+// always has bit a set iff T_a = 2^32 (every site of class a flips).  Metropolis only needs
+// T_3 and T_4: the threshold bit of plane k is then all4 * sel[k] + m3[k] (m3[k] = all ones
+// iff bit 7 - k of T_3's top bits is set; sel[k] = +1 / -1 / 0 where only T_4's, only T_3's
+// or both or neither bits are set), one multiply-add instead of a test per class.
 struct ClassThr {
     unsigned int top[5];
     unsigned int low[5];
     unsigned int always;
+    int metropolis;
+    unsigned int m3[8], sel[8];
 };
 
 __device__ ClassThr class_thresholds(int update, u64 T4, u64 T8)
@@ -65,6 +70,12 @@ __device__ ClassThr class_thresholds(int update, u64 T4, u64 T8)
             c.top[a] = (unsigned int)(T[a] >> 24);
             c.low[a] = (unsigned int)(T[a] & 0xFFFFFFull);
         }
+    }
+    c.metropolis = update != PA_UPDATE_HEATBATH;
+    for (int k = 0; k < 8; ++k) {
+        const unsigned int b3 = (c.top[3] >> (7 - k)) & 1u, b4 = (c.top[4] >> (7 - k)) & 1u;
+        c.m3[k] = b3 ? 0xFFFFFFFFu : 0u;
+        c.sel[k] = (b3 == b4) ? 0u : (b4 ? 1u : 0xFFFFFFFFu);
     }
     return c;
 }
@@ -104,15 +115,50 @@ __host__ __device__ AnyGeo any_geo(int L)
     return g;
 }
 
+// all4 * sel + m3 on each 32-bit half (all4, the sites whose four neighbours align)
+template <typename W>
+__device__ __forceinline__ W metropolis_bits(W all4, unsigned int sel, unsigned int m3)
+{
+    if constexpr (sizeof(W) == 4) {
+        return all4 * sel + m3;
+    } else {
+        const unsigned int lo = (unsigned int)all4 * sel + m3, hi = (unsigned int)(all4 >> 32) * sel + m3;
+        return ((W)hi << 32) | (W)lo;
+    }
+}
+
 // Classes and the top-8-bit decision of one word: returns the decided flips; eq = the
 // sites whose top bits tie with their class threshold, cls = the class masks (a aligned
-// neighbours, a = 0..4).  Sites outside V stay clear.
+// neighbours, a = 0..4; Metropolis: only classes 3 and 4, the others always flip).  Sites
+// outside V stay clear.
 template <typename W>
 __device__ __forceinline__ W decide(W s, W up, W dn, W o, W side, W V, const W *pl, const ClassThr &th, W &eq,
                                     W *cls)
 {
-    // aligned-neighbour count a = x1 + x2 + x3 + x4 in three bit slices
     const W x1 = ~(s ^ up) & V, x2 = ~(s ^ dn) & V, x3 = ~(s ^ o) & V, x4 = ~(s ^ side) & V;
+    if (th.metropolis) {
+        // a >= 3: both of one pair aligned and at least one of the other
+        const W t12 = x1 & x2, t34 = x3 & x4;
+        const W all4 = t12 & t34;
+        const W ge3 = (t12 & (x3 | x4)) | (t34 & (x1 | x2));
+        const W eq3 = ge3 & ~all4;
+        cls[0] = cls[1] = cls[2] = 0;
+        cls[3] = eq3;
+        cls[4] = all4;
+        W alw = V & ~ge3;
+        if (th.always & 8u) alw |= eq3;
+        if (th.always & 16u) alw |= all4;
+        W lt = 0, e = V & ~alw;
+        for (int k = 7; k >= 0; --k) {
+            const W tm = metropolis_bits<W>(all4, th.sel[k], th.m3[k]);
+            const W np = ~pl[k];
+            lt = (np & tm) | (np & lt) | (tm & lt);
+            e &= ~(pl[k] ^ tm);
+        }
+        eq = e;
+        return alw | (lt & ~alw & V);  // tm has bits outside V where m3 is all ones
+    }
+    // aligned-neighbour count a = x1 + x2 + x3 + x4 in three bit slices
     const W s12 = x1 ^ x2, c12 = x1 & x2, s34 = x3 ^ x4, c34 = x3 & x4;
     const W b0 = s12 ^ s34, cr = s12 & s34;
     const W b1 = c12 ^ c34 ^ cr;
@@ -144,7 +190,12 @@ __device__ __forceinline__ bool tie_accept(int r, int p, int a, unsigned int slo
                                            unsigned int k0, unsigned int k1, const ClassThr &th)
 {
     const uint4 x = philox(make_uint4((unsigned int)(64 * r + p), slot, (kStreamRefine << 28) | tag, step), k0, k1);
-    return (x.x & 0xFFFFFFu) < th.low[a];
+    // select with constant indices (a run-time index would move the thresholds to local memory)
+    unsigned int low = th.low[0];
+#pragma unroll
+    for (int c = 1; c < 5; ++c)
+        if (a == c) low = th.low[c];
+    return (x.x & 0xFFFFFFu) < low;
 }
 
 template <typename W>
@@ -158,7 +209,7 @@ __device__ __forceinline__ int class_of(const W *cls, W bit)
 
 // One colour q of one sweep, narrow sizes: the lane updates chunks c0, c0 + Gc, ... of the
 // replica S (S[2r] = even-column half of row r, S[2r + 1] = odd-column half).
-__device__ void half_sweep_chunks(u64 *S, const AnyGeo &g, int q, unsigned int slot, unsigned int tag,
+__device__ __forceinline__ void half_sweep_chunks(u64 *S, const AnyGeo &g, int q, unsigned int slot, unsigned int tag,
                                   unsigned int step, unsigned int k0, unsigned int k1, const ClassThr &th, int c0)
 {
     const int L = g.L, H = g.H, HP = g.HP, P = g.P;
@@ -207,7 +258,7 @@ __device__ void half_sweep_chunks(u64 *S, const AnyGeo &g, int q, unsigned int s
 
 // One colour q of one sweep, wide sizes: the lane updates rows c0, c0 + 32, ... (one row =
 // chunks 2r and 2r + 1, four Philox calls for its planes).
-__device__ void half_sweep_rows(u64 *S, const AnyGeo &g, int q, unsigned int slot, unsigned int tag,
+__device__ __forceinline__ void half_sweep_rows(u64 *S, const AnyGeo &g, int q, unsigned int slot, unsigned int tag,
                                 unsigned int step, unsigned int k0, unsigned int k1, const ClassThr &th, int c0)
 {
     const int L = g.L, H = g.H;
