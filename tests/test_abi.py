@@ -101,3 +101,13 @@ def test_init_rejects_null_and_misaligned_buffers():
     bufs.work = 4096
     assert lib.pa_init(ctypes.byref(cfg), ctypes.byref(bufs), None, ctypes.byref(ctx)) == _lib.PA_ERR_INVALID_ARG
     assert not ctx.value
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """Without a CUDA device the product path raises instead of computing anywhere else."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2102_06611_gb300 import PopulationAnnealing
+    with pytest.raises(Exception):
+        PopulationAnnealing(8, 100, 1)
