@@ -1,5 +1,5 @@
 """Pins of the oracle's learned-schedule pieces: bfloat16 rounding, the MLP gradient
-(finite differences), the Adam step (closed form of its first step) and the features
+(finite differences), the Adam step (closed forms of its first steps) and the features
 (moments from per-replica energies instead of the histogram)."""
 import math
 
@@ -48,6 +48,28 @@ def test_adam_first_step_is_lr_times_sign():
     g = np.array([0.3, -2.0, 1e-3])
     th, m, v = mlp.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, lr=0.01)
     assert np.allclose(th, -0.01 * np.sign(g), rtol=1e-4)
+
+
+def test_adam_constant_gradient_steps_by_lr():
+    """With the same gradient at every step the bias-corrected moments equal g and g^2 at
+    every t (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so each step moves lr * sign(g):
+    after t steps theta = -t lr sign(g).  A bias correction with a fixed t = 1 would move
+    (1 + b1) / sqrt(1 + b2) ~ 1.34 lr at step 2."""
+    g = np.array([0.3, -2.0, 1e-3])
+    th, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    for t in (1, 2, 3):
+        th, m, v = mlp.adam_step(th, m, v, g, t, lr=0.01)
+        assert np.allclose(th, -0.01 * t * np.sign(g), rtol=1e-4), t
+
+
+def test_adam_second_step_after_zero_gradient():
+    """Gradient g at step 1 and 0 at step 2: m_2 = b1 (1 - b1) g and v_2 = b2 (1 - b2) g^2, so
+    the bias-corrected step is lr sign(g) (b1 / (1 + b1)) / sqrt(b2 / (1 + b2)); with
+    b1 = 0.9, b2 = 0.999 that is 0.670058 lr (to 6 digits)."""
+    g = np.array([0.5, -4.0])
+    th, m, v = mlp.adam_step(np.zeros(2), np.zeros(2), np.zeros(2), g, 1, lr=0.01)
+    th2, _, _ = mlp.adam_step(th, m, v, np.zeros(2), 2, lr=0.01)
+    assert np.allclose(th2 - th, -0.01 * 0.670058 * np.sign(g), rtol=2e-6)
 
 
 def test_features_from_population():
