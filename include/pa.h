@@ -363,8 +363,10 @@ pa_status pa_export_spins(pa_ctx *ctx, long long first, long long count, unsigne
    level tables, block sums) is one fixed array of 493,056 bytes in the library image, present
    on every GPU that loads the library until the process exits.  Limits: L even, 4 <= L <= 128
    (so at most 16385 levels) and 1 <= R_prev <= 4,194,304; a larger R_prev returns
-   PA_ERR_TOO_LARGE.  Allocates nothing.  The first call on a device also looks up the array's
-   device address (once per device); make that first call before any stream capture.  All calls
+   PA_ERR_TOO_LARGE.  Allocates nothing.  Every call looks up the array's device address on the
+   current device (so the address stays valid across cudaDeviceReset); the first call on a
+   device may also load the library's code there, so make that first call before any stream
+   capture.  `stream` must belong to the current device (else PA_ERR_INVALID_ARG).  All calls
    share the array and each clears what it needs first; calls that overlap on the GPU (e.g. on
    two streams) race.  Synchronises `stream`. */
 pa_status pa_copy_numbers_static(int L, long long R_target, long long R_prev, const int *level_dev,
@@ -432,7 +434,12 @@ void pa_batch_destroy(pa_batch *b);
    current population; pa_save writes them to host memory; pa_load restores them into a
    context created with the same pa_config, after which the run continues exactly as the
    uninterrupted one.  All synchronising; PA_ERR_INVALID_ARG for a short buffer, a foreign or
-   truncated checkpoint, or a different configuration. */
+   truncated checkpoint, or a different configuration.  pa_load checks the body on the host
+   before copying anything to the device and also returns PA_ERR_INVALID_ARG, leaving the
+   context as it was, if the state block disagrees with the header or carries an error, or if
+   an energy level lies outside [0, N], a magnetisation outside [-N, N] (or of the wrong
+   parity), a family id outside [0, R) or out of tree order, or a copy number is negative or
+   the copy numbers add up to more than the capacity. */
 pa_status pa_checkpoint_size(pa_ctx *ctx, size_t *bytes);
 pa_status pa_save(pa_ctx *ctx, void *host_buf, size_t n);
 pa_status pa_load(pa_ctx *ctx, const void *host_buf, size_t n);

@@ -686,6 +686,57 @@ size_t ckpt_bytes(const pa_ctx *c, long long R, long long Rp, long long nlog)
            (size_t)R * (bpr + 4 * sizeof(int)) + (size_t)Rp * sizeof(int) + (size_t)nlog * sizeof(pa_sched_entry);
 }
 
+// Host-side check of a checkpoint body before anything reaches the device: the kernels bound
+// their loops by the state block's R_cur / R_prev and index the level tables by stored energy
+// levels, so a file whose state block disagrees with its header, or whose levels, family ids,
+// magnetisations or copy numbers are out of range, is rejected here instead of driving
+// out-of-range device accesses.  Returns null if the body is consistent, else the reason.
+const char *ckpt_invalid(const pa_ctx *c, const CkptHeader &h, const char *p)
+{
+    const int N = c->N;
+    if (h.step < 0 || h.sweeps_in_step < 0 || h.theta_last < 0 || (h.measured != 0 && h.measured != 1) ||
+        !std::isfinite(h.beta) || !std::isfinite(h.dbeta))
+        return "header fields out of range";
+    pa::DevState ds;
+    std::memcpy(&ds, p, sizeof(ds));
+    p += sizeof(ds);
+    if (ds.R_cur != h.R_cur || ds.R_prev != h.R_prev) return "state block sizes differ from the header";
+    if (ds.error != 0) return "state block carries an error";
+    if (ds.update != c->cfg.update || ds.kmin < 0 || ds.kmin > N || ds.theta < 0 ||
+        ds.T4 > (1ull << 32) || ds.T8 > (1ull << 32))
+        return "state block fields out of range";
+    auto ints = [&p](long long n) {
+        const char *q = p;
+        p += sizeof(int) * (size_t)n;
+        return q;
+    };
+    auto get = [](const char *base, long long j) {
+        int v;
+        std::memcpy(&v, base + sizeof(int) * (size_t)j, sizeof(v));
+        return v;
+    };
+    const char *hist = ints(N + 1);
+    for (int k = 0; k <= N; ++k)
+        if (get(hist, k) < 0) return "negative histogram entry";
+    p += (size_t)pa::bytes_per_replica(c->cfg.L) * (size_t)h.R_cur;
+    const char *level = ints(h.R_cur), *mag = ints(h.R_cur), *fam = ints(h.R_cur), *snap = ints(h.R_cur);
+    const char *counts = ints(h.R_prev);
+    for (long long j = 0; j < h.R_cur; ++j) {
+        const int k = get(level, j), m = get(mag, j), f = get(fam, j), k0 = get(snap, j);
+        if (k < 0 || k > N || k0 < 0 || k0 > N) return "energy level out of range";
+        if (m < -N || m > N || ((m + N) & 1)) return "magnetisation out of range";
+        if (f < 0 || f >= c->cfg.R || (j > 0 && f < get(fam, j - 1))) return "family ids out of range or order";
+    }
+    long long total = 0;
+    for (long long j = 0; j < h.R_prev; ++j) {
+        const int r = get(counts, j);
+        if (r < 0) return "negative copy number";
+        total += r;
+    }
+    if (total > c->cfg.capacity) return "copy numbers exceed the capacity";
+    return nullptr;
+}
+
 pa_status read_sizes(pa_ctx *c, long long *R, long long *Rp)
 {
     pa_status s = sync_and_check(c);
@@ -767,6 +818,8 @@ pa_status pa_load(pa_ctx *c, const void *host_buf, size_t n)
     if (h.R_cur < 1 || h.R_cur > c->cfg.capacity || h.R_prev < 0 || h.R_prev > c->cfg.capacity || h.n_log < 0 ||
         n < ckpt_bytes(c, h.R_cur, h.R_prev, h.n_log))
         return fail(c, PA_ERR_INVALID_ARG, "truncated or inconsistent checkpoint");
+    if (const char *why = ckpt_invalid(c, h, static_cast<const char *>(host_buf) + sizeof(h)))
+        return fail(c, PA_ERR_INVALID_ARG, "invalid checkpoint: %s", why);
     DeviceGuard g(c->device);
     if ((s = sync_and_check(c)) != PA_OK) return s;
     const char *p = static_cast<const char *>(host_buf) + sizeof(h);

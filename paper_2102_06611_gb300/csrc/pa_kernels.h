@@ -1,6 +1,8 @@
 // pa_kernels.h -- argument blocks and launchers of the library's kernels (internal).
 #pragma once
 
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "pa.h"
@@ -8,6 +10,31 @@
 namespace pa {
 
 struct DevState;
+
+// Runs a one-time set-up step (e.g. raising a kernel's dynamic shared-memory limit, an
+// attribute each device keeps separately) once per device: the device current at the call
+// selects the flag.  Thread safe.
+class PerDeviceOnce {
+public:
+    template <class F>
+    cudaError_t operator()(F &&f)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kDevices) return f();
+        std::lock_guard<std::mutex> lock(mu_);
+        if (done_[dev]) return cudaSuccess;
+        e = f();
+        if (e == cudaSuccess) done_[dev] = true;
+        return e;
+    }
+
+private:
+    static constexpr int kDevices = 64;
+    std::mutex mu_;
+    bool done_[kDevices] = {};
+};
 
 // Workspace layout (byte offsets, all 256-byte aligned), computed by plan_workspace().
 struct Workspace {

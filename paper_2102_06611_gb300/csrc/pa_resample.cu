@@ -522,16 +522,19 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
 
 __global__ void __launch_bounds__(kCountThreads) k_copy(ResampleArgs a, int chunks16) { copy_body(a, chunks16); }
 
+// k_table's dynamic shared-memory limit (up to 16385 doubles), raised once per device
+static PerDeviceOnce table_smem_once;
+
 cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
 {
     const int nlev = a.L * a.L + 1;
     const size_t smem = (size_t)nlev * sizeof(double);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+    {
+        cudaError_t e = table_smem_once([] {
+            return cudaFuncSetAttribute(k_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     k_table<<<1, kTableThreads, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -561,12 +564,12 @@ cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s)
 {
     const int nlev = a.L * a.L + 1;
     const size_t smem = (size_t)nlev * sizeof(double);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+    {
+        cudaError_t e = table_smem_once([] {
+            return cudaFuncSetAttribute(k_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     k_table<<<1, kTableThreads, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -985,12 +988,13 @@ cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl 
                               long long *item_start, pa_obs *records, int n, int nblk_max, int nlev_max,
                               const BatchSweepPlan &plan, cudaStream_t s)
 {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_b_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+    {
+        static PerDeviceOnce once;
+        cudaError_t e = once([] {
+            return cudaFuncSetAttribute(k_b_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     cudaError_t e;
     k_b_begin<<<1, 256, 0, s>>>(runs, state, n);

@@ -11,16 +11,17 @@
 //
 // The array is part of the library image, so every GPU that loads the library holds its
 // kStaticScratchBytes until the process exits.  Host code cannot use the array's name as a
-// device address (on the host it is only a stand-in symbol); the first call on each device
-// looks up its device address with cudaGetSymbolAddress while that device is current, and
-// later calls reuse it.  That first call should therefore come before any stream capture.
+// device address (on the host it is only a stand-in symbol); every call looks up its device
+// address with cudaGetSymbolAddress on the current device (a lookup, not an allocation), so an
+// address never outlives the context it came from (e.g. across cudaDeviceReset).  The first
+// call on a device may load the library's code onto it, so that first call should come before
+// any stream capture.  The stream passed must belong to the current device.
 // All calls share the one array: each call clears the state and histogram it relies on, and
 // two calls whose kernels overlap on the GPU (e.g. on two streams) race on it.
 //
 // The kernels are the library's own level-table, copy-number and prefix-sum kernels; only the
 // location of their scratch differs.  Nothing here allocates device memory.
 #include <cmath>
-#include <mutex>
 
 #include "pa_common.cuh"
 #include "pa_kernels.h"
@@ -45,27 +46,27 @@ constexpr size_t kStaticScratchBytes = a256(kOffBlock + (size_t)kStaticMaxBlocks
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device (looked up once per device).
+// Device address of g_static_scratch in the current device's context.  Looked up on every
+// call: after a cudaDeviceReset the array lives in a new context, possibly at another address.
 cudaError_t scratch_for_current_device(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        if (!p) return cudaErrorInvalidSymbol;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    if (!p) return cudaErrorInvalidSymbol;
+    *out = p;
     return cudaSuccess;
+}
+
+// True if `s` is a stream of the current device (the legacy and per-thread default streams
+// always are).
+bool stream_on_current_device(cudaStream_t s)
+{
+    int dev = 0, sdev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) return true;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return false;
+    return sdev == dev;
 }
 
 // Level histogram of the caller's parents; a level outside [0, N] is reported, not used.
@@ -96,6 +97,7 @@ extern "C" pa_status pa_copy_numbers_static(int L, long long R_target, long long
         return PA_ERR_INVALID_ARG;
     if (R_prev > kStaticMaxParents) return PA_ERR_TOO_LARGE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!stream_on_current_device(s)) return PA_ERR_INVALID_ARG;
     void *base = nullptr;
     if (scratch_for_current_device(&base) != cudaSuccess) return PA_ERR_CUDA;
     unsigned char *b = static_cast<unsigned char *>(base);

@@ -438,15 +438,13 @@ template <bool INIT>
 cudaError_t launch_any_t(int L, const SweepArgs &a, int num_sms, cudaStream_t s)
 {
     const size_t smem = any_smem_bytes(L);
-    static bool attr_set = false;  // the limit is set once, for the largest need
-    cudaError_t e = cudaSuccess;
-    if (!attr_set) {
+    static PerDeviceOnce once;  // the limit is set once per device, for the largest need
+    cudaError_t e = once([] {
         size_t most = 0;
         for (int l = 4; l <= 128; l += 2) most = any_smem_bytes(l) > most ? any_smem_bytes(l) : most;
-        e = cudaFuncSetAttribute(k_sweep_any<INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaFuncSetAttribute(k_sweep_any<INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    });
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_any<INIT>, 32 * kAnyWarps, smem);
     if (e != cudaSuccess) return e;

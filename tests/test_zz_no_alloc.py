@@ -4,8 +4,10 @@ pa_copy_numbers_static serves callers that cannot hand the library a workspace b
 that may only touch the arrays it is given, or a process that forbids cudaMalloc after
 start-up).  Its scratch is a fixed device array inside the library.  This test calls it
 through the C ABI on two consecutive resampling steps and requires the same copy numbers,
-population size and ln Q as pa_resample on the same parents.  The file is named so that
-pytest collects it last.
+population size and ln Q as pa_resample on the same parents, and as the CPU oracle's
+resampling step given the same parent levels.  L = 128 covers the largest level table
+(16385 levels, more than 48 KB of shared memory in the table kernel).  The file is named so
+that pytest collects it last.
 """
 import ctypes
 
@@ -27,8 +29,10 @@ def _static_copy_numbers(lib, L, R_target, levels_dev, beta_prev, beta_new, step
     return st, counts.cpu().numpy(), lnQ.value, R_new.value
 
 
-@pytest.mark.parametrize("L,R,kind", [(32, 20000, "nearest"), (16, 5000, "poisson")])
+@pytest.mark.parametrize("L,R,kind", [(32, 20000, "nearest"), (16, 5000, "poisson"), (128, 3000, "nearest"),
+                                      (96, 2000, "poisson")])
 def test_static_entry_point_matches_resample(L, R, kind):
+    import oracle
     from paper_2102_06611_gb300 import PopulationAnnealing, _lib
     seed = 13
     pa = PopulationAnnealing(L, R, seed, resample=kind)
@@ -46,6 +50,11 @@ def test_static_entry_point_matches_resample(L, R, kind):
         assert st == _lib.PA_OK
         assert np.array_equal(counts, expected)
         assert R_new == pa.R == int(expected.sum())
+        o_kind = oracle.POISSON if kind == "poisson" else oracle.NEAREST
+        o_st, o_counts, o_lnQ, _, _, o_R = oracle.resample_levels(L, R, levels, beta_prev, beta, step, seed, o_kind,
+                                                                  oracle.default_capacity(R))
+        assert o_st == 0 and np.array_equal(counts, o_counts) and R_new == o_R
+        assert abs(lnQ - o_lnQ) <= 1e-12 * max(1.0, abs(o_lnQ))
         pa.anneal_step(2)
         obs = pa.observables()
         assert abs(lnQ - obs["lnQ"]) <= 1e-12 * max(1.0, abs(obs["lnQ"]))
