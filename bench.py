@@ -58,6 +58,10 @@ def _parse_args():
     p.add_argument("--theta", type=int, default=THETA)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-schedule-eval", action="store_true")
+    p.add_argument("--no-batch-eval", action="store_true",
+                   help="skip the bounded 64-run batch figure of the default line")
+    p.add_argument("--no-whole-anneal", action="store_true",
+                   help="skip the whole-anneal end-to-end figure of the default line")
     p.add_argument("--workload", choices=["single", "batch"], default="single",
                    help="single: the L=64, R=1e6 run (default); batch: 64 mixed independent runs")
     p.add_argument("--update", choices=["metropolis", "heatbath"], default="metropolis",
@@ -135,23 +139,60 @@ def oracle_rate(L: int, R_sample: int, steps: int, theta: int, seed: int):
     return attempts / (dt * 1e9), attempts, dt
 
 
+def _oracle_worker(job):
+    L, R_sample, steps, theta, seed = job
+    _, att, dt = oracle_rate(L, R_sample, steps, theta, seed)
+    return att, dt
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
 def cpu_baseline(L: int, theta: int) -> dict:
-    R_sample, steps = 1000, 10
-    v, att, dt = oracle_rate(L, R_sample, steps, theta, SEED)
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"L={L}, R={R_sample}, {steps} temperature steps beta=i/300, theta={theta}: "
-                      f"{att:.3g} attempts in {dt:.1f} s (single-threaded C oracle)"}
+    """The oracle as it stands on the host: one core, and every core of the process's affinity
+    set running its own oracle population (a replica-parallel split of the same workload:
+    the per-attempt cost does not depend on R).  Worker processes are started with spawn."""
+    import multiprocessing as mp
+    R_sample, steps = 1000, 6
+    v1, att1, dt1 = oracle_rate(L, R_sample, steps, theta, SEED)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(L, R_sample, steps, theta, SEED + 1 + c) for c in range(cores)])
+    att_all = sum(a for a, _ in res)
+    dt_all = max(d for _, d in res)
+    model = cpu_model()
+    return {"value": att_all / (dt_all * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": model,
+            "sample": f"L={L}, {cores} independent oracle populations of R={R_sample} (one per core, "
+                      f"spawned processes), {steps} temperature steps beta=i/300, theta={theta}: "
+                      f"{att_all:.3g} attempts, slowest worker {dt_all:.1f} s",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": model,
+                            "sample": f"L={L}, R={R_sample}, {steps} temperature steps beta=i/300, theta={theta}: "
+                                      f"{att1:.3g} attempts in {dt1:.1f} s (single-threaded C oracle)"}}
 
 
 # ------------------------------------------------------------------------------ schedules
 SCHED_L, SCHED_R, SCHED_SEEDS, SCHED_TARGET = 128, 200_000, (1, 2, 3, 4), 1e-4
 
 
+SCHED_MODES = ("plain", "rule", "learned")
+
+
 def schedule_eval(dev) -> dict:
     """Second half of the metric: wall time of a whole anneal (beta 0 -> 1, L=128, R=2e5) with
-    the plain adaptive schedule (overlap bisection at 0.8, theta = 10) and with the learned one,
-    and each run's free-energy deviation per spin at beta = 1 from the exact finite-lattice
-    value (Kaufman's closed form, tests/golden/exact_lnZ.json); seeds 1-4."""
+    the plain adaptive schedule (overlap bisection at 0.8, theta = 10), with the same bisection
+    plus the measured-decorrelation rule for theta and no network ("rule", the ablation of the
+    network), and with the learned one, and each run's free-energy deviation per spin at
+    beta = 1 from the exact finite-lattice value (Kaufman's closed form,
+    tests/golden/exact_lnZ.json); seeds 1-4."""
     import torch
 
     from paper_2102_06611_gb300 import PopulationAnnealing
@@ -165,7 +206,7 @@ def schedule_eval(dev) -> dict:
            "exact_lnZ_beta1": exact, "runs": []}
     for seed in SCHED_SEEDS:
         run = {"seed": seed}
-        for mode in ("plain", "learned"):
+        for mode in SCHED_MODES:
             pa = PopulationAnnealing(SCHED_L, SCHED_R, seed, device=dev)
             r = anneal(pa, mode, model)
             r["abs_dbetaf_per_spin"] = abs(r["minus_betaF"] - exact) / (SCHED_L * SCHED_L)
@@ -176,11 +217,14 @@ def schedule_eval(dev) -> dict:
             del pa
             torch.cuda.empty_cache()
         run["speedup"] = run["plain"]["wall_s"] / run["learned"]["wall_s"]
+        run["speedup_over_rule"] = run["rule"]["wall_s"] / run["learned"]["wall_s"]
         out["runs"].append(run)
-    for mode in ("plain", "learned"):
+    for mode in SCHED_MODES:
         out[mode + "_wall_s_total"] = sum(r[mode]["wall_s"] for r in out["runs"])
+        out[mode + "_sweeps_total"] = sum(r[mode]["sweeps"] for r in out["runs"])
         out[mode + "_reached_target"] = sum(bool(r[mode]["reached_target"]) for r in out["runs"])
     out["speedup"] = out["plain_wall_s_total"] / out["learned_wall_s_total"]
+    out["speedup_over_rule"] = out["rule_wall_s_total"] / out["learned_wall_s_total"]
     return out
 
 
@@ -283,16 +327,21 @@ def run_ours(args):
                    "(host record, synchronising); beta passes by value, no input tensor is copied"}
     pa2.close()
     del pa2
+    torch.cuda.empty_cache()
+    whole = None if args.no_whole_anneal else whole_anneal_e2e(args, dev, stream, rank)
 
     from paper_2102_06611_gb300.multi import aggregate
     ms, sweep_ms, attempts = aggregate(ms, sweep_ms, attempts, device=dev)
 
+    pc = philox_ceiling(dev, stream)
     if rank == 0:
         value = attempts / (ms * 1e6)
         sweep_rate = (attempts / world) / (sweep_ms * 1e6)
         f_mhz = clk["sm_mhz"] or 2070.0
         peak_tops = SMS * INT_OPS_PER_SM_CLK * f_mhz * 1e6 / 1e12           # int32 Tops/s
         achieved_tops = sweep_rate * 1e9 * OPS_PER_ATTEMPT / 1e12
+        traffic = (SWEEP64_DRAM_BYTES_PER_ATTEMPT * attempts / world / K
+                   if (L == 64 and SWEEP64_DRAM_BYTES_PER_ATTEMPT) else None)
         line = {
             "metric": METRIC,
             "value": value,
@@ -313,27 +362,32 @@ def run_ours(args):
                        "parallelism": f"independent runs x{world}" if world > 1 else "single run",
                        "beta_timed": [beta(W + 1), beta(W + K)],
                        "l2": "inputs larger than L2 (2 x %.0f MB spin buffers)" % (R * L * 2 * 4 / 1e6)},
-            "roofline": {"bound": "alu", "kernel": f"k_sweep<{L}>", "achieved": achieved_tops,
-                         "peak": peak_tops, "unit": "Tops/s (int32)", "frac": achieved_tops / peak_tops,
-                         "traffic": (SWEEP64_DRAM_BYTES_PER_ATTEMPT * attempts / world / K
-                                     if (L == 64 and SWEEP64_DRAM_BYTES_PER_ATTEMPT) else None),
+            "roofline": {"bound": "alu", "kernel": f"k_sweep<{L}>", "achieved": sweep_rate,
+                         "peak": pc["attempts_per_ns"], "unit": "attempts/ns",
+                         "frac": sweep_rate / pc["attempts_per_ns"],
+                         "peak_basis": "measured Philox4x32-10 rate alone on this GPU (pa_philox_xor, the "
+                                       "sweep's round code, every SM filled) x 16 attempts per call: the "
+                                       "generator's share of the bit-plane Metropolis step alone",
+                         "traffic": traffic,
                          "traffic_unit": "DRAM bytes per launch (ncu, scaled from R=262144 by attempts)",
-                         "achieved_attempts_per_ns": sweep_rate,
-                         "peak_attempts_per_ns": peak_tops * 1e3 / OPS_PER_ATTEMPT,
-                         "ops_per_attempt": OPS_PER_ATTEMPT,
-                         "peak_basis": "152 SM x 128 int32 ops/clk/SM x median SM clock (sampled); "
-                                       "algorithmic ops per attempt of the bit-plane Metropolis step"},
+                         "philox_ceiling": pc,
+                         "dispatch_peak": {"achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
+                                           "frac": achieved_tops / peak_tops, "ops_per_attempt": OPS_PER_ATTEMPT,
+                                           "peak_attempts_per_ns": peak_tops * 1e3 / OPS_PER_ATTEMPT,
+                                           "basis": "152 SM x 128 int32 ops/clk/SM x median SM clock "
+                                                    "(sampled); algorithmic ops per attempt of the "
+                                                    "bit-plane Metropolis step"}},
             "sweep_share": sweep_ms / ms,
             "clocks": clk,
             "gpu_launches": KERNELS_PER_STEP * K,
             "wall_s": wall,
         }
-        if world == 1:
-            pc = philox_ceiling(dev, stream)
-            pc["sweep_frac"] = sweep_rate / pc["attempts_per_ns"]
-            line["roofline"]["philox_ceiling"] = pc
         if e2e:
             line["e2e"] = e2e
+        if whole:
+            line["e2e_whole_anneal"] = whole
+        if not args.no_batch_eval and world == 1:
+            line["batch_c4"] = batch_eval(dev, BATCH_EVAL_STEPS, True)
         if not args.no_schedule_eval and world == 1:
             line["learned_schedule"] = schedule_eval(dev)
         if not args.no_cpu_baseline and world == 1:
@@ -341,6 +395,47 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+BATCH_EVAL_STEPS = 20
+
+
+def whole_anneal_e2e(args, dev, stream, rank: int) -> dict:
+    """One whole anneal through the public API, timed end to end on the host clock: pa_init
+    from the seed (buffers included), all 300 temperature steps (pa_resample, pa_anneal_step,
+    pa_observables with its host record every step), and the final host readback of the level
+    histogram."""
+    import ctypes
+
+    import torch
+
+    from paper_2102_06611_gb300 import PopulationAnnealing, pa_obs
+    from paper_2102_06611_gb300.multi import rank_seed
+
+    L, R, theta = args.L, args.R, args.theta
+    N = L * L
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pa = PopulationAnnealing(L, R, rank_seed(SEED, rank), device=dev, stream=stream, update=args.update,
+                             resample=args.resample)
+    att = 0.0
+    for i in range(1, N_TEMPS):
+        pa.resample(i / (N_TEMPS - 1))
+        pa.anneal_step(theta)
+        att += float(N) * pa.observables()["R"] * theta
+    hist = pa.histogram()
+    dt = time.perf_counter() - t0
+    assert int(hist.sum()) == pa.R
+    pa.close()
+    del pa
+    torch.cuda.empty_cache()
+    steps = N_TEMPS - 1
+    return {"value": att / (dt * 1e9), "unit": UNIT, "wall_s": dt, "steps": steps,
+            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": ctypes.sizeof(pa_obs),
+            "d2h_bytes_final": 4 * (N + 1),
+            "note": "host clock: buffers + pa_init (simple sampling on the GPU) + 300 x (pa_resample, "
+                    "pa_anneal_step, pa_observables) + final histogram readback; the configuration and "
+                    "beta pass by value, so no input array is copied"}
 
 
 def philox_ceiling(dev, stream) -> dict:
@@ -408,10 +503,10 @@ def run_reference(args):
     }), flush=True)
 
 
-def run_batch(args):
-    """64 independent runs (mixed L, R, temperature count, theta) to completion, batched (one
-    graph replay per temperature step) and, for comparison, the same runs one after another
-    through the single-run API."""
+def batch_eval(dev, steps: int = 0, sequential: bool = True) -> dict:
+    """64 independent runs (mixed L, R, temperature count, theta), batched (one graph replay per
+    temperature step) and, for comparison, the same runs one after another through the
+    single-run API; `steps` > 0 bounds both to the first `steps` temperature steps."""
     import ctypes
 
     import torch
@@ -419,13 +514,10 @@ def run_batch(args):
     from paper_2102_06611_gb300 import OBS_BYTES, PopulationAnnealing, pa_obs
     from paper_2102_06611_gb300.batch import Batch, mixed_runs
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
     specs = mixed_runs()
     n = len(specs)
-    steps = max(s.n_temps for s in specs) - 1
-    if args.batch_steps > 0:
-        steps = min(steps, args.batch_steps)
+    total_steps = max(s.n_temps for s in specs) - 1
+    steps = min(total_steps, steps) if steps > 0 else total_steps
     words = (OBS_BYTES + 7) // 8
     b = Batch(specs, device=dev)
     rec = torch.zeros((steps, n, words), dtype=torch.int64, device=dev)
@@ -445,14 +537,14 @@ def run_batch(args):
         for r in range(n):
             o = pa_obs.from_buffer_copy(recs[s, r].tobytes()[: ctypes.sizeof(pa_obs)])
             if o.step == s + 1:
+                assert o.status == 0, f"run {r}: device error {o.status}"
                 attempts += float(specs[r].L ** 2) * o.R * specs[r].theta
     tuning = b.tuning()
     b.close()
     del b
     torch.cuda.empty_cache()
-    # the same runs (the same temperature steps) through the single-run API, one after another
     ms_seq = None
-    if not args.no_sequential:
+    if sequential:
         ctxs = [PopulationAnnealing(sp.L, sp.R, sp.seed, device=dev) for sp in specs]
         torch.cuda.synchronize()
         t0.record(stream)
@@ -463,15 +555,33 @@ def run_batch(args):
         t1.record(stream)
         torch.cuda.synchronize()
         ms_seq = t0.elapsed_time(t1)
-    line = {"metric": METRIC + " (64 mixed runs, batched)", "value": attempts / (ms * 1e6), "unit": UNIT,
-            "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": ms / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "64 independent runs: L in {8..64}, R log-uniform [1e3, 2e5], 51-301 "
-                                   "temperatures, theta in {1, 5, 10}, seeds 100-163", "runs": n},
+        for pa in ctxs:
+            pa.close()
+        del ctxs
+        torch.cuda.empty_cache()
+    return {"value": attempts / (ms * 1e6), "unit": UNIT, "runs": n, "steps": steps,
+            "steps_bounded": steps < total_steps, "batch_ms": ms, "attempts": attempts,
+            "workload": "64 independent runs: L in {8..64}, R log-uniform [1e3, 2e5], 51-301 temperatures, "
+                        "theta in {1, 5, 10}, seeds 100-163"
+                        + (f"; first {steps} temperature steps of every run" if steps < total_steps else ""),
             "sequential_single_run": ({"value": attempts / (ms_seq * 1e6), "unit": UNIT, "ms": ms_seq}
                                       if ms_seq else None),
-            "gain_over_sequential": ms_seq / ms if ms_seq else None, "batch_ms": ms, "tuning": tuning,
+            "gain_over_sequential": ms_seq / ms if ms_seq else None, "tuning": tuning,
             "gpu_launches": 11 * steps}
+
+
+def run_batch(args):
+    """The batched workload alone (--workload batch)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    r = batch_eval(dev, args.batch_steps, not args.no_sequential)
+    line = {"metric": METRIC + " (64 mixed runs, batched)", "value": r["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": r["steps"], "warmup": 0, "ms_per_step": r["batch_ms"] / r["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": r["workload"], "runs": r["runs"]},
+            "sequential_single_run": r["sequential_single_run"], "gain_over_sequential": r["gain_over_sequential"],
+            "batch_ms": r["batch_ms"], "tuning": r["tuning"], "gpu_launches": r["gpu_launches"]}
     print(json.dumps(line), flush=True)
 
 

@@ -189,16 +189,22 @@ def anneal(pa: PopulationAnnealing, mode: str = "plain", model: ScheduleMLP | No
     check included).
 
     plain:   overlap bisection (alpha_target) and theta0 sweeps per temperature.
+    rule:    overlap bisection (alpha_target) for dbeta and the decorrelation rule without the
+             network for theta: one sweep at a time until the replicas' energy levels have
+             decorrelated from their values after resampling (corr <= corr_target) or theta_max
+             sweeps have run -- the rule that labels the network's training data.
     learned: the network proposes (dbeta, theta); dbeta is kept if the overlap reaches
              alpha_floor (else the bisection decides and theta0 sweeps are used); after the
              proposed sweeps the decorrelation since resampling is measured and, while it is
              above corr_target, more sweeps run (half as many again each time, up to theta_max).
     """
+    if mode not in ("plain", "rule", "learned"):
+        raise ValueError(f"unknown schedule mode {mode!r}")
     torch.cuda.synchronize(pa.device)
     t0 = time.perf_counter()
     beta, steps, sweeps, fallbacks, extended = 0.0, 0, 0, 0, 0
     while beta < beta_final:
-        if mode == "plain":
+        if mode in ("plain", "rule"):
             b, _ = pa.propose_schedule(alpha_target, dbeta_max, beta_final)
             theta = theta0
         else:
@@ -206,8 +212,16 @@ def anneal(pa: PopulationAnnealing, mode: str = "plain", model: ScheduleMLP | No
             b, theta = p["beta_next"], p["theta_next"]
             fallbacks += p["source"] == _lib.PA_SCHED_FALLBACK
         pa.resample(b)
-        pa.anneal_step(theta)
-        if mode != "plain":
+        if mode == "rule":
+            theta = 0
+            while theta < theta_max:
+                pa.anneal_step(1)
+                theta += 1
+                if pa.decorrelation() <= corr_target:
+                    break
+        else:
+            pa.anneal_step(theta)
+        if mode == "learned":
             while theta < theta_max and pa.decorrelation() > corr_target:
                 more = min(max(1, theta // 2), theta_max - theta)
                 pa.anneal_step(more)
