@@ -350,6 +350,69 @@ pa_status pa_copy_counts(pa_ctx *ctx, int *host_out, long long *count_out);
 pa_status pa_hashes(pa_ctx *ctx, unsigned long long *host_out);
 pa_status pa_export_spins(pa_ctx *ctx, long long first, long long count, unsigned int *host_out);
 
+/* ---------------------------------------------------------------------------------------
+   One population split over several shards (devices or processes) by contiguous ranges of
+   replica slots (Sec. II: the population is one set of R_i replicas with one normalisation
+   per step, Eqs. Q and taus).  Every random number is keyed by the global slot, so the split
+   does not change any result: hashes, histograms, copy numbers, family ids and observables
+   are those of the same population held whole.  The caller moves data between shards; per
+   temperature step each shard calls, in order:
+     pa_anneal_step            theta sweeps of its own replicas and their measurement;
+     pa_shard_summary          its level histogram, exact sums and family edges (device int64
+                               [pa_shard_summary_len(L)]);
+     (exchange)                every shard obtains all shards' summaries in slot order (an
+                               all-gather);
+     pa_shard_combine          the whole population's histogram, sums and family statistics,
+                               identical on every shard (exact integer arithmetic);
+     pa_observables/pa_record  step 4 of the whole population (optional);
+     pa_resample               Eq. Q and Eq. taus from the whole histogram; copy numbers of its
+                               own parents (keyed by their global index) and their offsets in
+                               tree order; the children are not yet stored;
+     pa_shard_layout           the number of its children c_s (synchronising);
+     (exchange)                an all-gather of the c_s; their exclusive scan o_s gives the
+                               children of shard s the global slots [o_s, o_s + c_s); the new
+                               population is re-split into contiguous ranges of (nearly) equal
+                               size [lo_t, hi_t);
+     pa_shard_copy             for each range that its children meet, the children
+                               [first, first + count) (local child indices) written to the given
+                               arrays: the non-current buffers of the owning shard at index
+                               (o_s + first - lo_t), directly when both are on one device, or a
+                               staging area that the caller sends there;
+     pa_shard_adopt            once every range of this shard has arrived in its non-current
+                               buffers: the new local size hi_t - lo_t and slot base lo_t; the
+                               non-current buffers become current.
+   Nearest-integer and Poisson resampling (multinomial draws need every parent's weight); the
+   schedule, feature, analysis and checkpoint calls need a whole population and return
+   PA_ERR_STATE on a shard, as do the calls above out of order.  A shard's buffers hold its
+   parents and its share of the next population, never all of its children, so its capacity
+   only needs to cover its share (about R / P plus the population's fluctuation).
+
+   pa_shard_init: cfg->R is the whole population's target size, cfg->capacity this shard's
+   buffer capacity (buffers sized by pa_query_sizes for a config with R = capacity); the
+   shard starts with replicas [slot_base, slot_base + R_local) of the simple-sampling
+   population of step 1 (family id = global slot).  PA_ERR_INVALID_ARG unless
+   0 <= slot_base, 1 <= R_local <= capacity and slot_base + R_local <= R.
+   pa_shard_summary_len: int64 entries of one summary, N + 1 + 16 (0 for an unsupported L).
+   pa_shard_summary: asynchronous; dev_out 8-byte aligned device memory.
+   pa_shard_combine: dev_all = n_shards summaries back to back in slot order (device);
+   asynchronous; an inconsistent set (histogram total != replicas, or none) sets the sticky
+   error PA_ERR_NUMERIC.
+   pa_shard_copy: asynchronous; spins_dst 16-byte aligned (count replicas of
+   pa_sizes.bytes_per_replica bytes), level/mag/fam_dst int32[count]; children outside
+   [0, c_s) are not written.
+   pa_shard_adopt: asynchronous; 0 <= R_local <= capacity.
+   pa_shard_layout: which buffer index (0/1) is current, the local size (after pa_resample:
+   the number of children c_s) and slot base (synchronising). */
+pa_status pa_shard_init(const pa_config *cfg, long long slot_base, long long R_local, const pa_buffers *buf,
+                        void *stream, pa_ctx **out);
+long long pa_shard_summary_len(int L);
+pa_status pa_shard_summary(pa_ctx *ctx, long long *dev_out);
+pa_status pa_shard_combine(pa_ctx *ctx, const long long *dev_all, int n_shards);
+pa_status pa_shard_copy(pa_ctx *ctx, long long first, long long count, void *spins_dst, int *level_dst, int *mag_dst,
+                        int *fam_dst);
+pa_status pa_shard_adopt(pa_ctx *ctx, long long R_local, long long slot_base);
+pa_status pa_shard_layout(pa_ctx *ctx, int *cur, long long *R_local, long long *slot_base);
+
 /* Copy numbers of one resampling step WITHOUT a workspace (the paper has no counterpart: this
    is a deployment variant of the level-table / copy-number / prefix-sum kernels of
    pa_resample, not a step of the method).

@@ -97,6 +97,14 @@ def lib():
                                                        i32p, ctypes.c_double, ctypes.c_double,
                                                        ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                                        ctypes.c_int64, i32p, P(_Info)]),
+                "orc_resample_shard": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_int64,
+                                                      ctypes.c_int64, i32p, ctypes.c_int64, ctypes.c_double,
+                                                      ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64,
+                                                      ctypes.c_int, i32p, P(_Info)]),
+                "orc_observables_from_sums": (None, [ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_double,
+                                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_double, ctypes.c_uint32, ctypes.c_int, dp]),
+                "orc_population_sums": (None, [ctypes.c_int64, i32p, i32p, i32p, i64p]),
                 "orc_pa_create": (vp, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_uint64, ctypes.c_int]),
                 "orc_pa_destroy": (None, [vp]),
@@ -233,6 +241,40 @@ def resample_levels(L, R_target, levels, beta_prev, beta_new, step, seed, kind, 
                                    float(beta_prev), float(beta_new), step, seed, kind,
                                    capacity, _ptr(counts, ctypes.c_int32), ctypes.byref(info))
     return st, counts, info.lnQ, info.S, info.kmin, info.R_new
+
+
+def resample_shard(L, R_target, hist, R_prev, levels, parent_base, beta_prev, beta_new, step, seed, kind):
+    """Step 2 for the parents of one shard of a population split by slot ranges: tables from
+    the whole population's histogram `hist` (R_prev parents), copy numbers of the local parents
+    keyed by their global index parent_base + j.  Returns (status, counts, lnQ, R_new_local)."""
+    h = np.ascontiguousarray(hist, dtype=np.int64)
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    counts = np.zeros(len(lv), dtype=np.int32)
+    info = _Info()
+    st = lib().orc_resample_shard(L, R_target, _ptr(h, ctypes.c_int64), R_prev, len(lv), _ptr(lv, ctypes.c_int32),
+                                  parent_base, float(beta_prev), float(beta_new), step, seed, kind,
+                                  _ptr(counts, ctypes.c_int32), ctypes.byref(info))
+    return st, counts, info.lnQ, info.R_new
+
+
+def population_sums(E, M, fam) -> np.ndarray:
+    """Exact integer sums of a population in slot order: sum E, E^2, |M|, M^2, families f,
+    sum of family size^2."""
+    E, M, F = (np.ascontiguousarray(a, np.int32) for a in (E, M, fam))
+    out = np.zeros(6, np.int64)
+    lib().orc_population_sums(len(E), _ptr(E, ctypes.c_int32), _ptr(M, ctypes.c_int32), _ptr(F, ctypes.c_int32),
+                              _ptr(out, ctypes.c_int64))
+    return out
+
+
+def observables_from_sums(N, R, isums, beta, dbeta, lnQ, sum_lnQ, sum_lnR, step, theta) -> dict:
+    """Step 4 (Sec. III, Sec. VII) of a population of R replicas from its exact integer sums
+    (population_sums order)."""
+    s = np.ascontiguousarray(isums, np.int64)
+    out = np.zeros(15)
+    lib().orc_observables_from_sums(int(N), int(R), _ptr(s, ctypes.c_int64), float(beta), float(dbeta), float(lnQ),
+                                    float(sum_lnQ), float(sum_lnR), int(step), int(theta), _ptr(out, ctypes.c_double))
+    return dict(zip(OBS_FIELDS, out.tolist()))
 
 
 # ----------------------------------------------------------------------------- schedule

@@ -380,23 +380,17 @@ typedef struct {
     int64_t R_new;     /* new population size */
 } orc_resample_info;
 
-/* Status codes shared in meaning (not in code) with the library: 0 ok, 3 capacity,
-   6 numeric (empty population). */
-int orc_resample_levels(int L, int64_t R_target, int64_t R_prev, const int32_t *level,
-                        double beta_prev, double beta_new, uint32_t step, uint64_t seed,
-                        int kind, int64_t capacity, int32_t *counts_out,
-                        orc_resample_info *info)
+/* Step 2's tables from the level histogram h of the R_prev parents (Eqs. Q and taus):
+   E_ref = the lowest occupied level's energy, w_k = exp(-dbeta (E_k - E_ref)) for occupied k,
+   S = sum over occupied k, ascending, of h_k w_k, ln Q_i = -dbeta E_ref + ln(S / R_prev),
+   tau_k = R_target w_k / S, fl_k = floor(tau_k), thr_k = floor((tau_k - fl_k) 2^32).
+   Returns 6 (numeric) for an empty histogram, else 0. */
+static int resample_tables(int N, int64_t R_target, const int64_t *h, int64_t R_prev, double dbeta,
+                           double *w, double *tau, int64_t *fl, uint64_t *thr, orc_resample_info *info)
 {
-    int N = L * L;
-    int64_t *h = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
-    double *w = (double *)calloc((size_t)N + 1, sizeof(double));
-    double *tau = (double *)calloc((size_t)N + 1, sizeof(double));
-    int64_t *fl = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
-    uint64_t *thr = (uint64_t *)calloc((size_t)N + 1, sizeof(uint64_t));
-    for (int64_t j = 0; j < R_prev; ++j) h[level[j]] += 1;
     int kmin = 0;
     while (kmin <= N && h[kmin] == 0) ++kmin;
-    double dbeta = beta_new - beta_prev;
+    if (kmin > N) return 6;
     int Eref = 4 * kmin - 2 * N;
     for (int k = 0; k <= N; ++k) {
         if (h[k] == 0) continue;
@@ -413,6 +407,43 @@ int orc_resample_levels(int L, int64_t R_target, int64_t R_prev, const int32_t *
         double f = floor(tau[k]);
         fl[k] = (int64_t)f;
         thr[k] = (uint64_t)floor((tau[k] - f) * 4294967296.0);
+    }
+    info->lnQ = lnQ;
+    info->S = S;
+    info->kmin = kmin;
+    return 0;
+}
+
+/* Copy number of parent j (global index) at level k (Eq. resampling-factors for nearest
+   integer, kind 0; a Poisson draw of mean tau_k, kind 1). */
+static int64_t copy_number(int kind, int64_t fl, uint64_t thr, double tau, uint64_t seed, uint32_t j,
+                           uint32_t step)
+{
+    if (kind == 0) {
+        uint32_t x = philox_word(seed, j, 0, (uint32_t)STREAM_RESAMPLE << 28, step, 0);
+        return fl + (((uint64_t)x <= thr) ? 1 : 0);
+    }
+    return orc_poisson(tau, seed, j, step);
+}
+
+/* Status codes shared in meaning (not in code) with the library: 0 ok, 3 capacity,
+   6 numeric (empty population). */
+int orc_resample_levels(int L, int64_t R_target, int64_t R_prev, const int32_t *level,
+                        double beta_prev, double beta_new, uint32_t step, uint64_t seed,
+                        int kind, int64_t capacity, int32_t *counts_out,
+                        orc_resample_info *info)
+{
+    int N = L * L;
+    int64_t *h = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    double *w = (double *)calloc((size_t)N + 1, sizeof(double));
+    double *tau = (double *)calloc((size_t)N + 1, sizeof(double));
+    int64_t *fl = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    uint64_t *thr = (uint64_t *)calloc((size_t)N + 1, sizeof(uint64_t));
+    for (int64_t j = 0; j < R_prev; ++j) h[level[j]] += 1;
+    double dbeta = beta_new - beta_prev;
+    if (resample_tables(N, R_target, h, R_prev, dbeta, w, tau, fl, thr, info) != 0) {
+        free(h); free(w); free(tau); free(fl); free(thr);
+        return 6;
     }
     int64_t R_new = 0;
     if (kind == 2) {
@@ -449,24 +480,45 @@ int orc_resample_levels(int L, int64_t R_target, int64_t R_prev, const int32_t *
     }
     for (int64_t j = 0; kind != 2 && j < R_prev; ++j) {
         int k = level[j];
-        int64_t r;
-        if (kind == 0) {
-            uint32_t x = philox_word(seed, (uint32_t)j, 0, (uint32_t)STREAM_RESAMPLE << 28, step, 0);
-            r = fl[k] + (((uint64_t)x <= thr[k]) ? 1 : 0);
-        } else {
-            r = orc_poisson(tau[k], seed, (uint32_t)j, step);
-        }
+        int64_t r = copy_number(kind, fl[k], thr[k], tau[k], seed, (uint32_t)j, step);
         counts_out[j] = (int32_t)r;
         R_new += r;
     }
-    info->lnQ = lnQ;
-    info->S = S;
-    info->kmin = kmin;
     info->R_new = R_new;
     free(h); free(w); free(tau); free(fl); free(thr);
     if (R_new > capacity) return 3;
     if (R_new == 0) return 6;
     return 0;
+}
+
+/* Copy numbers of the n parents of one shard of a population split by contiguous slot
+   ranges (a population too large for one device): h is the level histogram of the whole
+   population of R_prev parents, so the tables (and ln Q_i) are those of the whole
+   population, and local parent j has the global index parent_base + j, which keys its
+   random numbers.  Every shard thus draws the numbers one unsplit population would draw.
+   Nearest-integer (kind 0) and Poisson (kind 1) only: multinomial draws need all parents'
+   weights.  info->R_new = this shard's children; 6 for an empty histogram, 1 for kind 2. */
+int orc_resample_shard(int L, int64_t R_target, const int64_t *h, int64_t R_prev, int64_t n,
+                       const int32_t *level, int64_t parent_base, double beta_prev, double beta_new,
+                       uint32_t step, uint64_t seed, int kind, int32_t *counts_out, orc_resample_info *info)
+{
+    if (kind != 0 && kind != 1) return 1;
+    int N = L * L;
+    double *w = (double *)calloc((size_t)N + 1, sizeof(double));
+    double *tau = (double *)calloc((size_t)N + 1, sizeof(double));
+    int64_t *fl = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    uint64_t *thr = (uint64_t *)calloc((size_t)N + 1, sizeof(uint64_t));
+    int st = resample_tables(N, R_target, h, R_prev, beta_new - beta_prev, w, tau, fl, thr, info);
+    int64_t R_new = 0;
+    for (int64_t j = 0; st == 0 && j < n; ++j) {
+        int k = level[j];
+        int64_t r = copy_number(kind, fl[k], thr[k], tau[k], seed, (uint32_t)(parent_base + j), step);
+        counts_out[j] = (int32_t)r;
+        R_new += r;
+    }
+    info->R_new = R_new;
+    free(w); free(tau); free(fl); free(thr);
+    return st;
 }
 
 /* ------------------------------------------------------------------------------------
@@ -598,25 +650,48 @@ void orc_pa_sweep(orc_pa *p, int theta)
     measure_all(p);
 }
 
-/* Step 4: population averages (Sec. III) and the free energy (Sec. VII), all from exact
-   integer sums; formula order fixed.
+/* Step 4: population averages (Sec. III) and the free energy (Sec. VII) of a population of
+   R replicas, from its exact integer sums; formula order fixed.
+   isums[0] sum E, [1] sum E^2, [2] sum |M|, [3] sum M^2, [4] families f, [5] sum size^2.
    out[0] beta, [1] dbeta, [2] R_i, [3] e, [4] C, [5] m, [6] m2, [7] chi, [8] lnQ,
    [9] -beta F, [10] families f, [11] rho_t, [12] step, [13] theta,
-   [14] sum_k ln(R_{k-1} / R) (the population-size factor of Eq. modified-weights2).
-   isums[0] sum E, [1] sum E^2, [2] sum |M|, [3] sum M^2, [4] f, [5] sum size^2. */
-void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
+   [14] sum_k ln(R_{k-1} / R) (the population-size factor of Eq. modified-weights2). */
+void orc_observables_from_sums(int N, int64_t R, const int64_t *isums, double beta, double dbeta,
+                               double lnQ, double sum_lnQ, double sum_lnR, uint32_t step, int theta,
+                               double *out)
+{
+    double Rd = (double)R, Nd = (double)N, b = beta;
+    double meanE = (double)isums[0] / Rd;
+    double meanE2 = (double)isums[1] / Rd;
+    double e = meanE / Nd;
+    double C = ((b * b) * (meanE2 - meanE * meanE)) / Nd;
+    double m = ((double)isums[2] / Rd) / Nd;
+    double m2 = ((double)isums[3] / Rd) / (Nd * Nd);
+    double chi = (b * Nd) * (m2 - m * m);
+    double rho_t = (double)isums[5] / Rd;
+    double mbF = Nd * 0.6931471805599453094 + sum_lnQ;
+    out[0] = beta; out[1] = dbeta; out[2] = Rd; out[3] = e; out[4] = C;
+    out[5] = m; out[6] = m2; out[7] = chi; out[8] = lnQ; out[9] = mbF;
+    out[10] = (double)isums[4]; out[11] = rho_t; out[12] = (double)step;
+    out[13] = (double)theta;
+    out[14] = sum_lnR;
+}
+
+/* The exact integer sums of the current population (isums as above): energies and
+   magnetisations summed over replicas; families (Sec. V) are the runs of equal ids, which
+   stay sorted in tree order. */
+void orc_population_sums(int64_t R, const int32_t *E, const int32_t *M, const int32_t *fam, int64_t *isums)
 {
     int64_t sE = 0, sE2 = 0, sAM = 0, sM2 = 0;
-    for (int64_t j = 0; j < p->R; ++j) {
-        int64_t e = p->E[j], m = p->M[j];
+    for (int64_t j = 0; j < R; ++j) {
+        int64_t e = E[j], m = M[j];
         sE += e; sE2 += e * e;
         sAM += (m < 0 ? -m : m);
         sM2 += m * m;
     }
-    /* families (Sec. V): sizes of runs of equal ids; ids stay sorted in tree order */
     int64_t f = 0, s2 = 0, run = 0;
-    for (int64_t j = 0; j < p->R; ++j) {
-        if (j == 0 || p->fam[j] != p->fam[j - 1]) {
+    for (int64_t j = 0; j < R; ++j) {
+        if (j == 0 || fam[j] != fam[j - 1]) {
             if (run) s2 += run * run;
             run = 0;
             ++f;
@@ -624,25 +699,16 @@ void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
         ++run;
     }
     if (run) s2 += run * run;
-    double Rd = (double)p->R, Nd = (double)p->N, b = p->beta;
-    double meanE = (double)sE / Rd;
-    double meanE2 = (double)sE2 / Rd;
-    double e = meanE / Nd;
-    double C = ((b * b) * (meanE2 - meanE * meanE)) / Nd;
-    double m = ((double)sAM / Rd) / Nd;
-    double m2 = ((double)sM2 / Rd) / (Nd * Nd);
-    double chi = (b * Nd) * (m2 - m * m);
-    double rho_t = (double)s2 / Rd;
-    double mbF = Nd * 0.6931471805599453094 + p->sum_lnQ;
-    out[0] = p->beta; out[1] = p->dbeta; out[2] = Rd; out[3] = e; out[4] = C;
-    out[5] = m; out[6] = m2; out[7] = chi; out[8] = p->lnQ; out[9] = mbF;
-    out[10] = (double)f; out[11] = rho_t; out[12] = (double)p->step;
-    out[13] = (double)p->theta_last;
-    out[14] = p->sum_lnR;
-    if (isums) {
-        isums[0] = sE; isums[1] = sE2; isums[2] = sAM; isums[3] = sM2; isums[4] = f;
-        isums[5] = s2;
-    }
+    isums[0] = sE; isums[1] = sE2; isums[2] = sAM; isums[3] = sM2; isums[4] = f; isums[5] = s2;
+}
+
+void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
+{
+    int64_t sums[6];
+    orc_population_sums(p->R, p->E, p->M, p->fam, sums);
+    orc_observables_from_sums(p->N, p->R, sums, p->beta, p->dbeta, p->lnQ, p->sum_lnQ, p->sum_lnR, p->step,
+                              p->theta_last, out);
+    if (isums) memcpy(isums, sums, sizeof(sums));
 }
 
 /* ------------------------------------------------------------------------------------

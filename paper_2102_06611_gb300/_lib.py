@@ -142,6 +142,14 @@ SIGNATURES = {
                                               ctypes.c_double, ctypes.c_double, ctypes.c_uint,
                                               ctypes.c_ulonglong, ctypes.c_int, _vp, _P(ctypes.c_double),
                                               _P(ctypes.c_longlong), _vp]),
+    "pa_shard_init": (ctypes.c_int, [_P(pa_config), ctypes.c_longlong, ctypes.c_longlong, _P(pa_buffers), _vp,
+                                     _P(_vp)]),
+    "pa_shard_summary_len": (ctypes.c_longlong, [ctypes.c_int]),
+    "pa_shard_summary": (ctypes.c_int, [_vp, _vp]),
+    "pa_shard_combine": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "pa_shard_copy": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_longlong, _vp, _vp, _vp, _vp]),
+    "pa_shard_adopt": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_longlong]),
+    "pa_shard_layout": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_longlong), _P(ctypes.c_longlong)]),
     "pa_last_error": (ctypes.c_char_p, [_vp]),
     "pa_destroy": (None, [_vp]),
 }

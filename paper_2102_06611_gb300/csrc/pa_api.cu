@@ -33,6 +33,11 @@ struct pa_ctx {
     int prop_source;
     int failed;            // sticky host-side status
     char err[256];
+    // one shard of a population split by contiguous slot ranges (pa_shard_*)
+    bool shard;
+    long long slot_base;   // global slot of local replica 0
+    bool combined;         // the histogram and sums are the whole population's (pa_shard_combine)
+    bool adopt_pending;    // resampled; the rebalanced population is not yet adopted
 };
 
 namespace {
@@ -84,6 +89,14 @@ pa_status check_live(pa_ctx *c)
 {
     if (!c) return PA_ERR_INVALID_ARG;
     if (c->failed) return (pa_status)c->failed;
+    return PA_OK;
+}
+
+// Calls that need the whole population in one context (schedules, features, analysis,
+// checkpoints) are refused on a shard.
+pa_status whole_only(pa_ctx *c, const char *what)
+{
+    if (c->shard) return fail(c, PA_ERR_STATE, "%s needs the whole population in one context, not a shard", what);
     return PA_OK;
 }
 
@@ -172,12 +185,16 @@ pa_status pa_query_sizes(const pa_config *cfg, pa_sizes *out)
     return PA_OK;
 }
 
-pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_ctx **out)
+}  // extern "C"
+
+namespace {
+
+// Context creation and step 1 (simple sampling at beta_0 = 0) for R_local replicas with
+// global slots [slot_base, slot_base + R_local); a whole population has slot_base = 0 and
+// R_local = cfg->R.
+pa_status create_ctx(const pa_config *cfg, const pa_buffers *buf, void *stream, long long slot_base,
+                     long long R_local, bool shard, pa_ctx **out)
 {
-    if (!out) return PA_ERR_INVALID_ARG;
-    *out = nullptr;
-    pa_sizes sz;
-    if (!cfg || !buf || pa_query_sizes(cfg, &sz) != PA_OK) return PA_ERR_INVALID_ARG;
     for (int b = 0; b < 2; ++b)
         if (!aligned256(buf->spins[b]) || !aligned256(buf->level[b]) || !aligned256(buf->mag[b]) ||
             !aligned256(buf->fam[b]))
@@ -200,13 +217,16 @@ pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_
     c->sweeps_in_step = 0;
     c->measured = true;
     c->prop_valid = false;
+    c->shard = shard;
+    c->slot_base = slot_base;
+    c->combined = false;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {
         delete c;
         return PA_ERR_CUDA;
     }
-    e = pa::launch_setup(c->st, cfg->R, at<int>(c, c->ws.hist), c->N, cfg->update, c->stream);
+    e = pa::launch_setup(c->st, R_local, at<int>(c, c->ws.hist), c->N, cfg->update, c->stream);
     if (e == cudaSuccess) {
         pa::SweepArgs a{};
         a.spins = buf->spins[0];
@@ -215,13 +235,14 @@ pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_
         a.fam = cur_fam(c);
         a.hist = at<int>(c, c->ws.hist);
         a.st = c->st;
-        a.R_init = cfg->R;
-        a.R_bound = cfg->R;
+        a.R_init = R_local;
+        a.R_bound = R_local;
         a.k0 = (unsigned int)(cfg->seed & 0xffffffffu);
         a.k1 = (unsigned int)(cfg->seed >> 32);
         a.step = 0;
         a.t0 = 0;
         a.theta = 0;
+        a.slot_base = (unsigned int)slot_base;
         host_thresholds(cfg->update, 0.0, &a.T4, &a.T8);
         e = pa::launch_sweep(cfg->L, true, a, c->num_sms, c->stream);
     }
@@ -233,15 +254,49 @@ pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_
     return PA_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_ctx **out)
+{
+    if (!out) return PA_ERR_INVALID_ARG;
+    *out = nullptr;
+    pa_sizes sz;
+    if (!cfg || !buf || pa_query_sizes(cfg, &sz) != PA_OK) return PA_ERR_INVALID_ARG;
+    return create_ctx(cfg, buf, stream, 0, cfg->R, false, out);
+}
+
+pa_status pa_shard_init(const pa_config *cfg, long long slot_base, long long R_local, const pa_buffers *buf,
+                        void *stream, pa_ctx **out)
+{
+    if (!out) return PA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg || !buf) return PA_ERR_INVALID_ARG;
+    // the buffers hold `capacity` replicas of this shard; cfg->R is the whole population's target
+    pa_config local = *cfg;
+    local.R = local.capacity;
+    pa_sizes sz;
+    if (pa_query_sizes(&local, &sz) != PA_OK || cfg->R < 1 || cfg->R > 2147483647LL) return PA_ERR_INVALID_ARG;
+    if (cfg->resample != PA_RESAMPLE_NEAREST && cfg->resample != PA_RESAMPLE_POISSON) return PA_ERR_INVALID_ARG;
+    if (slot_base < 0 || R_local < 1 || R_local > cfg->capacity || slot_base + R_local > cfg->R)
+        return PA_ERR_INVALID_ARG;
+    return create_ctx(cfg, buf, stream, slot_base, R_local, true, out);
+}
+
 pa_status pa_resample(pa_ctx *c, double beta_new)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
     if (!std::isfinite(beta_new) || beta_new < c->beta)
         return fail(c, PA_ERR_STATE, "beta_new %.17g must be finite and >= current beta %.17g", beta_new, c->beta);
+    if (c->shard && (!c->combined || c->adopt_pending))
+        return fail(c, PA_ERR_STATE, "a shard resamples after pa_shard_combine of the current measurement");
     DeviceGuard g(c->device);
     const int nxt = c->cur ^ 1;
     pa::ResampleArgs a{};
+    a.sharded = c->shard ? 1 : 0;
+    a.parent_base = (unsigned int)c->slot_base;
     a.L = c->cfg.L;
     a.kind = c->cfg.resample;
     a.R_target = c->cfg.R;
@@ -270,9 +325,11 @@ pa_status pa_resample(pa_ctx *c, double beta_new)
     a.level_dst = static_cast<int *>(c->buf.level[nxt]);
     a.mag_dst = static_cast<int *>(c->buf.mag[nxt]);
     a.fam_dst = static_cast<int *>(c->buf.fam[nxt]);
-    cudaError_t e = pa::launch_resample(a, c->stream);
+    // a shard only draws its parents' copy numbers here: its children are copied by
+    // pa_shard_copy into the shards that own their global slots
+    cudaError_t e = c->shard ? pa::launch_copy_numbers(a, c->stream) : pa::launch_resample(a, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "resample launch");
-    c->cur = nxt;
+    if (!c->shard) c->cur = nxt;
     c->step += 1;
     c->dbeta = beta_new - c->beta;
     pa_sched_entry rec{};
@@ -288,6 +345,8 @@ pa_status pa_resample(pa_ctx *c, double beta_new)
     c->beta = beta_new;
     c->sweeps_in_step = 0;
     c->measured = false;
+    c->combined = false;
+    c->adopt_pending = c->shard;
     return PA_OK;
 }
 
@@ -313,10 +372,12 @@ static pa_status sweep_and_measure(pa_ctx *c, int theta)
     a.t0 = c->sweeps_in_step;
     a.theta = theta;
     a.update = c->cfg.update;
+    a.slot_base = (unsigned int)c->slot_base;
     host_thresholds(c->cfg.update, c->beta, &a.T4, &a.T8);
     e = pa::launch_sweep(c->cfg.L, false, a, c->num_sms, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->measured = true;
+    c->combined = false;
     return PA_OK;
 }
 
@@ -326,6 +387,7 @@ pa_status pa_anneal_step(pa_ctx *c, int theta)
     if (s != PA_OK) return s;
     if (theta < 0 || (long long)c->sweeps_in_step + theta > (1 << 27))
         return fail(c, PA_ERR_INVALID_ARG, "theta %d out of range", theta);
+    if (c->adopt_pending) return fail(c, PA_ERR_STATE, "a shard adopts its rebalanced population before sweeping");
     DeviceGuard g(c->device);
     if ((s = sweep_and_measure(c, theta)) != PA_OK) return s;
     c->sweeps_in_step += theta;
@@ -339,6 +401,7 @@ pa_status pa_propose_schedule(pa_ctx *c, double alpha_target, double dbeta_max, 
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if ((s = whole_only(c, "the adaptive schedule")) != PA_OK) return s;
     if (!beta_next || !alpha_out || !(alpha_target > 0.0 && alpha_target <= 1.0) || !(dbeta_max > 0.0) ||
         !std::isfinite(dbeta_max) || !std::isfinite(beta_final))
         return fail(c, PA_ERR_INVALID_ARG, "bad schedule parameters");
@@ -378,6 +441,7 @@ pa_status pa_decorrelation(pa_ctx *c, double *corr_out, long long *sums_out)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if ((s = whole_only(c, "the decorrelation measure")) != PA_OK) return s;
     if (!corr_out) return PA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
@@ -429,6 +493,7 @@ pa_status pa_features(pa_ctx *c, int theta0, float *host_out)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if ((s = whole_only(c, "the schedule features")) != PA_OK) return s;
     if (!host_out || theta0 < 1) return fail(c, PA_ERR_INVALID_ARG, "bad feature arguments");
     DeviceGuard g(c->device);
     if ((s = launch_feature_pass(c, theta0, nullptr)) != PA_OK) return s;
@@ -442,6 +507,7 @@ pa_status pa_propose_learned(pa_ctx *c, const pa_learned_model *model, double al
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if ((s = whole_only(c, "the learned schedule")) != PA_OK) return s;
     if (!model || !model->params_bf16 || !model->norm || !out || theta0 < 1 || theta_max < 1 ||
         !(alpha_floor > 0.0 && alpha_floor <= 1.0) || !(alpha_target > 0.0 && alpha_target <= 1.0) ||
         !(dbeta_max > 0.0) || !std::isfinite(dbeta_max) || !std::isfinite(beta_final))
@@ -504,9 +570,12 @@ pa_status pa_record(pa_ctx *c, void *device_dst)
     if (s != PA_OK) return s;
     if (!device_dst || (reinterpret_cast<uintptr_t>(device_dst) & 7u))
         return fail(c, PA_ERR_INVALID_ARG, "record destination must be an 8-byte aligned device pointer");
+    if (c->shard && !(c->measured && c->combined))
+        return fail(c, PA_ERR_STATE, "a shard reports observables after pa_shard_combine of its measurement");
     DeviceGuard g(c->device);
     if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
     pa::ObsArgs a{};
+    a.glob = c->shard ? 1 : 0;
     a.L = c->cfg.L;
     a.R_target = c->cfg.R;
     a.step = c->step;
@@ -549,6 +618,7 @@ pa_status pa_analyze(pa_ctx *c, int n_blocks, pa_analysis *host_out)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if ((s = whole_only(c, "the population analysis")) != PA_OK) return s;
     if (!host_out || n_blocks < 2 || n_blocks > pa::kMaxAnaBlocks)
         return fail(c, PA_ERR_INVALID_ARG, "n_blocks %d outside [2, %d]", n_blocks, pa::kMaxAnaBlocks);
     DeviceGuard g(c->device);
@@ -600,6 +670,7 @@ pa_status pa_replicas(pa_ctx *c, int *level, int *mag, int *fam)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if (c->adopt_pending) return fail(c, PA_ERR_STATE, "the shard's children are not adopted yet");
     DeviceGuard g(c->device);
     const long long R = read_R(c, false, &s);
     if (s != PA_OK) return s;
@@ -629,6 +700,7 @@ pa_status pa_hashes(pa_ctx *c, unsigned long long *host_out)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if (c->adopt_pending) return fail(c, PA_ERR_STATE, "the shard's children are not adopted yet");
     if (!host_out) return PA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     unsigned long long *dev = at<unsigned long long>(c, c->ws.hashes);
@@ -644,6 +716,7 @@ pa_status pa_export_spins(pa_ctx *c, long long first, long long count, unsigned 
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if (c->adopt_pending) return fail(c, PA_ERR_STATE, "the shard's children are not adopted yet");
     if (!host_out || first < 0 || count < 0) return PA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     const long long R = read_R(c, false, &s);
@@ -751,6 +824,7 @@ pa_status pa_checkpoint_size(pa_ctx *c, size_t *bytes)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if ((s = whole_only(c, "a checkpoint")) != PA_OK) return s;
     if (!bytes) return PA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     long long R, Rp;
@@ -763,6 +837,7 @@ pa_status pa_save(pa_ctx *c, void *host_buf, size_t n)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if ((s = whole_only(c, "a checkpoint")) != PA_OK) return s;
     if (!host_buf) return PA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     long long R, Rp;
@@ -809,6 +884,7 @@ pa_status pa_load(pa_ctx *c, const void *host_buf, size_t n)
 {
     pa_status s = check_live(c);
     if (s != PA_OK) return s;
+    if ((s = whole_only(c, "a checkpoint")) != PA_OK) return s;
     if (!host_buf || n < sizeof(CkptHeader)) return PA_ERR_INVALID_ARG;
     CkptHeader h;
     std::memcpy(&h, host_buf, sizeof(h));
@@ -848,6 +924,111 @@ pa_status pa_load(pa_ctx *c, const void *host_buf, size_t n)
     c->theta_last = h.theta_last;
     c->measured = h.measured != 0;
     c->prop_valid = false;
+    return PA_OK;
+}
+
+// ------------------------------------------------------------------------------ shards
+long long pa_shard_summary_len(int L)
+{
+    if (!supported_L(L)) return 0;
+    return (long long)L * L + 1 + pa::kShardExtra;
+}
+
+pa_status pa_shard_summary(pa_ctx *c, long long *dev_out)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!c->shard) return fail(c, PA_ERR_STATE, "pa_shard_summary needs a shard context");
+    if (!dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 7u))
+        return fail(c, PA_ERR_INVALID_ARG, "summary destination must be an 8-byte aligned device pointer");
+    if (c->combined || c->adopt_pending)
+        return fail(c, PA_ERR_STATE, "summarise a shard once after each measurement");
+    DeviceGuard g(c->device);
+    if (!c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
+    cudaError_t e = pa::launch_families(c->st, cur_fam(c), at<long long>(c, c->ws.fampart), c->stream);
+    if (e == cudaSuccess)
+        e = pa::launch_shard_summary(c->st, at<int>(c, c->ws.hist), cur_fam(c), at<long long>(c, c->ws.fampart), c->N,
+                                     dev_out, c->stream);
+    return e == cudaSuccess ? PA_OK : cuda_fail(c, e, "shard summary launch");
+}
+
+pa_status pa_shard_combine(pa_ctx *c, const long long *dev_all, int n_shards)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!c->shard) return fail(c, PA_ERR_STATE, "pa_shard_combine needs a shard context");
+    if (!dev_all || n_shards < 1 || (reinterpret_cast<uintptr_t>(dev_all) & 7u))
+        return fail(c, PA_ERR_INVALID_ARG, "bad shard summaries");
+    if (!c->measured || c->combined) return fail(c, PA_ERR_STATE, "combine once after each measurement");
+    DeviceGuard g(c->device);
+    cudaError_t e = pa::launch_shard_combine(c->st, at<int>(c, c->ws.hist), c->N, dev_all, n_shards, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "shard combine launch");
+    c->combined = true;
+    return PA_OK;
+}
+
+pa_status pa_shard_copy(pa_ctx *c, long long first, long long count, void *spins_dst, int *level_dst, int *mag_dst,
+                        int *fam_dst)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!c->shard) return fail(c, PA_ERR_STATE, "pa_shard_copy needs a shard context");
+    if (!c->adopt_pending) return fail(c, PA_ERR_STATE, "pa_shard_copy follows pa_resample");
+    if (first < 0 || count < 0 || !spins_dst || !level_dst || !mag_dst || !fam_dst ||
+        (reinterpret_cast<uintptr_t>(spins_dst) & 15u) || (reinterpret_cast<uintptr_t>(level_dst) & 3u) ||
+        (reinterpret_cast<uintptr_t>(mag_dst) & 3u) || (reinterpret_cast<uintptr_t>(fam_dst) & 3u))
+        return fail(c, PA_ERR_INVALID_ARG, "bad children window or destination");
+    if (count == 0) return PA_OK;
+    DeviceGuard g(c->device);
+    pa::ResampleArgs a{};
+    a.L = c->cfg.L;
+    a.st = c->st;
+    a.counts = at<int>(c, c->ws.counts);
+    a.blocksum = at<long long>(c, c->ws.blocksum);
+    a.nblk = c->ws.nblk;
+    a.spins_src = c->buf.spins[c->cur];
+    a.level_src = static_cast<const int *>(c->buf.level[c->cur]);
+    a.mag_src = static_cast<const int *>(c->buf.mag[c->cur]);
+    a.fam_src = static_cast<const int *>(c->buf.fam[c->cur]);
+    a.spins_dst = spins_dst;
+    a.level_dst = level_dst;
+    a.mag_dst = mag_dst;
+    a.fam_dst = fam_dst;
+    a.sharded = 1;
+    a.win_lo = first;
+    a.win_n = count;
+    cudaError_t e = pa::launch_copy(a, c->stream);
+    return e == cudaSuccess ? PA_OK : cuda_fail(c, e, "shard copy launch");
+}
+
+pa_status pa_shard_adopt(pa_ctx *c, long long R_local, long long slot_base)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!c->shard) return fail(c, PA_ERR_STATE, "pa_shard_adopt needs a shard context");
+    if (!c->adopt_pending) return fail(c, PA_ERR_STATE, "pa_shard_adopt follows pa_resample");
+    if (R_local < 0 || R_local > c->cfg.capacity || slot_base < 0 || slot_base + R_local > 2147483647LL)
+        return fail(c, PA_ERR_INVALID_ARG, "R_local %lld / slot_base %lld out of range", R_local, slot_base);
+    DeviceGuard g(c->device);
+    cudaError_t e = pa::launch_set_population(c->st, R_local, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "shard adopt launch");
+    c->cur ^= 1;
+    c->slot_base = slot_base;
+    c->adopt_pending = false;
+    return PA_OK;
+}
+
+pa_status pa_shard_layout(pa_ctx *c, int *cur, long long *R_local, long long *slot_base)
+{
+    pa_status s = check_live(c);
+    if (s != PA_OK) return s;
+    if (!cur || !R_local || !slot_base) return PA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    const long long R = read_R(c, false, &s);
+    if (s != PA_OK) return s;
+    *cur = c->cur;
+    *R_local = R;
+    *slot_base = c->slot_base;
     return PA_OK;
 }
 

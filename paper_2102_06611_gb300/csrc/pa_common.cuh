@@ -217,6 +217,7 @@ struct DevState {
     int update;               // pa_update_kind of the run (selects the thresholds below)
     unsigned long long mn_total;  // multinomial resampling: sum of the integer parent weights
     double sum_lnR;           // sum_k ln(R_{k-1} / R) over the resamplings so far
+    long long R_glob;         // sharded population: the whole population's size (0 otherwise)
 };
 
 __device__ __forceinline__ void set_error(DevState *st, int code)

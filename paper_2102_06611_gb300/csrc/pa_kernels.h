@@ -93,6 +93,10 @@ struct SweepArgs {
     // same binary64 arithmetic as DevState::T4 / T8 (k_sweep reads them from its
     // parameters, where they are warp-uniform operands, and checks them against DevState)
     unsigned long long T4, T8;
+    // global slot of local replica 0: a population split over several shards by contiguous slot
+    // ranges keys every random number (and the initial family id) by the global slot (0 for a
+    // population held whole)
+    unsigned int slot_base;
 };
 
 cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s);
@@ -126,10 +130,18 @@ struct ResampleArgs {
     void *spins_dst;
     const int *level_src, *mag_src, *fam_src;
     int *level_dst, *mag_dst, *fam_dst;
+    // sharded population: the histogram is the whole population's (DevState::R_glob parents,
+    // used for ln Q_i) and local parent j has the global index parent_base + j
+    int sharded;
+    unsigned int parent_base;
+    // the replica copy writes only children [win_lo, win_lo + win_n) (local child indices, in
+    // tree order) to destination index child - win_lo; win_n = 0: every child, at its index
+    long long win_lo, win_n;
 };
 
 cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s);
 cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s);
+cudaError_t launch_copy(const ResampleArgs &a, cudaStream_t s);
 cudaError_t launch_thresholds(DevState *st, double beta, cudaStream_t s);
 cudaError_t launch_zero_measure(DevState *st, int *hist, int N, cudaStream_t s);
 cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, int update, cudaStream_t s);
@@ -145,9 +157,18 @@ struct ObsArgs {
     const int *fam;
     long long *fampart;
     pa_obs *dst;
+    int glob;               // sharded population: R, family counts and sums from the combined state
 };
 
 cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s);
+
+// Sharded populations: one shard's summary (level histogram, exact sums, family edges) and
+// the combination of all shards' summaries into the whole population's state.
+constexpr int kShardExtra = 16;  // int64 entries after the N + 1 histogram entries
+cudaError_t launch_shard_summary(const DevState *st, const int *hist, const int *fam, const long long *fampart,
+                                 int N, long long *out, cudaStream_t s);
+cudaError_t launch_shard_combine(DevState *st, int *hist, int N, const long long *all, int n_shards, cudaStream_t s);
+cudaError_t launch_set_population(DevState *st, long long R, cudaStream_t s);
 
 // Weighted average over independent runs' records (pa_analysis.cu).
 cudaError_t launch_weighted(const pa_obs *rec, int M, int mode, pa_weighted *out, cudaStream_t s);

@@ -238,14 +238,15 @@ __device__ __forceinline__ void table_body(const ResampleArgs &a)
         }
     }
     if (tid == 0) {
-        const long long Rp = st->R_cur;
+        // R_{i-1}: the whole population's size (a shard's own parents are st->R_cur)
+        const long long Rp = a.sharded ? st->R_glob : st->R_cur;
         const double lnQ = __dadd_rn(-__dmul_rn(dbeta, (double)Eref), log(__ddiv_rn(S, (double)Rp)));
         st->lnQ = lnQ;
         st->sum_lnQ = __dadd_rn(st->sum_lnQ, lnQ);
         st->sum_lnR = __dadd_rn(st->sum_lnR, log(__ddiv_rn((double)Rp, (double)a.R_target)));
         st->S = S;
         st->kmin = kmin;
-        st->R_prev = Rp;
+        st->R_prev = st->R_cur;
         set_thresholds(st, a.beta_new);
         if (!(S > 0.0) || !isfinite(S)) set_error(st, PA_ERR_NUMERIC);
     }
@@ -294,12 +295,13 @@ __device__ __forceinline__ void counts_body(const ResampleArgs &a)
         const long long j = base + it * kCountThreads + threadIdx.x;
         if (j < Rp) {
             const int k = a.level_src[j];
+            const unsigned int jg = (unsigned int)j + a.parent_base;  // global parent index
             long long r;
             if (a.kind == PA_RESAMPLE_NEAREST) {
-                const uint4 x = philox(make_uint4((unsigned int)j, 0u, kStreamResample << 28, a.step), a.k0, a.k1);
+                const uint4 x = philox(make_uint4(jg, 0u, kStreamResample << 28, a.step), a.k0, a.k1);
                 r = (long long)a.fl[k] + (x.x <= a.thr[k] ? 1 : 0);
             } else {
-                r = poisson_draw(a.tau[k], (unsigned int)j, a.step, a.k0, a.k1);
+                r = poisson_draw(a.tau[k], jg, a.step, a.k0, a.k1);
             }
             if (r > INT_MAX) r = INT_MAX;  // the capacity check rejects this population
             a.counts[j] = (int)r;
@@ -435,7 +437,8 @@ __device__ __forceinline__ void scan_body(const ResampleArgs &a)
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        if (carry > a.capacity) set_error(st, PA_ERR_CAPACITY);
+        if (a.sharded) st->R_cur = carry;  // a shard's children: re-split before they are stored
+        else if (carry > a.capacity) set_error(st, PA_ERR_CAPACITY);
         else if (carry == 0) set_error(st, PA_ERR_NUMERIC);
         else st->R_cur = carry;
     }
@@ -475,6 +478,17 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
     const uint4 *src = reinterpret_cast<const uint4 *>(a.spins_src);
     uint4 *dst = reinterpret_cast<uint4 *>(a.spins_dst);
     const int nloc = (int)min((long long)kCountBlockItems, Rp - base);
+    // children [k_lo, k_hi) of a parent whose children start at index o, written at o + k - shift
+    const bool win = a.win_n > 0;
+    const long long shift = win ? a.win_lo : 0;
+    auto clip = [&](long long o, int cnt, int &k_lo, int &k_hi) {
+        k_lo = 0;
+        k_hi = cnt;
+        if (win) {
+            k_lo = (int)max(0LL, min((long long)cnt, a.win_lo - o));
+            k_hi = (int)max((long long)k_lo, min((long long)cnt, a.win_lo + a.win_n - o));
+        }
+    };
     if (chunks16 >= 32) {
         // a warp per parent
         for (int p = wid; p < nloc; p += kCountThreads / 32) {
@@ -482,15 +496,18 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
             if (cnt == 0) continue;
             const long long j = base + p;
             const long long o = sh_off[p];
+            int k_lo, k_hi;
+            clip(o, cnt, k_lo, k_hi);
+            if (k_lo >= k_hi) continue;
             for (int ch = lane; ch < chunks16; ch += 32) {
                 const uint4 v = src[(size_t)j * chunks16 + ch];
-                for (int k = 0; k < cnt; ++k) dst[(size_t)(o + k) * chunks16 + ch] = v;
+                for (int k = k_lo; k < k_hi; ++k) dst[(size_t)(o + k - shift) * chunks16 + ch] = v;
             }
             const int lv = a.level_src[j], mg = a.mag_src[j], fm = a.fam_src[j];
-            for (int k = lane; k < cnt; k += 32) {
-                a.level_dst[o + k] = lv;
-                a.mag_dst[o + k] = mg;
-                a.fam_dst[o + k] = fm;
+            for (int k = k_lo + lane; k < k_hi; k += 32) {
+                a.level_dst[o + k - shift] = lv;
+                a.mag_dst[o + k - shift] = mg;
+                a.fam_dst[o + k - shift] = fm;
             }
         }
         return;
@@ -507,15 +524,18 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
         if (cnt == 0) continue;
         const long long j = base + p;
         const long long o = sh_off[p];
+        int k_lo, k_hi;
+        clip(o, cnt, k_lo, k_hi);
+        if (k_lo >= k_hi) continue;
         if (li < chunks16) {
             const uint4 v = src[(size_t)j * chunks16 + li];
-            for (int k = 0; k < cnt; ++k) dst[(size_t)(o + k) * chunks16 + li] = v;
+            for (int k = k_lo; k < k_hi; ++k) dst[(size_t)(o + k - shift) * chunks16 + li] = v;
         }
         const int lv = a.level_src[j], mg = a.mag_src[j], fm = a.fam_src[j];
-        for (int k = li; k < cnt; k += S) {
-            a.level_dst[o + k] = lv;
-            a.mag_dst[o + k] = mg;
-            a.fam_dst[o + k] = fm;
+        for (int k = k_lo + li; k < k_hi; k += S) {
+            a.level_dst[o + k - shift] = lv;
+            a.mag_dst[o + k - shift] = mg;
+            a.fam_dst[o + k - shift] = fm;
         }
     }
 }
@@ -558,8 +578,17 @@ cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The replica copy alone (children of the parents in spins_src ... into spins_dst ..., or the
+// window [win_lo, win_lo + win_n) of them), after the copy numbers and their offsets.
+cudaError_t launch_copy(const ResampleArgs &a, cudaStream_t s)
+{
+    const int chunks16 = bytes_per_replica(a.L) / 16;
+    k_copy<<<(unsigned int)a.nblk, kCountThreads, 0, s>>>(a, chunks16);
+    return cudaGetLastError();
+}
+
 // Level table, copy numbers and their total, without the replica copy (used by the
-// no-workspace entry point, whose scratch is a static device array).
+// no-workspace entry point, whose scratch is a static device array, and by shards).
 cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s)
 {
     const int nlev = a.L * a.L + 1;
@@ -634,7 +663,11 @@ __device__ __forceinline__ void obs_body(const ObsArgs &a)
     fc = block_sum<long long, 1024>(fc);
     f2 = block_sum<long long, 1024>(f2);
     if (threadIdx.x != 0) return;
-    const long long R = st->R_cur;
+    if (a.glob) {  // sharded population: the combined whole-population values
+        fc = st->fam_count;
+        f2 = st->fam_size2;
+    }
+    const long long R = a.glob ? st->R_glob : st->R_cur;
     const double Rd = (double)R, Nd = (double)N, b = a.beta;
     const double meanE = __ddiv_rn((double)sE, Rd);
     const double meanE2 = __ddiv_rn((double)sE2, Rd);
@@ -673,9 +706,11 @@ __global__ void __launch_bounds__(1024) k_obs(ObsArgs a) { obs_body(a); }
 
 cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s)
 {
-    k_families<<<kFamBlocks, 256, 0, s>>>(a.st, a.fam, a.fampart);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (!a.glob) {
+        k_families<<<kFamBlocks, 256, 0, s>>>(a.st, a.fam, a.fampart);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     k_obs<<<1, 1024, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -885,8 +885,9 @@ __global__ void __launch_bounds__(PA_SWEEP_THREADS, sweep_min_blocks(L)) k_sweep
         const bool active = j < R;
         W A[RPL], B[RPL];
         W *rep = spins + (size_t)(active ? j : 0) * (2 * L);
+        const unsigned int slot = (unsigned int)j + a.slot_base;  // global replica slot
         if (INIT) {
-            init_rows<L>((unsigned int)j, r0, a.k0, a.k1, A, B);
+            init_rows<L>(slot, r0, a.k0, a.k1, A, B);
         } else {
             if (active) load_rows<L>(rep, r0, A, B);
             else {
@@ -894,7 +895,8 @@ __global__ void __launch_bounds__(PA_SWEEP_THREADS, sweep_min_blocks(L)) k_sweep
                 for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
             }
         }
-        sweep_rows<L, HB>(A, B, r0, lane, (unsigned int)j, (unsigned int)base, a.t0, a.theta, a.step, rk0, rk1, ac, tq);
+        sweep_rows<L, HB>(A, B, r0, lane, slot, (unsigned int)base + a.slot_base, a.t0, a.theta, a.step, rk0, rk1, ac,
+                          tq);
         int anti, ups;
         measure_rows<L>(A, B, r0, lane, anti, ups);
         anti = group_sum<G>(anti);
@@ -921,7 +923,7 @@ __global__ void __launch_bounds__(PA_SWEEP_THREADS, sweep_min_blocks(L)) k_sweep
                 }
                 a.level[j] = level;
                 a.mag[j] = M;
-                if (INIT) a.fam[j] = (int)j;
+                if (INIT) a.fam[j] = (int)slot;
                 v[0] = (unsigned long long)(M < 0 ? -M : M);
                 v[1] = (unsigned long long)((long long)M * M);
             }

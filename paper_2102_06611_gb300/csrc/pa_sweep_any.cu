@@ -344,9 +344,10 @@ __global__ void __launch_bounds__(32 * kAnyWarps) k_sweep_any(SweepArgs a, int L
     for (long long base = warp * g.k; base < R; base += nwarps * g.k) {
         const long long j = base + sub;
         const bool active = j < R;
+        const unsigned int slot = (unsigned int)j + a.slot_base;  // global replica slot
         // the warp's k replicas are consecutive in HBM; slots past R read as zero
         if (INIT) {
-            init_any(S, g, (unsigned int)j, a.k0, a.k1, c0);
+            init_any(S, g, slot, a.k0, a.k1, c0);
         } else if (g.wide) {
             const u64 *src = reinterpret_cast<const u64 *>(a.spins) + (size_t)base * W2;
             for (int w = lane; w < KW; w += 32) Sw[w] = (base + w / W2 < R) ? src[w] : 0ull;
@@ -358,8 +359,8 @@ __global__ void __launch_bounds__(32 * kAnyWarps) k_sweep_any(SweepArgs a, int L
         for (int t = 0; t < a.theta; ++t)
             for (int q = 0; q < 2; ++q) {
                 const unsigned int tag = (unsigned int)(2 * (a.t0 + t) + q);
-                if (g.wide) half_sweep_rows(S, g, q, (unsigned int)j, tag, a.step, a.k0, a.k1, th, c0);
-                else half_sweep_chunks(S, g, q, (unsigned int)j, tag, a.step, a.k0, a.k1, th, c0);
+                if (g.wide) half_sweep_rows(S, g, q, slot, tag, a.step, a.k0, a.k1, th, c0);
+                else half_sweep_chunks(S, g, q, slot, tag, a.step, a.k0, a.k1, th, c0);
                 __syncwarp();
             }
         // measurement: antiparallel bonds (row r: (2p, 2p+1), (2p+1, 2p+2); column: r, r+1)
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(32 * kAnyWarps) k_sweep_any(SweepArgs a, int L
             }
             a.level[j] = level;
             a.mag[j] = M;
-            if (INIT) a.fam[j] = (int)j;
+            if (INIT) a.fam[j] = (int)slot;
             atomicAdd(&sh_hist[level], 1);
             for (int i = 0; i < (INIT ? 2 : 7); ++i) atomicAdd(&sh_sum[i], v[i]);
         }

@@ -264,3 +264,27 @@ def test_anneal_padded_rows_against_exact(L, update):
     e_ex, _, lnZ = oracle.kaufman_thermo(L, 1.0)
     assert abs(o["e"] - e_ex / N) < 0.01
     assert abs(o["minus_betaF"] - lnZ) / N < 5e-3
+
+
+@pytest.mark.parametrize("kind", [oracle.NEAREST, oracle.POISSON])
+def test_resample_shard_equals_whole_population(kind):
+    """Copy numbers drawn shard by shard (tables from the whole histogram, parents keyed by
+    their global index) are those of the whole population (Sec. II), for any split; ln Q_i
+    is the whole population's."""
+    L, R = 8, 4000
+    pa = oracle.PA(L, R, seed=21)
+    pa.init()
+    E, _, _ = pa.state()
+    levels = _levels_energy(L, E).astype(np.int32)
+    hist = np.bincount(levels, minlength=L * L + 1)
+    st, counts, lnQ, _, _, R_new = oracle.resample_levels(L, R, levels, 0.0, 0.35, 1, 21, kind,
+                                                          oracle.default_capacity(R))
+    assert st == 0
+    for cuts in ([0, R], [0, 1234, R], [0, 1, 2, 2999, R], [0, 1000, 1000, 2500, R]):
+        parts, total = [], 0
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            s, c, q, n = oracle.resample_shard(L, R, hist, R, levels[a:b], a, 0.0, 0.35, 1, 21, kind)
+            assert s == 0 and q == lnQ
+            parts.append(c)
+            total += n
+        assert np.array_equal(np.concatenate(parts), counts) and total == R_new
