@@ -62,6 +62,12 @@ def _parse_args():
                    help="skip the bounded 64-run batch figure of the default line")
     p.add_argument("--no-whole-anneal", action="store_true",
                    help="skip the whole-anneal end-to-end figure of the default line")
+    p.add_argument("--parallel", choices=["independent", "shard"], default="independent",
+                   help="N > 1 ranks: independent populations (default) or one population sharded over the "
+                        "ranks by slot ranges")
+    p.add_argument("--shards", type=int, default=1,
+                   help="--parallel shard: shards held by each rank (several shards of one population on one "
+                        "GPU measure the protocol's cost)")
     p.add_argument("--workload", choices=["single", "batch"], default="single",
                    help="single: the L=64, R=1e6 run (default); batch: 64 mixed independent runs")
     p.add_argument("--update", choices=["metropolis", "heatbath"], default="metropolis",
@@ -585,12 +591,99 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sharded(args):
+    """One population of R replicas split over world x --shards shards by contiguous slot ranges
+    (NCCL between ranks, direct copies between shards of one rank); a step is the same
+    temperature step as the default workload, for the whole population."""
+    import ctypes
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2102_06611_gb300 import OBS_BYTES, pa_obs
+    from paper_2102_06611_gb300.shard import DistTransport, LocalTransport, ShardedRun, gpu_shards
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    L, R, theta, k = args.L, args.R, args.theta, max(1, args.shards)
+    N = L * L
+    P = world * k
+    K, W = args.steps, args.warmup
+    assert W + K <= N_TEMPS - 1, "schedule has 300 steps"
+    transport = LocalTransport() if world == 1 else DistTransport(shards_per_rank=k)
+    engines = gpu_shards(L, R, SEED, list(range(rank * k, (rank + 1) * k)), P, device=dev, stream=stream)
+    run = ShardedRun(engines, P, transport)
+    first = engines[rank * k]
+    records = torch.zeros((K, (OBS_BYTES + 7) // 8), dtype=torch.int64, device=dev)
+
+    def beta(i):
+        return i / (N_TEMPS - 1)
+
+    for i in range(1, W + 1):
+        run.resample(beta(i))
+        run.anneal_step(theta)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(K):
+        run.resample(beta(W + 1 + s))
+        run.anneal_step(theta)
+        first.record(records[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    recs = records.cpu().numpy()
+    Rs = []
+    for s in range(K):
+        o = pa_obs.from_buffer_copy(recs[s].tobytes()[: ctypes.sizeof(pa_obs)])
+        assert o.status == 0, f"device error {o.status}"
+        Rs.append(o.R)
+    attempts = float(N) * float(sum(Rs)) * theta  # the whole population's, the same on every rank
+    from paper_2102_06611_gb300.multi import aggregate
+    ms, _, _ = aggregate(ms, 0.0, 0.0, device=dev)
+    if rank == 0:
+        value = attempts / (ms * 1e6)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic (simple sampling at beta=0, Philox4x32-10 seed 7)",
+                "config": {"workload": f"2D Ising PA L={L} R={R} theta={theta} beta=i/300 nearest",
+                           "L": L, "R": R, "theta": theta, "temperatures": N_TEMPS,
+                           "parallelism": f"one population sharded by slot ranges: {P} shards "
+                                          f"({k} per rank, {world} rank(s))",
+                           "beta_timed": [beta(W + 1), beta(W + K)],
+                           "l2": "inputs larger than L2 (%.0f MB of spins per shard)" % (R / P * L * 2 * 4 * 2 / 1e6)},
+                "clocks": clk, "gpu_launches": (KERNELS_PER_STEP + 4) * K * k}
+        print(json.dumps(line), flush=True)
+    for e in engines.values():
+        e.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = _parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.parallel == "shard":
+        run_sharded(args)
     else:
         run_ours(args)
 
