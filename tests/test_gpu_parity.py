@@ -168,19 +168,21 @@ def test_call_order_errors():
 
 
 # ------------------------------------------------------------------------------ full size
-def _replay_steps(L, R, kind, seed, betas, theta, n_sample, update="metropolis"):
+def _replay_steps(L, R, kind, seed, betas, theta, n_sample, update="metropolis", gpu=None, beta_prev=0.0,
+                  first_step=1):
     """Run the device at full size; replay every resampling in full and a sample of the
-    sweeps in the oracle."""
-    gpu = _pa(L, R, seed=seed, resample=kind, update=update)
+    sweeps in the oracle.  With `gpu` given, continue that run (at beta_prev, next step
+    first_step) instead of starting from simple sampling."""
     N = L * L
-    rng = np.random.default_rng(seed)
-    # init: sampled slots against the oracle's init
-    sample = np.unique(np.concatenate([[0, R - 1], rng.integers(0, R, n_sample)]))
-    for j in sample:
-        w = gpu.export_spins(int(j), 1)[0]
-        assert np.array_equal(w.reshape(-1), oracle.pack(L, oracle.init_replica(L, seed, int(j)))), j
-    beta_prev = 0.0
-    for i, beta in enumerate(betas, start=1):
+    rng = np.random.default_rng(seed + first_step)
+    if gpu is None:
+        gpu = _pa(L, R, seed=seed, resample=kind, update=update)
+        # init: sampled slots against the oracle's init
+        sample = np.unique(np.concatenate([[0, R - 1], rng.integers(0, R, n_sample)]))
+        for j in sample:
+            w = gpu.export_spins(int(j), 1)[0]
+            assert np.array_equal(w.reshape(-1), oracle.pack(L, oracle.init_replica(L, seed, int(j)))), j
+    for i, beta in enumerate(betas, start=first_step):
         lv, mg, fm = gpu.replicas()
         R_prev = len(lv)
         h = np.bincount(lv, minlength=N + 1)
@@ -235,6 +237,26 @@ def test_full_size_L64_R1e6_replay():
 
 def test_full_size_L64_R1e6_heatbath_replay():
     _replay_steps(64, 1_000_000, "nearest", seed=7, betas=[0.3, 0.7], theta=10, n_sample=24, update="heatbath")
+
+
+@pytest.mark.parametrize("update", ["metropolis", "heatbath"])
+def test_full_size_L64_R1e6_low_temperature_replay(update):
+    """The headline population at the critical point and deep in the ordered phase, where most
+    sites have all four neighbours aligned and the Metropolis decisions hinge on the rare
+    random numbers below e^{-8 beta} (ties of the top bits are frequent): a short anneal on the
+    headline schedule (theta = 1) reaches beta = 0.44 and 0.9, then two steps each are replayed
+    with 512 sampled slots and the whole resampling."""
+    L, R, seed, theta = 64, 1_000_000, 7, 10
+    gpu = _pa(L, R, seed=seed, update=update)
+    i = 0
+    for target in (132, 270):                       # beta = i / 300: 0.44, 0.9
+        while i < target:
+            i += 1
+            gpu.resample(i / 300)
+            gpu.anneal_step(1)
+        _replay_steps(L, R, "nearest", seed, [(i + 1) / 300, (i + 2) / 300], theta, 512, update=update, gpu=gpu,
+                      beta_prev=i / 300, first_step=i + 1)
+        i += 2
 
 
 def test_full_size_L128_R2e5_replay():
