@@ -716,12 +716,38 @@ void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
  * step that keeps the energy-histogram overlap above about 0.7, Sec. X; the procedure itself
  * is not printed).  Reading: the overlap of the energy distribution at beta, estimated by
  * the population histogram p_k = h_k / R, with the one reweighted to beta + dbeta,
- * q_k = h_k w_k / S (w_k and S as in the resampling step), is
- *     alpha(dbeta) = sum over occupied k, ascending, of min(p_k, q_k);
- * the next step is the largest dbeta in (0, hi], hi = min(dbeta_max, beta_final - beta),
- * with alpha(dbeta) >= alpha_target, found by `iters` bisection steps on [0, hi] after
- * trying hi itself.
+ * q_k = t_k / S, t_k = h_k w_k, w_k = exp(-dbeta (E_k - E_ref)) (E_ref as in the resampling
+ * step), S = sum of the t_k, is
+ *     alpha(dbeta) = sum over occupied k of min(p_k, q_k).
+ * Both sums run over the occupied levels in ascending order, in a fixed pairwise order: the
+ * n terms are cut into 1024 consecutive chunks of c = ceil(n / 1024) terms, each chunk is
+ * summed from its first term, and the 1024 chunk sums are added as a binary tree
+ * (x_i = x_i + x_{i+s} for s = 512, 256, ..., 1; result x_0).
+ * The next step is the largest dbeta in (0, hi], hi = min(dbeta_max, beta_final - beta),
+ * with alpha(dbeta) >= alpha_target: hi itself if it qualifies; else a search keeps a
+ * bracket [lo, hi) with alpha(lo) >= alpha_target (lo = 0 at first) and, ceil(iters / 6)
+ * times, evaluates the K - 1 = 63 points x_m = lo + (hi - lo) (m / 64), takes m* = the
+ * number of leading points that reach the target and narrows the bracket to
+ * [x_{m*}, x_{m*+1}) (x_0 = lo, x_64 = hi).  If no point ever qualifies, the step is the
+ * smallest tried (the final hi).
  * ---------------------------------------------------------------------------------- */
+#define ORC_CHUNKS 1024
+#define ORC_SEARCH_K 64
+
+static double pairwise_sum(const double *x, int n)
+{
+    double part[ORC_CHUNKS];
+    int c = (n + ORC_CHUNKS - 1) / ORC_CHUNKS;
+    for (int j = 0; j < ORC_CHUNKS; ++j) {
+        double s = 0.0;
+        for (int i = j * c; i < (j + 1) * c && i < n; ++i) s = s + x[i];
+        part[j] = s;
+    }
+    for (int s = ORC_CHUNKS / 2; s > 0; s /= 2)
+        for (int j = 0; j < s; ++j) part[j] = part[j] + part[j + s];
+    return part[0];
+}
+
 double orc_overlap(int N, const int64_t *h, double dbeta)
 {
     int kmin = 0;
@@ -730,20 +756,25 @@ double orc_overlap(int N, const int64_t *h, double dbeta)
     int Eref = 4 * kmin - 2 * N;
     int64_t R = 0;
     for (int k = 0; k <= N; ++k) R += h[k];
-    double S = 0.0;
-    for (int k = 0; k <= N; ++k) {
-        if (h[k] == 0) continue;
+    double *t = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    double *m = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    int *occ = (int *)malloc(sizeof(int) * (size_t)(N + 1));
+    int n = 0;
+    for (int k = 0; k <= N; ++k)
+        if (h[k] != 0) occ[n++] = k;
+    for (int i = 0; i < n; ++i) {
+        int k = occ[i];
         double w = orc_exp(-(dbeta * (double)(4 * k - 2 * N - Eref)));
-        S = S + (double)h[k] * w;
+        t[i] = (double)h[k] * w;
     }
-    double alpha = 0.0;
-    for (int k = 0; k <= N; ++k) {
-        if (h[k] == 0) continue;
-        double w = orc_exp(-(dbeta * (double)(4 * k - 2 * N - Eref)));
-        double pk = (double)h[k] / (double)R;
-        double qk = ((double)h[k] * w) / S;
-        alpha = alpha + (pk < qk ? pk : qk);
+    double S = pairwise_sum(t, n);
+    for (int i = 0; i < n; ++i) {
+        double pk = (double)h[occ[i]] / (double)R;
+        double qk = t[i] / S;
+        m[i] = pk < qk ? pk : qk;
     }
+    double alpha = pairwise_sum(m, n);
+    free(t); free(m); free(occ);
     return alpha;
 }
 
@@ -764,15 +795,21 @@ double orc_bisect_next_beta(int N, const int64_t *h, double beta, double beta_fi
         alpha = a_hi;
     } else {
         double lo = 0.0, a_lo = 1.0;
-        for (int it = 0; it < iters; ++it) {
-            double mid = 0.5 * (lo + hi);
-            double a_mid = orc_overlap(N, h, mid);
-            if (a_mid >= alpha_target) {
-                lo = mid;
-                a_lo = a_mid;
-            } else {
-                hi = mid;
+        const int rounds = (iters + 5) / 6;
+        for (int r = 0; r < rounds; ++r) {
+            const double d = hi - lo;
+            double a[ORC_SEARCH_K];
+            for (int j = 1; j < ORC_SEARCH_K; ++j)
+                a[j] = orc_overlap(N, h, lo + d * ((double)j / (double)ORC_SEARCH_K));
+            int ms = 0;
+            while (ms + 1 < ORC_SEARCH_K && a[ms + 1] >= alpha_target) ++ms;
+            const double new_lo = lo + d * ((double)ms / (double)ORC_SEARCH_K);
+            const double new_hi = lo + d * ((double)(ms + 1) / (double)ORC_SEARCH_K);
+            if (ms > 0) {
+                lo = new_lo;
+                a_lo = a[ms];
             }
+            if (ms + 1 < ORC_SEARCH_K) hi = new_hi;
         }
         if (lo > 0.0) {
             dbeta = lo;

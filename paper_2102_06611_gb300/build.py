@@ -2,7 +2,8 @@
 
 Each ``csrc/*.cu`` file is compiled to an object in parallel, then linked into one shared
 library against the shared CUDA runtime (the same runtime PyTorch loads).  The FP64
-resampling / observables and population-analysis units are compiled with ``-fmad=false``
+resampling / observables, temperature-step search and population-analysis units are compiled
+with ``-fmad=false``
 so no multiply-add is ever contracted there.
 """
 from __future__ import annotations
@@ -21,7 +22,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "--expt-relaxed-constexpr", "-I", INCLUDE]
-PER_FILE = {"pa_resample.cu": ["-fmad=false"], "pa_analysis.cu": ["-fmad=false"]}
+PER_FILE = {"pa_resample.cu": ["-fmad=false"], "pa_analysis.cu": ["-fmad=false"], "pa_schedule.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:

@@ -422,7 +422,7 @@ pa_status pa_propose_schedule(pa_ctx *c, double alpha_target, double dbeta_max, 
     a.dbeta_max = dbeta_max;
     a.alpha_target = alpha_target;
     a.iters = pa::kBisectIters;
-    cudaError_t e = pa::launch_bisect(a, c->stream);
+    cudaError_t e = pa::launch_bisect(a, at<pa::SearchState>(c, c->ws.search), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "bisection launch");
     if ((s = sync_and_check(c)) != PA_OK) return s;
     double out[2];
@@ -535,7 +535,7 @@ pa_status pa_propose_learned(pa_ctx *c, const pa_learned_model *model, double al
     a.iters = pa::kBisectIters;
     a.use_prop = 1;
     a.alpha_floor = alpha_floor;
-    e = pa::launch_bisect(a, c->stream);
+    e = pa::launch_bisect(a, at<pa::SearchState>(c, c->ws.search), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "proposal check launch");
     if ((s = sync_and_check(c)) != PA_OK) return s;
     pa::DevState h;

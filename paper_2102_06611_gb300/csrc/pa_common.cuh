@@ -220,6 +220,53 @@ struct DevState {
     long long R_glob;         // sharded population: the whole population's size (0 otherwise)
 };
 
+// Block-wide exclusive prefix sum (every thread gets its prefix; *total the block sum) and
+// block-wide sum (valid in thread 0).  Every thread of the block must call them.
+template <typename T, int THREADS>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *total)
+{
+    __shared__ T warp_tot[THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T t = lane < THREADS / 32 ? warp_tot[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < THREADS / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const T before = wid > 0 ? warp_tot[wid - 1] : T(0);
+    *total = warp_tot[THREADS / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <typename T, int THREADS>
+__device__ __forceinline__ T block_sum(T v)
+{
+    __shared__ T part[THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[wid] = v;
+    __syncthreads();
+    T t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < THREADS / 32; ++i) t += part[i];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
 __device__ __forceinline__ void set_error(DevState *st, int code)
 {
     atomicCAS(&st->error, 0, code);

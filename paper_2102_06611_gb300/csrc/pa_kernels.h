@@ -61,6 +61,7 @@ struct Workspace {
     size_t ana_out;     // pa_analysis
     size_t wint;        // uint64[N + 1]  multinomial: integer weights floor(w_k 2^32)
     size_t cdf;         // uint64[capacity] multinomial: running sum of the parents' weights
+    size_t search;      // SearchState        temperature-step search
     size_t total;
     long long nblk;     // blocks of the copy-count / copy kernels
 };
@@ -178,7 +179,7 @@ cudaError_t launch_analysis(const DevState *st, const int *level, const int *mag
                             double beta, int n, long long capacity, long long *blk, int *sizes, pa_analysis *out,
                             cudaStream_t s);
 
-// Adaptive temperature step: bisection on dbeta for the histogram overlap (see k_bisect).
+// Adaptive temperature step: search on dbeta for the histogram overlap (pa_schedule.cu).
 struct BisectArgs {
     int L;
     DevState *st;
@@ -193,7 +194,19 @@ struct BisectArgs {
 
 constexpr int kBisectIters = 48;
 
-cudaError_t launch_bisect(const BisectArgs &a, cudaStream_t s);
+// State of one search for the next temperature step (device workspace, pa_schedule.cu).
+constexpr int kSearchK = 64;  // points per round: the bracket shrinks by 64 per round
+struct SearchBracket {
+    double lo, hi, a_lo;
+};
+struct SearchState {
+    int nocc, kmin, done, source;
+    long long R;
+    double hi0, dbeta, alpha;
+    SearchBracket br[2];                 // bracket of the last two rounds
+    double alpha_pts[2][kSearchK];       // overlaps at the points of the last two rounds
+};
+cudaError_t launch_bisect(const BisectArgs &a, SearchState *ss, cudaStream_t s);
 cudaError_t launch_families(const DevState *st, const int *fam, long long *fampart, cudaStream_t s);
 
 // Learned schedule (pa_mlp.cu).

@@ -1,7 +1,7 @@
 // pa_mlp.cu -- the learned temperature schedule: population features, a small MLP
 // (12 -> 64 -> 64 -> 64 tanh -> 2) with bfloat16 parameters and float32 accumulation, its
 // batched training kernels (forward, backward, Adam), and the proposal step that feeds the
-// network's (dbeta, theta) through the histogram-overlap check of k_bisect.
+// network's (dbeta, theta) through the histogram-overlap check of the step search (pa_schedule.cu).
 //
 // The paper has no learned schedule; it names self-adaptive steps (Sec. II), the overlap
 // guideline alpha > 0.7 and an adaptive theta (Sec. X).  The network only proposes; every

@@ -56,56 +56,12 @@ Workspace plan_workspace(int L, long long capacity)
     w.ana_out = off;  off = align256(off + sizeof(pa_analysis));
     w.wint = off;     off = align256(off + nlev * 8);
     w.cdf = off;      off = align256(off + (size_t)capacity * 8);
+    w.search = off;   off = align256(off + sizeof(SearchState));
     w.total = off;
     w.nblk = nblk;
     return w;
 }
 
-// ------------------------------------------------------------------------------ helpers
-template <typename T, int THREADS>
-__device__ __forceinline__ T block_exclusive_scan(T v, T *total)
-{
-    __shared__ T warp_tot[THREADS / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    T x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        T t = lane < THREADS / 32 ? warp_tot[lane] : T(0);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        if (lane < THREADS / 32) warp_tot[lane] = t;
-    }
-    __syncthreads();
-    const T before = wid > 0 ? warp_tot[wid - 1] : T(0);
-    *total = warp_tot[THREADS / 32 - 1];
-    __syncthreads();
-    return before + x - v;
-}
-
-template <typename T, int THREADS>
-__device__ __forceinline__ T block_sum(T v)
-{
-    __shared__ T part[THREADS / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) part[wid] = v;
-    __syncthreads();
-    T t = 0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < THREADS / 32; ++i) t += part[i];
-    __syncthreads();
-    return t;  // valid in thread 0
-}
 
 // Thresholds of the run's spin update at beta: Metropolis floor(e^{-4 beta} 2^32),
 // floor(e^{-8 beta} 2^32); heatbath T_3 = floor(2^32 / (1 + e^{4 beta})), T_4 likewise with 8 beta.
@@ -715,155 +671,12 @@ cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------ schedule
-// Adaptive temperature step.  alpha(dbeta) = sum over occupied levels k, ascending, of
-// min(p_k, q_k) with p_k = h_k / R (current energy distribution) and q_k = h_k w_k / S (its
-// reweighting to beta + dbeta; w_k, S as in k_table).  The step is the largest dbeta in
-// (0, hi], hi = min(dbeta_max, beta_final - beta), with alpha >= alpha_target: hi itself if
-// it qualifies, else `iters` bisection steps on [0, hi].  One block: the exps and the
-// per-level terms are computed in parallel, the two sums by one thread in ascending order.
-constexpr int kBisectThreads = 1024;
-
-__global__ void __launch_bounds__(kBisectThreads) k_bisect(BisectArgs a)
-{
-    __shared__ int sh_nocc, sh_kmin;
-    __shared__ long long sh_R;
-    __shared__ double sh_S, sh_alpha;
-    const int N = a.L * a.L, nlev = N + 1, tid = threadIdx.x;
-    DevState *st = a.st;
-
-    // compact the occupied levels in ascending order
-    const int chunk = (nlev + kBisectThreads - 1) / kBisectThreads;
-    const int k_lo = min(tid * chunk, nlev), k_hi = min(k_lo + chunk, nlev);
-    int occ = 0;
-    long long rsum = 0;
-    for (int k = k_lo; k < k_hi; ++k) {
-        occ += a.hist[k] > 0;
-        rsum += a.hist[k];
-    }
-    int nocc;
-    int pos = block_exclusive_scan<int, kBisectThreads>(occ, &nocc);
-    const long long R = block_sum<long long, kBisectThreads>(rsum);
-    for (int k = k_lo; k < k_hi; ++k) {
-        const int h = a.hist[k];
-        if (h > 0) {
-            a.occ_k[pos] = k;
-            a.occ_h[pos] = h;
-            ++pos;
-        }
-    }
-    if (tid == 0) {
-        sh_nocc = nocc;
-        sh_R = R;
-    }
-    __syncthreads();
-    if (tid == 0) sh_kmin = nocc > 0 ? a.occ_k[0] : 0;
-    __syncthreads();
-    nocc = sh_nocc;
-    const double Rd = (double)sh_R;
-    const int Eref = 4 * sh_kmin - 2 * N;
-
-    auto overlap = [&](double dbeta) -> double {
-        for (int i = tid; i < nocc; i += kBisectThreads) {
-            const int Ek = 4 * a.occ_k[i] - 2 * N;
-            a.occ_w[i] = det_exp(-__dmul_rn(dbeta, (double)(Ek - Eref)));
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double S = 0.0;
-            for (int i = 0; i < nocc; ++i) S = __dadd_rn(S, __dmul_rn((double)a.occ_h[i], a.occ_w[i]));
-            sh_S = S;
-        }
-        __syncthreads();
-        const double S = sh_S;
-        for (int i = tid; i < nocc; i += kBisectThreads) {
-            const double hk = (double)a.occ_h[i];
-            const double pk = __ddiv_rn(hk, Rd);
-            const double qk = __ddiv_rn(__dmul_rn(hk, a.occ_w[i]), S);
-            a.occ_t[i] = pk < qk ? pk : qk;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double alpha = 0.0;
-            for (int i = 0; i < nocc; ++i) alpha = __dadd_rn(alpha, a.occ_t[i]);
-            sh_alpha = alpha;
-        }
-        __syncthreads();
-        return sh_alpha;
-    };
-
-    double hi = __dsub_rn(a.beta_final, a.beta);
-    if (a.dbeta_max < hi) hi = a.dbeta_max;
-    double beta_next, alpha;
-    if (!(hi > 0.0) || nocc == 0) {
-        beta_next = a.beta_final;
-        alpha = 1.0;
-        if (tid == 0) st->source_next = a.use_prop ? PA_SCHED_LEARNED : PA_SCHED_BISECT;
-    } else {
-        const double hi0 = hi;
-        double dbeta = 0.0;
-        bool done = false;
-        int source = PA_SCHED_BISECT;
-        if (a.use_prop) {
-            // a proposed step is kept if its overlap reaches the floor
-            double dp = st->dbeta_prop;
-            if (dp > hi) dp = hi;
-            const double a_p = overlap(dp);
-            if (a_p >= a.alpha_floor) {
-                dbeta = dp;
-                alpha = a_p;
-                done = true;
-                source = PA_SCHED_LEARNED;
-            } else {
-                source = PA_SCHED_FALLBACK;
-            }
-        }
-        const double a_hi = done ? 0.0 : overlap(hi);
-        if (done) {
-        } else if (a_hi >= a.alpha_target) {
-            dbeta = hi;
-            alpha = a_hi;
-        } else {
-            double lo = 0.0, a_lo = 1.0;
-            for (int it = 0; it < a.iters; ++it) {
-                const double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
-                const double a_mid = overlap(mid);
-                if (a_mid >= a.alpha_target) {
-                    lo = mid;
-                    a_lo = a_mid;
-                } else {
-                    hi = mid;
-                }
-            }
-            if (lo > 0.0) {
-                dbeta = lo;
-                alpha = a_lo;
-            } else {  // no tried step reaches the target: take the smallest one tried
-                dbeta = hi;
-                alpha = overlap(hi);
-            }
-        }
-        beta_next = (dbeta == hi0 && hi0 == __dsub_rn(a.beta_final, a.beta)) ? a.beta_final
-                                                                            : __dadd_rn(a.beta, dbeta);
-        if (tid == 0) st->source_next = source;
-    }
-    if (tid == 0) {
-        st->beta_next = beta_next;
-        st->alpha_next = alpha;
-    }
-}
-
 cudaError_t launch_families(const DevState *st, const int *fam, long long *fampart, cudaStream_t s)
 {
     k_families<<<kFamBlocks, 256, 0, s>>>(st, fam, fampart);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bisect(const BisectArgs &a, cudaStream_t s)
-{
-    k_bisect<<<1, kBisectThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
 
 // ------------------------------------------------------------------------------ batches
 // One temperature step of every active run: begin (advance beta_i = i / (n_temps - 1)),
