@@ -183,8 +183,11 @@ __global__ void __launch_bounds__(1024) k_features(FeatureArgs a)
         __syncthreads();
         return t;
     };
+    // empty levels add exact zeros: skipping them leaves every sum unchanged and saves most
+    // of the (slow) binary64 work
     double hsum = 0.0, esum = 0.0;
     for (int k = tid; k <= N; k += 1024) {
+        if (a.hist[k] == 0) continue;
         const double h = (double)a.hist[k];
         hsum += h;
         esum += h * (4.0 * k - 2.0 * N);
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(1024) k_features(FeatureArgs a)
     const double mean = block_sum_d(esum) / R;
     double s2 = 0.0, s3 = 0.0, s4 = 0.0;
     for (int k = tid; k <= N; k += 1024) {
+        if (a.hist[k] == 0) continue;
         const double h = (double)a.hist[k];
         const double d = (4.0 * k - 2.0 * N) - mean;
         s2 += h * d * d;
@@ -203,10 +207,10 @@ __global__ void __launch_bounds__(1024) k_features(FeatureArgs a)
     double f2 = 0.0;
     for (int b = tid; b < kFamBlocks; b += 1024) f2 += (double)a.fampart[2 * b + 1];
     const double size2 = block_sum_d(f2);
-    double zeros = 0.0;
+    long long zeros = 0;  // an exact count (as the binary64 count was, below 2^53)
     const long long R_prev = a.st->R_prev;
-    for (long long j = tid; j < R_prev; j += 1024) zeros += a.counts[j] == 0 ? 1.0 : 0.0;
-    const double z = block_sum_d(zeros);
+    for (long long j = tid; j < R_prev; j += 1024) zeros += a.counts[j] == 0;
+    const double z = block_sum_d((double)zeros);
     if (tid == 0) {
         const double lnR = log(R);
         double f[kIn];

@@ -194,9 +194,11 @@ def anneal(pa: PopulationAnnealing, mode: str = "plain", model: ScheduleMLP | No
              decorrelated from their values after resampling (corr <= corr_target) or theta_max
              sweeps have run -- the rule that labels the network's training data.
     learned: the network proposes (dbeta, theta); dbeta is kept if the overlap reaches
-             alpha_floor (else the bisection decides and theta0 sweeps are used); after the
-             proposed sweeps the decorrelation since resampling is measured and, while it is
-             above corr_target, more sweeps run (half as many again each time, up to theta_max).
+             alpha_floor (else the bisection decides and theta0 sweeps are used); theta - 1 of
+             the proposed sweeps run in one launch (the proposal, whose error is about a sweep,
+             taken as a lower estimate), then the decorrelation since resampling is measured
+             and, while it is above corr_target, one more sweep runs (up to theta_max) -- the
+             same stopping rule as "rule", with most sweeps batched into one launch.
     """
     if mode not in ("plain", "rule", "learned"):
         raise ValueError(f"unknown schedule mode {mode!r}")
@@ -219,14 +221,16 @@ def anneal(pa: PopulationAnnealing, mode: str = "plain", model: ScheduleMLP | No
                 theta += 1
                 if pa.decorrelation() <= corr_target:
                     break
+        elif mode == "learned":
+            if theta > 1 and p["source"] == _lib.PA_SCHED_LEARNED:
+                theta -= 1
+            pa.anneal_step(theta)
+            while theta < theta_max and pa.decorrelation() > corr_target:
+                pa.anneal_step(1)
+                theta += 1
+                extended += 1
         else:
             pa.anneal_step(theta)
-        if mode == "learned":
-            while theta < theta_max and pa.decorrelation() > corr_target:
-                more = min(max(1, theta // 2), theta_max - theta)
-                pa.anneal_step(more)
-                theta += more
-                extended += 1
         steps += 1
         sweeps += theta
         beta = b
