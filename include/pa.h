@@ -442,9 +442,11 @@ pa_status pa_copy_numbers_static(int L, long long R_target, long long R_prev, co
    follows the linear schedule beta_i = i / (n_temps - 1), i = 0 .. n_temps - 1 (Sec. II,
    equal steps) and computes exactly what a single-run context with the same pa_config and
    that schedule computes.  One step of every unfinished run is one replay of a captured CUDA
-   graph whose sweep phase is a single persistent launch over all runs' replicas; the
-   persistent grid is chosen at initialisation by timing candidate grids on the batch's own
-   data (dry sweeps into the spare buffers, which change no run's state). */
+   graph whose sweep phase is either a single persistent launch over all runs' replicas or
+   one persistent launch per lattice size (concurrent); that choice, the persistent blocks per
+   SM and the replica groups per work item are chosen at initialisation by timing candidate
+   shapes on the batch's own data (dry sweeps into the spare buffers, which change no run's
+   state). */
 typedef struct pa_batch pa_batch;
 
 typedef struct {
@@ -453,11 +455,21 @@ typedef struct {
     int theta;         /* sweeps per temperature (>= 0) */
 } pa_run_desc;
 
+/* One shape of the batch's sweep phase tried by the autotuner. */
+typedef struct {
+    int unified;        /* 1: one persistent launch over every lattice size; 0: one per size,
+                           concurrent on side streams */
+    int blocks_per_sm;  /* persistent blocks of 256 threads per SM (capped by occupancy) */
+    int ipw_scale;      /* replica groups per work item: the default count times this */
+    float ms;           /* dry-sweep time of one step (ms) */
+} pa_batch_shape;
+
 typedef struct {
     int n_candidates;
-    int chosen_grid;   /* blocks of 256 threads of the persistent sweep */
-    int grid[4];       /* candidate grids */
-    float ms[4];       /* their dry-sweep times (ms) */
+    int chosen;                 /* index of the chosen shape */
+    int chosen_grid;            /* blocks of the chosen shape's (largest) launch */
+    int pad;
+    pa_batch_shape cand[16];    /* the shapes tried, in order */
 } pa_batch_tuning;
 
 /* Bytes of the single caller-owned device arena (256-byte aligned) holding every run's
@@ -486,8 +498,13 @@ pa_status pa_batch_observables(pa_batch *b, pa_obs *host_out);
    *count_out receives R_i.  Synchronising. */
 pa_status pa_batch_hashes(pa_batch *b, int run, unsigned long long *host_out, long long *count_out);
 
-/* The autotuner's candidates and choice. */
+/* The autotuner's candidates and choice (chosen = -1 after pa_batch_set_shape). */
 pa_status pa_batch_get_tuning(const pa_batch *b, pa_batch_tuning *out);
+
+/* Replace the autotuner's choice by the given shape (ms ignored) and capture the step graph
+   again; results are the same for every shape.  Synchronising; PA_ERR_INVALID_ARG for
+   unified outside {0, 1}, blocks_per_sm outside [1, 32] or ipw_scale outside [1, 16]. */
+pa_status pa_batch_set_shape(pa_batch *b, const pa_batch_shape *shape);
 
 void pa_batch_destroy(pa_batch *b);
 

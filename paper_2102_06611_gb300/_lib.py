@@ -190,9 +190,14 @@ class pa_run_desc(ctypes.Structure):
     _fields_ = [("cfg", pa_config), ("n_temps", ctypes.c_int), ("theta", ctypes.c_int)]
 
 
+class pa_batch_shape(ctypes.Structure):
+    _fields_ = [("unified", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("ipw_scale", ctypes.c_int),
+                ("ms", ctypes.c_float)]
+
+
 class pa_batch_tuning(ctypes.Structure):
-    _fields_ = [("n_candidates", ctypes.c_int), ("chosen_grid", ctypes.c_int), ("grid", ctypes.c_int * 4),
-                ("ms", ctypes.c_float * 4)]
+    _fields_ = [("n_candidates", ctypes.c_int), ("chosen", ctypes.c_int), ("chosen_grid", ctypes.c_int),
+                ("pad", ctypes.c_int), ("cand", pa_batch_shape * 16)]
 
 
 SIGNATURES.update({
@@ -204,6 +209,7 @@ SIGNATURES.update({
     "pa_batch_observables": (ctypes.c_int, [_vp, _vp]),
     "pa_batch_hashes": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _P(ctypes.c_longlong)]),
     "pa_batch_get_tuning": (ctypes.c_int, [_vp, _P(pa_batch_tuning)]),
+    "pa_batch_set_shape": (ctypes.c_int, [_vp, _P(pa_batch_shape)]),
     "pa_batch_destroy": (None, [_vp]),
 })
 

@@ -77,8 +77,15 @@ class Batch:
     def tuning(self) -> dict:
         t = _lib.pa_batch_tuning()
         _check(self.lib, None, self.lib.pa_batch_get_tuning(self.h, ctypes.byref(t)))
-        return {"chosen_grid": t.chosen_grid,
-                "candidates": [(t.grid[i], t.ms[i]) for i in range(t.n_candidates)]}
+        shapes = [{"unified": c.unified, "blocks_per_sm": c.blocks_per_sm, "ipw_scale": c.ipw_scale, "ms": c.ms}
+                  for c in t.cand[: t.n_candidates]]
+        chosen = shapes[t.chosen] if 0 <= t.chosen < len(shapes) else None
+        return {"chosen": chosen, "chosen_grid": t.chosen_grid, "candidates": shapes}
+
+    def set_shape(self, unified: int, blocks_per_sm: int, ipw_scale: int = 1) -> None:
+        """Fix the sweep phase's shape instead of the autotuner's choice (same results)."""
+        sh = _lib.pa_batch_shape(unified=int(unified), blocks_per_sm=int(blocks_per_sm), ipw_scale=int(ipw_scale))
+        _check(self.lib, None, self.lib.pa_batch_set_shape(self.h, ctypes.byref(sh)))
 
     def run_to_end(self, max_steps: int = 100000) -> int:
         steps = 0

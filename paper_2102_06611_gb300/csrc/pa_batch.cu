@@ -112,7 +112,45 @@ struct pa_batch {
     int sweep_grid;
     pa_batch_tuning tuning;
     pa::BatchSweepPlan plan;
+    std::vector<pa::BatchRun> table;  // host copy of the run table
+    int occ[pa::kBatchGroups], occ_all, max_bps;
 };
+
+namespace {
+
+// Set the sweep phase's shape: plan, and the replica groups per work item in the run table
+// (copied to the device; synchronous).
+cudaError_t apply_shape(pa_batch *b, int unified, int bps, int scale)
+{
+    b->plan.unified = unified;
+    b->plan.grid_all = b->num_sms * std::min(bps, b->occ_all);
+    for (int i = 0; i < b->plan.ngroups; ++i) b->plan.grid[i] = b->num_sms * std::min(bps, b->occ[i]);
+    for (int i = 0; i < b->n; ++i)
+        b->table[(size_t)i].ipw = std::min(16, ipw_for(b->desc[(size_t)i].cfg.L, b->desc[(size_t)i].theta) * scale);
+    b->sweep_grid = unified ? b->plan.grid_all : b->num_sms * std::min(bps, b->max_bps);
+    return cudaMemcpy(b->arena + b->t.runs, b->table.data(), sizeof(pa::BatchRun) * b->table.size(),
+                      cudaMemcpyHostToDevice);
+}
+
+// Capture one temperature step of every run into b->graph / b->exec.
+cudaError_t capture_step(pa_batch *b)
+{
+    char *tb = b->arena;
+    cudaError_t e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = pa::launch_batch_step(
+            reinterpret_cast<const pa::BatchRun *>(tb + b->t.runs), reinterpret_cast<pa::BatchState *>(tb + b->t.state),
+            reinterpret_cast<pa::BatchCtl *>(tb + b->t.ctl), reinterpret_cast<const int *>(tb + b->t.order),
+            reinterpret_cast<long long *>(tb + b->t.item_start), reinterpret_cast<pa_obs *>(tb + b->t.records), b->n,
+            b->nblk_max, b->nlev_max, b->plan, b->cs);
+        e = cudaStreamEndCapture(b->cs, &b->graph);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    return e;
+}
+
+}  // namespace
 
 static void destroy_plan(pa::BatchSweepPlan &p)
 {
@@ -309,31 +347,36 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     if (e == cudaSuccess) e = pa::launch_batch_record(d_runs, d_state, d_records, n_runs, b->user);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->user);  // host tables must outlive the copies
 
-    // autotune the blocks per SM of the persistent sweeps on dry sweeps (spare buffers
-    // only); each size's kernel gets min(candidate, its occupancy) blocks per SM
-    int occ[pa::kBatchGroups];
-    int max_bps = 1;
+    // autotune the sweep phase on dry sweeps (spare buffers only): one launch over every size
+    // or one per size, persistent blocks per SM (each kernel capped by its occupancy), and
+    // replica groups per work item (the default count, or twice it)
+    b->max_bps = 1;
     for (int i = 0; i < b->plan.ngroups; ++i) {
-        occ[i] = pa::batch_sweep_max_blocks_per_sm(b->plan.L[i]);
-        max_bps = std::max(max_bps, occ[i]);
+        b->occ[i] = pa::batch_sweep_max_blocks_per_sm(b->plan.L[i]);
+        b->max_bps = std::max(b->max_bps, b->occ[i]);
     }
-    auto set_grids = [&](int bps) {
-        for (int i = 0; i < b->plan.ngroups; ++i) b->plan.grid[i] = b->num_sms * std::min(bps, occ[i]);
+    b->occ_all = pa::batch_sweep_max_blocks_per_sm(0);
+    b->plan.n = n_runs;
+    b->table = table;
+    struct Shape {
+        int unified, bps, scale;
     };
+    std::vector<Shape> shapes;
+    for (int unified = 0; unified < 2; ++unified)
+        for (int bps = 1; bps <= std::min(2, unified ? b->occ_all : b->max_bps); ++bps)
+            for (int scale = 1; scale <= 2; scale *= 2) shapes.push_back({unified, bps, scale});
+    auto apply = [&](const Shape &sh) -> cudaError_t { return apply_shape(b, sh.unified, sh.bps, sh.scale); };
     std::memset(&b->tuning, 0, sizeof(b->tuning));
-    b->sweep_grid = b->num_sms * max_bps;
-    set_grids(max_bps);
     if (e == cudaSuccess) {
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
         float best = 1e30f;
+        int chosen = 0;
         int dry = 1;
         e = cudaMemcpy(&reinterpret_cast<pa::BatchCtl *>(tb + b->t.ctl)->dry, &dry, sizeof(int), cudaMemcpyHostToDevice);
-        int nc = 0;
-        for (int bps = 1; bps <= max_bps && nc < 4 && e == cudaSuccess; ++bps, ++nc) {
-            const int grid = b->num_sms * bps;
-            set_grids(bps);
+        for (size_t c = 0; c < shapes.size() && c < 16 && e == cudaSuccess; ++c) {
+            e = apply(shapes[c]);
             float ms = 0.f;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                 e = pa::launch_batch_items(d_runs, d_state, d_ctl, d_order, d_items, n_runs, 0, b->user);
@@ -343,16 +386,19 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
             }
-            b->tuning.grid[nc] = grid;
-            b->tuning.ms[nc] = ms;
+            pa_batch_shape &cs = b->tuning.cand[b->tuning.n_candidates++];
+            cs.unified = shapes[c].unified;
+            cs.blocks_per_sm = shapes[c].bps;
+            cs.ipw_scale = shapes[c].scale;
+            cs.ms = ms;
             if (ms < best) {
                 best = ms;
-                b->sweep_grid = grid;
+                chosen = (int)c;
             }
         }
-        b->tuning.n_candidates = nc;
+        if (e == cudaSuccess) e = apply(shapes[(size_t)chosen]);
+        b->tuning.chosen = chosen;
         b->tuning.chosen_grid = b->sweep_grid;
-        set_grids(b->sweep_grid / b->num_sms);
         dry = 0;
         if (e == cudaSuccess)
             e = cudaMemcpy(&reinterpret_cast<pa::BatchCtl *>(tb + b->t.ctl)->dry, &dry, sizeof(int), cudaMemcpyHostToDevice);
@@ -361,14 +407,7 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     }
 
     // capture one temperature step of every run
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaError_t le = pa::launch_batch_step(d_runs, d_state, d_ctl, d_order, d_items, d_records, n_runs,
-                                               b->nblk_max, b->nlev_max, b->plan, b->cs);
-        e = cudaStreamEndCapture(b->cs, &b->graph);
-        if (le != cudaSuccess) e = le;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) e = capture_step(b);
     if (e != cudaSuccess) {
         destroy_plan(b->plan);
         cudaEventDestroy(b->ev_in);
@@ -445,6 +484,24 @@ pa_status pa_batch_hashes(pa_batch *b, int run, unsigned long long *host_out, lo
     if (e == cudaSuccess) e = cudaMemcpy(host_out, dev, sizeof(unsigned long long) * (size_t)R, cudaMemcpyDeviceToHost);
     *count_out = R;
     return e == cudaSuccess ? PA_OK : PA_ERR_CUDA;
+}
+
+pa_status pa_batch_set_shape(pa_batch *b, const pa_batch_shape *shape)
+{
+    if (!b || !shape || (shape->unified != 0 && shape->unified != 1) || shape->blocks_per_sm < 1 ||
+        shape->blocks_per_sm > 32 || shape->ipw_scale < 1 || shape->ipw_scale > 16)
+        return PA_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->cs) != cudaSuccess || cudaStreamSynchronize(b->user) != cudaSuccess)
+        return PA_ERR_CUDA;
+    if (apply_shape(b, shape->unified, shape->blocks_per_sm, shape->ipw_scale) != cudaSuccess) return PA_ERR_CUDA;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    if (capture_step(b) != cudaSuccess) return PA_ERR_CUDA;
+    b->tuning.chosen = -1;
+    b->tuning.chosen_grid = b->sweep_grid;
+    return PA_OK;
 }
 
 pa_status pa_batch_get_tuning(const pa_batch *b, pa_batch_tuning *out)

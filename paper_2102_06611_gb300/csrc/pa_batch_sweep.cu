@@ -1,0 +1,368 @@
+// pa_batch_sweep.cu -- the persistent sweep kernels of batches (pa_batch.cu): the
+// single-run sweep arithmetic (pa_sweep.cuh) applied to work items of many runs.
+#include "pa_sweep.cuh"
+
+// Minimum resident blocks of 256 threads per SM of the batched sweep kernels.
+#ifndef PA_BATCH_MIN_BLOCKS
+#define PA_BATCH_MIN_BLOCKS 2
+#endif
+
+namespace pa {
+
+// ------------------------------------------------------------------------------ batches
+// One persistent launch per lattice size present sweeps the active runs of that size (the
+// launches run concurrently on side streams): warps take work items (ipw consecutive
+// replica groups of one run) from the size's counter, largest items first (runs are
+// ordered by cost within a size).  The per-replica arithmetic
+// is exactly the single-run kernel's, with the histogram and sums going to the run's own
+// workspace: level counts aggregated over the warp, the seven exact sums once per item.
+template <int L>
+__device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
+                                            unsigned long long *tq_eq, unsigned long long *tq_a4,
+                                            unsigned int *tq_code, const unsigned int *rk0, const unsigned int *rk1,
+                                            unsigned long long *v)
+{
+    using Gm = Geo<L>;
+    using W = typename Gm::W;
+    constexpr int N = Gm::N, G = Gm::G, RPW = Gm::RPW, RPL = Gm::RPL;
+    const int q = lane & (G - 1);
+    const int sub = lane / G;
+    const int r0 = q * RPL;
+    const long long R = a.st->R_cur;
+    const long long j = g * RPW + sub;
+    const bool active = j < R;
+    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
+    W A[RPL], B[RPL];
+    W *rep = reinterpret_cast<W *>(a.spins) + (size_t)(active ? j : 0) * (2 * L);
+    if (active) load_rows<L>(rep, r0, A, B);
+    else {
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
+    }
+    const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), nullptr, tq_code};
+    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, ac, tq);
+    int anti, ups;
+    measure_rows<L>(A, B, r0, lane, anti, ups);
+    anti = group_sum<G>(anti);
+    ups = group_sum<G>(ups);
+    int level = -1;
+    if (active) {
+        if (dry) {
+            store_rows<L>(reinterpret_cast<W *>(const_cast<void *>(spare)) + (size_t)j * (2 * L), r0, A, B);
+        } else {
+            if (a.theta > 0) store_rows<L>(rep, r0, A, B);
+            if (q == 0) {
+                level = anti >> 1;
+                const int M = 2 * ups - N;
+                const unsigned long long k0 = (unsigned long long)a.level[j];
+                const unsigned long long k1 = (unsigned long long)level;
+                a.level_snap[j] = (int)k0;
+                a.level[j] = level;
+                a.mag[j] = M;
+                v[0] += (unsigned long long)(M < 0 ? -M : M);
+                v[1] += (unsigned long long)((long long)M * M);
+                v[2] += k0;
+                v[3] += k0 * k0;
+                v[4] += k1;
+                v[5] += k1 * k1;
+                v[6] += k0 * k1;
+            }
+        }
+    }
+    if constexpr (RPW >= 8) {
+        // many replicas per warp: one atomic per distinct level
+        const unsigned int grp = __match_any_sync(0xffffffffu, level);
+        if (level >= 0 && lane == __ffs((int)grp) - 1) atomicAdd(&a.hist[level], __popc(grp));
+    } else if (level >= 0) {
+        atomicAdd(&a.hist[level], 1);
+    }
+}
+
+// Items of one group (ipw = 1) take this form, which nvcc compiles to faster code for them
+// than the general loop below (measured).
+template <int L>
+__device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
+                                           unsigned long long *tq_eq, unsigned long long *tq_a4,
+                                           unsigned int *tq_code)
+{
+    using Gm = Geo<L>;
+    using W = typename Gm::W;
+    constexpr int N = Gm::N, G = Gm::G, RPW = Gm::RPW, RPL = Gm::RPL;
+    const int q = lane & (G - 1);
+    const int sub = lane / G;
+    const int r0 = q * RPL;
+    const long long R = a.st->R_cur;
+    const long long j = g * RPW + sub;
+    const bool active = j < R;
+    unsigned int rk0[10], rk1[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
+        rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
+    }
+    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
+    W A[RPL], B[RPL];
+    W *rep = reinterpret_cast<W *>(a.spins) + (size_t)(active ? j : 0) * (2 * L);
+    if (active) load_rows<L>(rep, r0, A, B);
+    else {
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
+    }
+    const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), nullptr, tq_code};
+    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, ac, tq);
+    int anti, ups;
+    measure_rows<L>(A, B, r0, lane, anti, ups);
+    anti = group_sum<G>(anti);
+    ups = group_sum<G>(ups);
+    unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (active) {
+        if (dry) {
+            store_rows<L>(reinterpret_cast<W *>(const_cast<void *>(spare)) + (size_t)j * (2 * L), r0, A, B);
+        } else {
+            if (a.theta > 0) store_rows<L>(rep, r0, A, B);
+            if (q == 0) {
+                const int level = anti >> 1;
+                const int M = 2 * ups - N;
+                const unsigned long long k0 = (unsigned long long)a.level[j];
+                const unsigned long long k1 = (unsigned long long)level;
+                a.level_snap[j] = (int)k0;
+                a.level[j] = level;
+                a.mag[j] = M;
+                atomicAdd(&a.hist[level], 1);
+                v[0] = (unsigned long long)(M < 0 ? -M : M);
+                v[1] = (unsigned long long)((long long)M * M);
+                v[2] = k0;
+                v[3] = k0 * k0;
+                v[4] = k1;
+                v[5] = k1 * k1;
+                v[6] = k0 * k1;
+            }
+        }
+    }
+    // all replicas of the item belong to one run: one atomic per sum and item
+#pragma unroll
+    for (int i = 0; i < 7; ++i) v[i] = group_sum<32>(v[i]);
+    if (lane == 0 && !dry) {
+        atomicAdd(&a.st->sum_absM, v[0]);
+        atomicAdd(&a.st->sum_M2, v[1]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), v[2]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), v[3]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), v[4]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), v[5]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), v[6]);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare, long long item, int ipw, int lane,
+                                           int dry, unsigned long long *tq_eq, unsigned long long *tq_a4,
+                                           unsigned int *tq_code)
+{
+    constexpr int RPW = Geo<L>::RPW;
+    if (ipw == 1) {  // uniform over the warp
+        batch_item_single<L>(a, spare, item, lane, dry, tq_eq, tq_a4, tq_code);
+        return;
+    }
+    unsigned int rk0[10], rk1[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
+        rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
+    }
+    const long long R = a.st->R_cur;
+    unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 1
+    for (int k = 0; k < ipw; ++k) {
+        const long long g = item * ipw + k;
+        if (g * RPW >= R) break;  // uniform over the warp
+        batch_group<L>(a, spare, g, lane, dry, tq_eq, tq_a4, tq_code, rk0, rk1, v);
+    }
+    // every replica of the item belongs to one run: one atomic per sum and item
+#pragma unroll
+    for (int i = 0; i < 7; ++i) v[i] = group_sum<32>(v[i]);
+    if (lane == 0 && !dry) {
+        atomicAdd(&a.st->sum_absM, v[0]);
+        atomicAdd(&a.st->sum_M2, v[1]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), v[2]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), v[3]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), v[4]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), v[5]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), v[6]);
+    }
+}
+
+// Persistent sweep over the work items of the runs with lattice size L (group g): warps
+// take items from the group's counter; the item's run is found by bisection over the
+// group's order positions.
+template <int L>
+__global__ void __launch_bounds__(256, PA_BATCH_MIN_BLOCKS) k_b_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl,
+                                                     const int *order, const long long *item_start)
+{
+    constexpr int g = batch_group_of(L);
+    const int lane = threadIdx.x & 31;
+    const int dry = ctl->dry;
+    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp; 8 warps per block
+    __shared__ unsigned long long tq_eq[8 * TQ], tq_a4[8 * TQ];
+    __shared__ unsigned int tq_code[8 * TQ];
+    const int wib = threadIdx.x >> 5;
+    unsigned long long *qe = tq_eq + wib * TQ, *qa = tq_a4 + wib * TQ;
+    unsigned int *qc = tq_code + wib * TQ;
+    const long long end = ctl->end[g];
+    const int p0 = ctl->pbeg[g], p1 = ctl->pend[g];
+    for (;;) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(&ctl->next[g], 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= end) break;
+        int lo = p0, hi = p1;  // largest lo with item_start[lo] <= item
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (item_start[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int r = order[lo];
+        const BatchState s = state[r];
+        const BatchRun &run = runs[r];
+        SweepArgs a = run.sw[s.cur];
+        a.step = (unsigned int)s.step;
+        a.t0 = 0;
+        a.theta = run.theta;
+        const void *spare = run.sw[s.cur ^ 1].spins;
+        batch_item<L>(a, spare, item - item_start[lo], run.ipw, lane, dry, qe, qa, qc);
+    }
+}
+
+template <int L>
+static cudaError_t launch_b_sweep_t(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
+                                    const long long *item_start, int grid, cudaStream_t s)
+{
+    k_b_sweep<L><<<grid, 256, 0, s>>>(runs, state, ctl, order, item_start);
+    return cudaGetLastError();
+}
+
+// One persistent launch for every run of the batch, whatever its lattice size: warps take
+// items from one counter over all runs (in the order of k_b_items: by size, then by cost)
+// and dispatch on the run's L to the same per-size item code.  Its tie queues are sized for
+// the largest size's need.
+constexpr int tq_len_max()
+{
+    int m = SweepStyle<4>::TQ_LEN;
+    m = m > SweepStyle<8>::TQ_LEN ? m : SweepStyle<8>::TQ_LEN;
+    m = m > SweepStyle<12>::TQ_LEN ? m : SweepStyle<12>::TQ_LEN;
+    m = m > SweepStyle<16>::TQ_LEN ? m : SweepStyle<16>::TQ_LEN;
+    m = m > SweepStyle<24>::TQ_LEN ? m : SweepStyle<24>::TQ_LEN;
+    m = m > SweepStyle<32>::TQ_LEN ? m : SweepStyle<32>::TQ_LEN;
+    m = m > SweepStyle<48>::TQ_LEN ? m : SweepStyle<48>::TQ_LEN;
+    m = m > SweepStyle<64>::TQ_LEN ? m : SweepStyle<64>::TQ_LEN;
+    m = m > SweepStyle<128>::TQ_LEN ? m : SweepStyle<128>::TQ_LEN;
+    return m;
+}
+
+__global__ void __launch_bounds__(256, PA_BATCH_MIN_BLOCKS) k_b_sweep_all(const BatchRun *runs,
+                                                                          const BatchState *state, BatchCtl *ctl,
+                                                                          const int *order,
+                                                                          const long long *item_start, int n)
+{
+    const int lane = threadIdx.x & 31;
+    const int dry = ctl->dry;
+    constexpr int TQ = tq_len_max();  // per warp; 8 warps per block
+    __shared__ unsigned long long tq_eq[8 * TQ], tq_a4[8 * TQ];
+    __shared__ unsigned int tq_code[8 * TQ];
+    const int wib = threadIdx.x >> 5;
+    unsigned long long *qe = tq_eq + wib * TQ, *qa = tq_a4 + wib * TQ;
+    unsigned int *qc = tq_code + wib * TQ;
+    const long long end = ctl->total_items;
+    for (;;) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(&ctl->next_item, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= end) break;
+        int lo = 0, hi = n;  // largest lo with item_start[lo] <= item
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (item_start[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int r = order[lo];
+        const BatchState s = state[r];
+        const BatchRun &run = runs[r];
+        SweepArgs a = run.sw[s.cur];
+        a.step = (unsigned int)s.step;
+        a.t0 = 0;
+        a.theta = run.theta;
+        const void *spare = run.sw[s.cur ^ 1].spins;
+        const long long it = item - item_start[lo];
+        switch (run.L) {
+            case 4: batch_item<4>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 8: batch_item<8>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 12: batch_item<12>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 16: batch_item<16>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 24: batch_item<24>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 32: batch_item<32>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 48: batch_item<48>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 64: batch_item<64>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 128: batch_item<128>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            default: break;
+        }
+    }
+}
+
+cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
+                               const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s)
+{
+    if (plan.unified) {
+        k_b_sweep_all<<<plan.grid_all, 256, 0, s>>>(runs, state, ctl, order, item_start, plan.n);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaEventRecord(plan.fork, s);
+    for (int i = 0; i < plan.ngroups && e == cudaSuccess; ++i) {
+        cudaStream_t t = plan.side[i];
+        if ((e = cudaStreamWaitEvent(t, plan.fork, 0)) != cudaSuccess) break;
+        switch (plan.L[i]) {
+            case 4: e = launch_b_sweep_t<4>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 8: e = launch_b_sweep_t<8>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 12: e = launch_b_sweep_t<12>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 16: e = launch_b_sweep_t<16>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 24: e = launch_b_sweep_t<24>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 32: e = launch_b_sweep_t<32>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 48: e = launch_b_sweep_t<48>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 64: e = launch_b_sweep_t<64>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 128: e = launch_b_sweep_t<128>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            default: e = cudaErrorInvalidValue; break;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(plan.join[i], t);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan.join[i], 0);
+    }
+    return e;
+}
+
+template <int L>
+static int b_sweep_occupancy()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep<L>, 256, 0) != cudaSuccess) return 1;
+    return b > 0 ? b : 1;
+}
+
+int batch_sweep_max_blocks_per_sm(int L)
+{
+    if (L == 0) {  // the kernel over every size
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep_all, 256, 0) != cudaSuccess) return 1;
+        return b > 0 ? b : 1;
+    }
+    switch (L) {
+        case 4: return b_sweep_occupancy<4>();
+        case 8: return b_sweep_occupancy<8>();
+        case 12: return b_sweep_occupancy<12>();
+        case 16: return b_sweep_occupancy<16>();
+        case 24: return b_sweep_occupancy<24>();
+        case 32: return b_sweep_occupancy<32>();
+        case 48: return b_sweep_occupancy<48>();
+        case 64: return b_sweep_occupancy<64>();
+        case 128: return b_sweep_occupancy<128>();
+        default: return 1;
+    }
+}
+
+}  // namespace pa

@@ -275,6 +275,8 @@ struct BatchSweepPlan {
     int grid[kBatchGroups];
     cudaStream_t side[kBatchGroups];
     cudaEvent_t fork, join[kBatchGroups];
+    // one launch over every size (k_b_sweep_all, grid_all blocks) instead of one per size
+    int unified, grid_all, n;
 };
 
 cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,

@@ -34,10 +34,16 @@ MIXED = [
 ]
 
 
-def test_mixed_batch_matches_single_runs():
+@pytest.mark.parametrize("shape", [None, (1, 2, 1), (0, 1, 2), (1, 1, 4)])
+def test_mixed_batch_matches_single_runs(shape):
+    """The autotuner's shape, and fixed shapes: one launch over every size or one per size,
+    1-2 blocks per SM, 1-4x the default replica groups per work item."""
     from paper_2102_06611_gb300.batch import Batch, RunSpec
     specs = [RunSpec(L, R, seed, nT, th, kind) for (L, R, seed, nT, th, kind) in MIXED]
     b = Batch(specs)
+    if shape is not None:
+        b.set_shape(*shape)
+        assert b.tuning()["chosen"] is None
     steps = b.run_to_end()
     assert steps == max(s.n_temps for s in specs) - 1
     active, status, step = b.status()
@@ -53,7 +59,9 @@ def test_mixed_batch_matches_single_runs():
             assert recs[i][k] == o[k], (i, k, recs[i][k], o[k])
         pa.close()
     t = b.tuning()
-    assert t["chosen_grid"] in [g for g, _ in t["candidates"]]
+    if shape is None:
+        assert t["chosen"] in t["candidates"] and t["chosen"]["ms"] == min(c["ms"] for c in t["candidates"])
+        assert {c["unified"] for c in t["candidates"]} == {0, 1}
 
 
 def test_batch_run_against_oracle():
