@@ -459,7 +459,7 @@ typedef struct {
 typedef struct {
     int unified;        /* 1: one persistent launch over every lattice size; 0: one per size,
                            concurrent on side streams */
-    int blocks_per_sm;  /* persistent blocks of 256 threads per SM (capped by occupancy) */
+    int blocks_per_sm;  /* persistent blocks per SM (capped by occupancy) */
     int ipw_scale;      /* replica groups per work item: the default count times this */
     float ms;           /* dry-sweep time of one step (ms) */
 } pa_batch_shape;

@@ -2,10 +2,17 @@
 // single-run sweep arithmetic (pa_sweep.cuh) applied to work items of many runs.
 #include "pa_sweep.cuh"
 
-// Minimum resident blocks of 256 threads per SM of the batched sweep kernels.
-#ifndef PA_BATCH_MIN_BLOCKS
-#define PA_BATCH_MIN_BLOCKS 2
+// Block shape of the batched sweep kernels: PA_BATCH_THREADS threads, at least
+// PA_BATCH_MIN_BLOCKS resident blocks per SM (so at most 65536 / (threads x blocks) registers).
+// One block of 384 per SM (12 warps, at most 170 registers) was measured best on the 64-run
+// mixed workload: 2.87 ms per dry sweep against 2.99 (512 x 1) and 3.02 (256 x 2).
+#ifndef PA_BATCH_THREADS
+#define PA_BATCH_THREADS 384
 #endif
+#ifndef PA_BATCH_MIN_BLOCKS
+#define PA_BATCH_MIN_BLOCKS 1
+#endif
+constexpr int kBatchWarps = PA_BATCH_THREADS / 32;
 
 namespace pa {
 
@@ -195,15 +202,15 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
 // take items from the group's counter; the item's run is found by bisection over the
 // group's order positions.
 template <int L>
-__global__ void __launch_bounds__(256, PA_BATCH_MIN_BLOCKS) k_b_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl,
+__global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl,
                                                      const int *order, const long long *item_start)
 {
     constexpr int g = batch_group_of(L);
     const int lane = threadIdx.x & 31;
     const int dry = ctl->dry;
-    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp; 8 warps per block
-    __shared__ unsigned long long tq_eq[8 * TQ], tq_a4[8 * TQ];
-    __shared__ unsigned int tq_code[8 * TQ];
+    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp
+    __shared__ unsigned long long tq_eq[kBatchWarps * TQ], tq_a4[kBatchWarps * TQ];
+    __shared__ unsigned int tq_code[kBatchWarps * TQ];
     const int wib = threadIdx.x >> 5;
     unsigned long long *qe = tq_eq + wib * TQ, *qa = tq_a4 + wib * TQ;
     unsigned int *qc = tq_code + wib * TQ;
@@ -236,7 +243,7 @@ template <int L>
 static cudaError_t launch_b_sweep_t(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
                                     const long long *item_start, int grid, cudaStream_t s)
 {
-    k_b_sweep<L><<<grid, 256, 0, s>>>(runs, state, ctl, order, item_start);
+    k_b_sweep<L><<<grid, PA_BATCH_THREADS, 0, s>>>(runs, state, ctl, order, item_start);
     return cudaGetLastError();
 }
 
@@ -258,16 +265,16 @@ constexpr int tq_len_max()
     return m;
 }
 
-__global__ void __launch_bounds__(256, PA_BATCH_MIN_BLOCKS) k_b_sweep_all(const BatchRun *runs,
+__global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_sweep_all(const BatchRun *runs,
                                                                           const BatchState *state, BatchCtl *ctl,
                                                                           const int *order,
                                                                           const long long *item_start, int n)
 {
     const int lane = threadIdx.x & 31;
     const int dry = ctl->dry;
-    constexpr int TQ = tq_len_max();  // per warp; 8 warps per block
-    __shared__ unsigned long long tq_eq[8 * TQ], tq_a4[8 * TQ];
-    __shared__ unsigned int tq_code[8 * TQ];
+    constexpr int TQ = tq_len_max();  // per warp
+    __shared__ unsigned long long tq_eq[kBatchWarps * TQ], tq_a4[kBatchWarps * TQ];
+    __shared__ unsigned int tq_code[kBatchWarps * TQ];
     const int wib = threadIdx.x >> 5;
     unsigned long long *qe = tq_eq + wib * TQ, *qa = tq_a4 + wib * TQ;
     unsigned int *qc = tq_code + wib * TQ;
@@ -311,7 +318,7 @@ cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, Ba
                                const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s)
 {
     if (plan.unified) {
-        k_b_sweep_all<<<plan.grid_all, 256, 0, s>>>(runs, state, ctl, order, item_start, plan.n);
+        k_b_sweep_all<<<plan.grid_all, PA_BATCH_THREADS, 0, s>>>(runs, state, ctl, order, item_start, plan.n);
         return cudaGetLastError();
     }
     cudaError_t e = cudaEventRecord(plan.fork, s);
@@ -340,7 +347,7 @@ template <int L>
 static int b_sweep_occupancy()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep<L>, 256, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep<L>, PA_BATCH_THREADS, 0) != cudaSuccess) return 1;
     return b > 0 ? b : 1;
 }
 
@@ -348,7 +355,7 @@ int batch_sweep_max_blocks_per_sm(int L)
 {
     if (L == 0) {  // the kernel over every size
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep_all, 256, 0) != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep_all, PA_BATCH_THREADS, 0) != cudaSuccess) return 1;
         return b > 0 ? b : 1;
     }
     switch (L) {

@@ -20,22 +20,22 @@
 #include "pa_common.cuh"
 #include "pa_kernels.h"
 
-// Build knobs of the sweep kernel, set to the measured best.  PA_SWEEP_THREADS: threads per
-// block (256; blocks of 128 or 192 were slower).  PA_SWEEP_MIN_BLOCKS: minimum resident
-// blocks per SM it is compiled for, which caps its registers at 65536 / (threads * n): 2,
-// except at L = 8 and 128, where one block of up to 255 registers per thread is faster
-// (L = 128: +3 % over two blocks of 128 registers).
-#ifndef PA_SWEEP_THREADS
-#define PA_SWEEP_THREADS 256
+// Block shape of the sweep kernel, set to the measured best: one block per SM of 512 threads
+// (16 warps, at most 128 registers), except L = 128: 384 threads (12 warps, at most 170
+// registers).  Measured at beta = 0.2 / 0.44 / 0.8 against two blocks of 256 per SM (one at
+// L = 8 and 128), the previous shape: +3 to +7 % at every size (L = 64 +4.5 %, L = 16 +7 %),
+// L = 128 +5.7 % with 384 threads (+1 % with 512); 320, 448 and 640 threads and two blocks of
+// 192 or three of 128 were slower.  PA_SWEEP_THREADS / PA_SWEEP_MIN_BLOCKS override the shape
+// for every size (build knobs).
+#ifdef PA_SWEEP_THREADS
+constexpr int sweep_threads(int) { return PA_SWEEP_THREADS; }
+#else
+constexpr int sweep_threads(int L) { return L == 128 ? 384 : 512; }
 #endif
 #ifndef PA_SWEEP_MIN_BLOCKS
-#define PA_SWEEP_MIN_BLOCKS 2
+#define PA_SWEEP_MIN_BLOCKS 1
 #endif
-constexpr int kSweepWarps = PA_SWEEP_THREADS / 32;  // warps per block of the sweep kernel
-constexpr int sweep_min_blocks(int L)
-{
-    return (L == 8 || L == 128) ? (256 / PA_SWEEP_THREADS > 0 ? 256 / PA_SWEEP_THREADS : 1) : PA_SWEEP_MIN_BLOCKS;
-}
+constexpr int sweep_min_blocks(int) { return PA_SWEEP_MIN_BLOCKS; }
 #ifndef PA_TM_IMAD
 #define PA_TM_IMAD 1   // threshold bits by multiply-add (see Accept)
 #endif
@@ -839,7 +839,7 @@ __device__ __forceinline__ void measure_rows(const typename Geo<L>::W *A, const 
 // Metropolis (!HB) or heatbath (HB) update, measure.
 // ------------------------------------------------------------------------------------
 template <int L, bool INIT, bool HB>
-__global__ void __launch_bounds__(PA_SWEEP_THREADS, sweep_min_blocks(L)) k_sweep(SweepArgs a)
+__global__ void __launch_bounds__(sweep_threads(L), sweep_min_blocks(L)) k_sweep(SweepArgs a)
 {
     using Gm = Geo<L>;
     using W = typename Gm::W;
@@ -874,8 +874,9 @@ __global__ void __launch_bounds__(PA_SWEEP_THREADS, sweep_min_blocks(L)) k_sweep
     __syncthreads();
     W *spins = reinterpret_cast<W *>(a.spins);
     constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp
-    __shared__ W tq_eq[kSweepWarps * TQ], tq_a4[kSweepWarps * TQ], tq_inv[HB ? kSweepWarps * TQ : 1];
-    __shared__ unsigned int tq_code[kSweepWarps * TQ];
+    constexpr int kWarps = sweep_threads(L) / 32;
+    __shared__ W tq_eq[kWarps * TQ], tq_a4[kWarps * TQ], tq_inv[HB ? kWarps * TQ : 1];
+    __shared__ unsigned int tq_code[kWarps * TQ];
     const int wib = threadIdx.x >> 5;
     const TieQueue<W> tq{tq_eq + wib * TQ, tq_a4 + wib * TQ, HB ? tq_inv + wib * TQ : nullptr,
                          tq_code + wib * TQ};
@@ -972,23 +973,28 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int num_sms, cudaStream_t s)
 {
     constexpr int N = Geo<L>::N;
     const size_t smem = (size_t)(N + 1) * sizeof(int);
-    static int blocks_per_sm = 0;  // occupancy of this instantiation, queried once
-    if (blocks_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep<L, INIT, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the dynamic shared-memory limit is a per-device attribute: raised once per device; the
+    // occupancy (the same on every device of one kind) is queried with it
+    static PerDeviceOnce once;
+    static int blocks_per_sm = 0;
+    cudaError_t e = once([&] {
+        cudaError_t r = cudaFuncSetAttribute(k_sweep<L, INIT, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
-        if (e != cudaSuccess) return e;
         int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep<L, INIT, HB>, PA_SWEEP_THREADS, smem);
-        if (e != cudaSuccess) return e;
-        blocks_per_sm = b > 0 ? b : 1;
-    }
+        if (r == cudaSuccess)
+            r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep<L, INIT, HB>, sweep_threads(L), smem);
+        if (r == cudaSuccess) blocks_per_sm = b > 0 ? b : 1;
+        return r;
+    });
+    if (e != cudaSuccess) return e;
     const long long R = a.R_bound;
     const long long groups = (R + Geo<L>::RPW - 1) / Geo<L>::RPW;  // warps needed
-    long long blocks = (groups + kSweepWarps - 1) / kSweepWarps;
+    constexpr int kWarps = sweep_threads(L) / 32;
+    long long blocks = (groups + kWarps - 1) / kWarps;
     const long long cap = (long long)num_sms * blocks_per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_sweep<L, INIT, HB><<<(unsigned int)blocks, PA_SWEEP_THREADS, smem, s>>>(a);
+    k_sweep<L, INIT, HB><<<(unsigned int)blocks, sweep_threads(L), smem, s>>>(a);
     return cudaGetLastError();
 }
 
