@@ -62,6 +62,8 @@ def _parse_args():
                    help="skip the bounded 64-run batch figure of the default line")
     p.add_argument("--no-whole-anneal", action="store_true",
                    help="skip the whole-anneal end-to-end figure of the default line")
+    p.add_argument("--schedule-arm", choices=["plain", "rule", "learned"], default=None,
+                   help="only one whole anneal of the schedule comparison (L=128, R=2e5, seed 1), for profiling")
     p.add_argument("--parallel", choices=["independent", "shard"], default="independent",
                    help="N > 1 ranks: independent populations (default) or one population sharded over the "
                         "ranks by slot ranges")
@@ -676,10 +678,30 @@ def run_sharded(args):
         dist.destroy_process_group()
 
 
+def run_schedule_arm(args):
+    """One whole anneal of one arm of the schedule comparison (L=128, R=2e5, seed 1)."""
+    import torch
+
+    from paper_2102_06611_gb300 import PopulationAnnealing
+    from paper_2102_06611_gb300.learned import ScheduleMLP, anneal
+    from paper_2102_06611_gb300.train_schedule import DEFAULT_WEIGHTS
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    model = ScheduleMLP.load(DEFAULT_WEIGHTS, device=dev)
+    pa = PopulationAnnealing(SCHED_L, SCHED_R, SCHED_SEEDS[0], device=dev)
+    r = anneal(pa, args.schedule_arm, model)
+    pa.close()
+    print(json.dumps({"arm": args.schedule_arm, "L": SCHED_L, "R": SCHED_R, "seed": SCHED_SEEDS[0],
+                      **{k: r[k] for k in ("wall_s", "steps", "sweeps", "extensions", "fallbacks")}}), flush=True)
+
+
 def main():
     args = _parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.schedule_arm:
+        run_schedule_arm(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.parallel == "shard":
