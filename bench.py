@@ -91,8 +91,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 50):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
         self.path = None
 
@@ -101,7 +102,8 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms",
+                 str(self.interval_ms),
                  "-i", str(self.gpu)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -423,6 +425,9 @@ def whole_anneal_e2e(args, dev, stream, rank: int) -> dict:
     L, R, theta = args.L, args.R, args.theta
     N = L * L
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.2)
     t0 = time.perf_counter()
     pa = PopulationAnnealing(L, R, rank_seed(SEED, rank), device=dev, stream=stream, update=args.update,
                              resample=args.resample)
@@ -433,6 +438,7 @@ def whole_anneal_e2e(args, dev, stream, rank: int) -> dict:
         att += float(N) * pa.observables()["R"] * theta
     hist = pa.histogram()
     dt = time.perf_counter() - t0
+    clk = clocks.stop()
     assert int(hist.sum()) == pa.R
     pa.close()
     del pa
@@ -440,7 +446,7 @@ def whole_anneal_e2e(args, dev, stream, rank: int) -> dict:
     steps = N_TEMPS - 1
     return {"value": att / (dt * 1e9), "unit": UNIT, "wall_s": dt, "steps": steps,
             "h2d_bytes_per_step": 0, "d2h_bytes_per_step": ctypes.sizeof(pa_obs),
-            "d2h_bytes_final": 4 * (N + 1),
+            "d2h_bytes_final": 4 * (N + 1), "clocks": clk,
             "note": "host clock: buffers + pa_init (simple sampling on the GPU) + 300 x (pa_resample, "
                     "pa_anneal_step, pa_observables) + final histogram readback; the configuration and "
                     "beta pass by value, so no input array is copied"}

@@ -403,14 +403,19 @@ __device__ __forceinline__ void scan_body(const ResampleArgs &a)
 __global__ void __launch_bounds__(kScanThreads) k_scan(ResampleArgs a) { scan_body(a); }
 
 // ------------------------------------------------------------------------------ copy
-__device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
+// Block `blk` of kCountBlockItems parents; with nsub > 1 several blocks share it, block `part`
+// copying the children of parents [part, part + 1) x kCountBlockItems / nsub of it (each scans
+// the whole block's copy numbers for its offsets), for more parallelism when there are few
+// parent blocks (large replicas, small populations).
+__device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16, long long blk = blockIdx.x,
+                                          int part = 0, int nsub = 1)
 {
     __shared__ int sh_cnt[kCountBlockItems];
     __shared__ long long sh_off[kCountBlockItems];
     DevState *st = a.st;
     if (st->error) return;
     const long long Rp = st->R_prev;
-    const long long base = (long long)blockIdx.x * kCountBlockItems;
+    const long long base = blk * kCountBlockItems;
     if (base >= Rp) return;
     // thread t scans parents base + 4t .. base + 4t + 3
     int c[kCountItems];
@@ -422,7 +427,7 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
         local += c[it];
     }
     long long tot;
-    long long off = block_exclusive_scan<long long, kCountThreads>(local, &tot) + a.blocksum[blockIdx.x];
+    long long off = block_exclusive_scan<long long, kCountThreads>(local, &tot) + a.blocksum[blk];
 #pragma unroll
     for (int it = 0; it < kCountItems; ++it) {
         sh_cnt[threadIdx.x * kCountItems + it] = c[it];
@@ -433,7 +438,9 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint4 *src = reinterpret_cast<const uint4 *>(a.spins_src);
     uint4 *dst = reinterpret_cast<uint4 *>(a.spins_dst);
-    const int nloc = (int)min((long long)kCountBlockItems, Rp - base);
+    const int span = kCountBlockItems / nsub;
+    const int p_lo = part * span;
+    const int nloc = (int)min((long long)(p_lo + span), Rp - base);
     // children [k_lo, k_hi) of a parent whose children start at index o, written at o + k - shift
     const bool win = a.win_n > 0;
     const long long shift = win ? a.win_lo : 0;
@@ -447,7 +454,7 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
     };
     if (chunks16 >= 32) {
         // a warp per parent
-        for (int p = wid; p < nloc; p += kCountThreads / 32) {
+        for (int p = p_lo + wid; p < nloc; p += kCountThreads / 32) {
             const int cnt = sh_cnt[p];
             if (cnt == 0) continue;
             const long long j = base + p;
@@ -473,7 +480,7 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
     int gs = 0;
     while ((1 << gs) < chunks16) ++gs;
     const int S = 1 << gs, sub = lane >> gs, li = lane & (S - 1), per_warp = 32 >> gs;
-    for (int p0 = wid * per_warp; p0 < nloc; p0 += (kCountThreads / 32) * per_warp) {
+    for (int p0 = p_lo + wid * per_warp; p0 < nloc; p0 += (kCountThreads / 32) * per_warp) {
         const int p = p0 + sub;
         if (p >= nloc) continue;
         const int cnt = sh_cnt[p];
@@ -496,7 +503,14 @@ __device__ __forceinline__ void copy_body(const ResampleArgs &a, int chunks16)
     }
 }
 
-__global__ void __launch_bounds__(kCountThreads) k_copy(ResampleArgs a, int chunks16) { copy_body(a, chunks16); }
+__global__ void __launch_bounds__(kCountThreads) k_copy(ResampleArgs a, int chunks16, int nsub)
+{
+    copy_body(a, chunks16, blockIdx.x / nsub, (int)(blockIdx.x % nsub), nsub);
+}
+
+// Blocks sharing one block of parents: more when there are few parent blocks (up to ~8 blocks
+// of 256 threads per SM of a 152-SM GPU).
+static int copy_split(long long nblk) { return nblk <= 304 ? 4 : (nblk <= 608 ? 2 : 1); }
 
 // k_table's dynamic shared-memory limit (up to 16385 doubles), raised once per device
 static PerDeviceOnce table_smem_once;
@@ -530,7 +544,8 @@ cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
     k_scan<<<1, kScanThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int chunks16 = bytes_per_replica(a.L) / 16;
-    k_copy<<<nblk, kCountThreads, 0, s>>>(a, chunks16);
+    const int nsub = copy_split(a.nblk);
+    k_copy<<<nblk * (unsigned int)nsub, kCountThreads, 0, s>>>(a, chunks16, nsub);
     return cudaGetLastError();
 }
 
@@ -539,7 +554,8 @@ cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
 cudaError_t launch_copy(const ResampleArgs &a, cudaStream_t s)
 {
     const int chunks16 = bytes_per_replica(a.L) / 16;
-    k_copy<<<(unsigned int)a.nblk, kCountThreads, 0, s>>>(a, chunks16);
+    const int nsub = copy_split(a.nblk);
+    k_copy<<<(unsigned int)a.nblk * (unsigned int)nsub, kCountThreads, 0, s>>>(a, chunks16, nsub);
     return cudaGetLastError();
 }
 
