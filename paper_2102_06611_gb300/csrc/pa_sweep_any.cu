@@ -31,7 +31,18 @@ namespace {
 
 using u64 = unsigned long long;
 
-constexpr int kAnyWarps = 8;  // warps per block
+// Block shape (build knobs): PA_ANY_WARPS warps per block, at least PA_ANY_MIN_BLOCKS
+// resident blocks per SM.  16 warps (so at most 128 registers) was measured best: 20-35 %
+// faster than 8 warps with the registers unbounded (which the compiler then took above 128,
+// halving the resident warps) and 3-7 % faster than 8 warps in two blocks per SM, except at
+// L = 6 (-6 %).
+#ifndef PA_ANY_WARPS
+#define PA_ANY_WARPS 16
+#endif
+#ifndef PA_ANY_MIN_BLOCKS
+#define PA_ANY_MIN_BLOCKS 1
+#endif
+constexpr int kAnyWarps = PA_ANY_WARPS;  // warps per block
 
 // Class thresholds T_a, a = 0..4 aligned neighbours, split into top 8 and low 24 bits;
 // always has bit a set iff T_a = 2^32 (every site of class a flips).  Metropolis only needs
@@ -318,7 +329,7 @@ __device__ void init_any(u64 *S, const AnyGeo &g, unsigned int slot, unsigned in
 }
 
 template <bool INIT>
-__global__ void __launch_bounds__(32 * kAnyWarps) k_sweep_any(SweepArgs a, int L)
+__global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_sweep_any(SweepArgs a, int L)
 {
     const AnyGeo g = any_geo(L);
     extern __shared__ u64 sh_dyn[];
