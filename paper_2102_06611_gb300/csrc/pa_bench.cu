@@ -1,9 +1,13 @@
 // pa_bench.cu -- a measurement kernel, not a step of the method: Philox4x32-10 calls alone
-// (Salmon, Moraes, Dror and Shaw, SC'11), written exactly as the sweep draws its bit planes
-// (precomputed round keys, the same round code), with the four output words XOR-reduced per
-// thread so that nothing but the generator's arithmetic is timed.  Two calls give the 8 bit
-// planes of 32 Metropolis attempts, so 16 x the call rate is the rate at which the sweep
-// could run if it did nothing but draw its random numbers.
+// (Salmon, Moraes, Dror and Shaw, SC'11) with the sweep's round function (precomputed round
+// keys, the 64-bit products as separate low and high multiplies) and, as in the sweep, calls
+// that differ only in counter word 0; the four output words are XOR-reduced per thread so
+// that nothing but the generator's arithmetic is timed.  Two calls give the 8 bit planes of 32
+// Metropolis attempts, so 16 x the call rate is the rate at which the sweep could run if it did
+// nothing but draw its random numbers.  Of the two ways to write these calls this is the
+// faster alone (about 500 calls/ns on a GB300, the compiler hoisting the product that does not
+// depend on word 0); the sweep's explicit sharing of rounds 1 and 2 (philox_c0, faster inside
+// the sweep) runs at about 364 calls/ns here, so the rate reported is the higher ceiling.
 #include "pa_sweep.cuh"
 
 namespace pa {
