@@ -79,11 +79,33 @@ struct PhiloxC0 {
     unsigned int u1k;  // u1 ^ (round-2 key word 0)
 };
 
+// Philox4x32-10 with the round keys precomputed (rk[i] = k + i W).
 template <bool SPLIT = (PA_MULHI_SPLIT != 0)>
+__device__ __forceinline__ uint4 philox_rk_t(uint4 c, const unsigned int *rk0, const unsigned int *rk1)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        unsigned int hi0, lo0, hi1, lo1;
+        mulhilo<SPLIT>(kPhiloxM0, c.x, hi0, lo0);
+        mulhilo<SPLIT>(kPhiloxM1, c.z, hi1, lo1);
+        c = make_uint4(hi1 ^ c.y ^ rk0[i], lo1, hi0 ^ c.w ^ rk1[i], lo0);
+    }
+    return c;
+}
+
+// RK: the calls written as plain rounds instead (the compiler then finds the shared part
+// itself); faster at some sizes, slower at others (SweepStyle::PLANE_RK, measured).
+template <bool SPLIT = (PA_MULHI_SPLIT != 0), bool RK = false>
 __device__ __forceinline__ PhiloxC0 philox_c0_setup(unsigned int c1, unsigned int c2, unsigned int c3,
                                                     const unsigned int *rk0, const unsigned int *rk1)
 {
     PhiloxC0 p;
+    if constexpr (RK) {
+        p.u0 = c1;
+        p.u1 = c2;
+        p.u2 = c3;
+        return p;
+    }
     unsigned int h1, l1;
     mulhilo<SPLIT>(kPhiloxM1, c2, h1, l1);
     p.u0 = h1 ^ c1 ^ rk0[0];
@@ -94,10 +116,11 @@ __device__ __forceinline__ PhiloxC0 philox_c0_setup(unsigned int c1, unsigned in
     return p;
 }
 
-template <bool SPLIT = (PA_MULHI_SPLIT != 0)>
+template <bool SPLIT = (PA_MULHI_SPLIT != 0), bool RK = false>
 __device__ __forceinline__ uint4 philox_c0(unsigned int c0, const PhiloxC0 &p, const unsigned int *rk0,
                                            const unsigned int *rk1)
 {
+    if constexpr (RK) return philox_rk_t<SPLIT>(make_uint4(c0, p.u0, p.u1, p.u2), rk0, rk1);
     unsigned int hi0, lo0;
     mulhilo<SPLIT>(kPhiloxM0, c0, hi0, lo0);
     // round 1: (u0, u1, hi0 ^ c3 ^ k1, lo0); round 2 with the shared M0 * u0
@@ -115,17 +138,9 @@ __device__ __forceinline__ uint4 philox_c0(unsigned int c0, const PhiloxC0 &p, c
     return c;
 }
 
-// Philox4x32-10 with the round keys precomputed (rk[i] = k + i W).
 __device__ __forceinline__ uint4 philox_rk(uint4 c, const unsigned int *rk0, const unsigned int *rk1)
 {
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        unsigned int hi0, lo0, hi1, lo1;
-        mulhilo(kPhiloxM0, c.x, hi0, lo0);
-        mulhilo(kPhiloxM1, c.z, hi1, lo1);
-        c = make_uint4(hi1 ^ c.y ^ rk0[i], lo1, hi0 ^ c.w ^ rk1[i], lo0);
-    }
-    return c;
+    return philox_rk_t<>(c, rk0, rk1);
 }
 
 // Load / store the RPL rows of one lane as (A, B) pairs: A_r = half (r & 1) of row r (the
@@ -240,6 +255,9 @@ struct SweepStyle {
     // Philox products of the bit planes as separate low/high multiplies (faster from L = 32
     // up, measured) or one widening multiply
     static constexpr bool SPLIT_MUL = (PA_MULHI_SPLIT != 0) && L >= 32;
+    // bit-plane calls as plain rounds (philox_c0's RK): +2 % at L = 32, +1.4 % at L = 64, within
+    // 1 % at L = 8, 16, 24, 48 and -2.6 % at L = 128 (measured)
+    static constexpr bool PLANE_RK = (L == 32 || L == 64);
 };
 
 
@@ -498,7 +516,8 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
     const W from_down = __shfl_sync(0xffffffffu, O[0], gbase | ((q + 1) & (G - 1)));
 
     // the plane stream's calls differ only in c0 (rounds 1 and 2 partly shared)
-    const PhiloxC0 pc = philox_c0_setup(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
+    constexpr bool SM = SweepStyle<L>::SPLIT_MUL, RK = SweepStyle<L>::PLANE_RK;
+    const PhiloxC0 pc = philox_c0_setup<SM, RK>(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
 
     // Metropolis: lt = decided accepts, g3 = sites with a >= 3; heatbath: lt = flip, g3 = clow
     W lt[RPL], eq[RPL], a4[RPL], g3[RPL];
@@ -517,15 +536,15 @@ __device__ __forceinline__ void half_sweep(typename Geo<L>::W *A, typename Geo<L
         // bit planes of the top 8 bits of every site's uniform
         W plane[8];
         if constexpr (NH == 1) {
-            const uint4 p0 = philox_c0((unsigned int)(2 * r), pc, rk0, rk1);
-            const uint4 p1 = philox_c0((unsigned int)(2 * r + 1), pc, rk0, rk1);
+            const uint4 p0 = philox_c0<SM, RK>((unsigned int)(2 * r), pc, rk0, rk1);
+            const uint4 p1 = philox_c0<SM, RK>((unsigned int)(2 * r + 1), pc, rk0, rk1);
             plane[0] = p0.x; plane[1] = p0.y; plane[2] = p0.z; plane[3] = p0.w;
             plane[4] = p1.x; plane[5] = p1.y; plane[6] = p1.z; plane[7] = p1.w;
         } else {
-            const uint4 a0 = philox_c0((unsigned int)(4 * r), pc, rk0, rk1);
-            const uint4 a1 = philox_c0((unsigned int)(4 * r + 1), pc, rk0, rk1);
-            const uint4 b0 = philox_c0((unsigned int)(4 * r + 2), pc, rk0, rk1);
-            const uint4 b1 = philox_c0((unsigned int)(4 * r + 3), pc, rk0, rk1);
+            const uint4 a0 = philox_c0<SM, RK>((unsigned int)(4 * r), pc, rk0, rk1);
+            const uint4 a1 = philox_c0<SM, RK>((unsigned int)(4 * r + 1), pc, rk0, rk1);
+            const uint4 b0 = philox_c0<SM, RK>((unsigned int)(4 * r + 2), pc, rk0, rk1);
+            const uint4 b1 = philox_c0<SM, RK>((unsigned int)(4 * r + 3), pc, rk0, rk1);
             const unsigned int lo[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const unsigned int hi[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -615,14 +634,14 @@ __device__ __forceinline__ void packed_planes(int r0, unsigned int slot, unsigne
                                               unsigned int (*plane)[8])
 {
     using Gm = Geo<L>;
-    constexpr bool SM = SweepStyle<L>::SPLIT_MUL;
-    const PhiloxC0 pc = philox_c0_setup<SM>(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
+    constexpr bool SM = SweepStyle<L>::SPLIT_MUL, RK = SweepStyle<L>::PLANE_RK;
+    const PhiloxC0 pc = philox_c0_setup<SM, RK>(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
     const unsigned int chunk0 = (unsigned int)(r0 / Gm::P);
 #pragma unroll
     for (int c = 0; c < Gm::C; ++c) {
         const unsigned int ch = chunk0 + (unsigned int)c;
-        const uint4 p0 = philox_c0<SM>(2 * ch, pc, rk0, rk1);
-        const uint4 p1 = philox_c0<SM>(2 * ch + 1, pc, rk0, rk1);
+        const uint4 p0 = philox_c0<SM, RK>(2 * ch, pc, rk0, rk1);
+        const uint4 p1 = philox_c0<SM, RK>(2 * ch + 1, pc, rk0, rk1);
         plane[c][0] = p0.x; plane[c][1] = p0.y; plane[c][2] = p0.z; plane[c][3] = p0.w;
         plane[c][4] = p1.x; plane[c][5] = p1.y; plane[c][6] = p1.z; plane[c][7] = p1.w;
     }
@@ -668,7 +687,8 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
 
     PhiloxC0 pc;
     if constexpr (!PRE)
-        pc = philox_c0_setup<SweepStyle<L>::SPLIT_MUL>(slot, (kStreamSweep << 28) | tag, step, rk0, rk1);
+        pc = philox_c0_setup<SweepStyle<L>::SPLIT_MUL, SweepStyle<L>::PLANE_RK>(slot, (kStreamSweep << 28) | tag,
+                                                                                 step, rk0, rk1);
 
     unsigned int lt[C], eq[C], a4[C], g3[C];
 #pragma unroll
@@ -699,8 +719,8 @@ __device__ __forceinline__ void packed_update(unsigned int *PA, unsigned int *PB
             for (int k = 0; k < 8; ++k) pl[k] = plane[c][k];
         } else {
             const unsigned int ch = (unsigned int)(r0 / P + c);
-            const uint4 p0 = philox_c0<SweepStyle<L>::SPLIT_MUL>(2 * ch, pc, rk0, rk1);
-            const uint4 p1 = philox_c0<SweepStyle<L>::SPLIT_MUL>(2 * ch + 1, pc, rk0, rk1);
+            const uint4 p0 = philox_c0<SweepStyle<L>::SPLIT_MUL, SweepStyle<L>::PLANE_RK>(2 * ch, pc, rk0, rk1);
+            const uint4 p1 = philox_c0<SweepStyle<L>::SPLIT_MUL, SweepStyle<L>::PLANE_RK>(2 * ch + 1, pc, rk0, rk1);
             pl[0] = p0.x; pl[1] = p0.y; pl[2] = p0.z; pl[3] = p0.w;
             pl[4] = p1.x; pl[5] = p1.y; pl[6] = p1.z; pl[7] = p1.w;
         }
