@@ -125,3 +125,41 @@ def test_shard_call_order_is_enforced():
         e.copy_children(0, 1, e.views(0, 1))   # likewise
     e.anneal_step(1)
     e.close()
+
+
+def test_sharded_population_through_nccl_transport_one_rank():
+    """The torch.distributed transport on this GPU: one NCCL rank holding 3 shards (summaries
+    and children counts all-gathered by NCCL, children moved by direct copies), bit-identical
+    to the whole population for a few steps."""
+    import os
+    import socket
+
+    import torch.distributed as dist
+
+    from paper_2102_06611_gb300.shard import DistTransport, ShardedRun, gpu_shards
+
+    if dist.is_initialized():
+        pytest.skip("a process group is already initialised")
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        L, R, seed, P, theta = 16, 2001, 5, 3, 3
+        engines = gpu_shards(L, R, seed, list(range(P)), P)
+        run = ShardedRun(engines, P, DistTransport(shards_per_rank=P))
+        whole = _whole(L, R, seed, "nearest", "metropolis")
+        _check_step(run, engines, whole, None, False)
+        for b in (0.2, 0.4, 0.6):
+            run.resample(b)
+            whole.resample(b)
+            run.anneal_step(theta)
+            whole.anneal_step(theta)
+            _check_step(run, engines, whole, None, True)
+        for e in engines.values():
+            e.close()
+        whole.close()
+    finally:
+        dist.destroy_process_group()
