@@ -83,7 +83,7 @@ typedef struct {
     long long R;                 /* target population size R (Eq. taus) */
     long long capacity;          /* replicas each buffer can hold (>= R) */
     unsigned long long seed;     /* Philox key */
-    int update;                  /* pa_update_kind (batches: Metropolis only) */
+    int update;                  /* pa_update_kind */
     int pad;                     /* 0 */
 } pa_config;
 

@@ -21,11 +21,14 @@ class RunSpec:
     theta: int
     resample: str = "nearest"
     capacity: int | None = None
+    update: str = "metropolis"
 
     def desc(self) -> _lib.pa_run_desc:
         cap = self.capacity if self.capacity is not None else default_capacity(self.R)
         kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON}[self.resample]
-        return _lib.pa_run_desc(_lib.pa_config(L=self.L, resample=kind, R=self.R, capacity=cap, seed=self.seed),
+        upd = {"metropolis": _lib.PA_UPDATE_METROPOLIS, "heatbath": _lib.PA_UPDATE_HEATBATH}[self.update]
+        return _lib.pa_run_desc(_lib.pa_config(L=self.L, resample=kind, R=self.R, capacity=cap, seed=self.seed,
+                                               update=upd),
                                 self.n_temps, self.theta)
 
 

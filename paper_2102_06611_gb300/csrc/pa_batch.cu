@@ -89,7 +89,8 @@ Tables layout_tables(int n)
 bool valid_desc(const pa_run_desc &d)
 {
     return batch_supported_L(d.cfg.L) && d.cfg.R >= 1 && d.cfg.capacity >= d.cfg.R &&
-           d.cfg.capacity <= 2147483647LL && d.cfg.update == PA_UPDATE_METROPOLIS && d.cfg.pad == 0 &&
+           d.cfg.capacity <= 2147483647LL && d.cfg.pad == 0 &&
+           (d.cfg.update == PA_UPDATE_METROPOLIS || d.cfg.update == PA_UPDATE_HEATBATH) &&
            (d.cfg.resample == PA_RESAMPLE_NEAREST ||
                                               d.cfg.resample == PA_RESAMPLE_POISSON) &&
            d.n_temps >= 2 && d.theta >= 0 && d.theta <= (1 << 26);
@@ -267,6 +268,7 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
             s.k0 = k0;
             s.k1 = k1;
             s.theta = d.theta;
+            s.update = d.cfg.update;
             pa::ObsArgs &o = r.obs[cur];
             o.L = d.cfg.L;
             o.R_target = d.cfg.R;
@@ -283,7 +285,7 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
         state[(size_t)i].beta_prev = 0.0;
         // step 1 (simple sampling at beta_0 = 0) and the first measurement
         e = pa::launch_setup(st, d.cfg.R, reinterpret_cast<int *>(work + L.ws.hist), d.cfg.L * d.cfg.L,
-                             PA_UPDATE_METROPOLIS, b->user);
+                             d.cfg.update, b->user);
         if (e == cudaSuccess) {
             pa::SweepArgs s = r.sw[0];
             s.R_init = d.cfg.R;

@@ -23,10 +23,23 @@ namespace pa {
 // ordered by cost within a size).  The per-replica arithmetic
 // is exactly the single-run kernel's, with the histogram and sums going to the run's own
 // workspace: level counts aggregated over the warp, the seven exact sums once per item.
-template <int L>
+// A warp's tie queue in the kernel's dynamic shared memory (inv: heatbath only).
+struct TqBuf {
+    unsigned long long *eq, *a4, *inv;
+    unsigned int *code;
+};
+
+template <int L, bool HB>
+__device__ __forceinline__ TieQueue<typename Geo<L>::W> tie_queue(const TqBuf &qb)
+{
+    using W = typename Geo<L>::W;
+    return TieQueue<W>{reinterpret_cast<W *>(qb.eq), reinterpret_cast<W *>(qb.a4),
+                       HB ? reinterpret_cast<W *>(qb.inv) : nullptr, qb.code};
+}
+
+template <int L, bool HB>
 __device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
-                                            unsigned long long *tq_eq, unsigned long long *tq_a4,
-                                            unsigned int *tq_code, const unsigned int *rk0, const unsigned int *rk1,
+                                            const TqBuf &qb, const unsigned int *rk0, const unsigned int *rk1,
                                             unsigned long long *v)
 {
     using Gm = Geo<L>;
@@ -46,8 +59,8 @@ __device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spar
 #pragma unroll
         for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
     }
-    const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), nullptr, tq_code};
-    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, ac, tq);
+    const TieQueue<W> tq = tie_queue<L, HB>(qb);
+    sweep_rows<L, HB>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, ac, tq);
     int anti, ups;
     measure_rows<L>(A, B, r0, lane, anti, ups);
     anti = group_sum<G>(anti);
@@ -87,10 +100,9 @@ __device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spar
 
 // Items of one group (ipw = 1) take this form, which nvcc compiles to faster code for them
 // than the general loop below (measured).
-template <int L>
+template <int L, bool HB>
 __device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
-                                           unsigned long long *tq_eq, unsigned long long *tq_a4,
-                                           unsigned int *tq_code)
+                                                  const TqBuf &qb)
 {
     using Gm = Geo<L>;
     using W = typename Gm::W;
@@ -115,8 +127,8 @@ __device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void
 #pragma unroll
         for (int i = 0; i < RPL; ++i) { A[i] = 0; B[i] = 0; }
     }
-    const TieQueue<W> tq{reinterpret_cast<W *>(tq_eq), reinterpret_cast<W *>(tq_a4), nullptr, tq_code};
-    sweep_rows<L, false>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, ac, tq);
+    const TieQueue<W> tq = tie_queue<L, HB>(qb);
+    sweep_rows<L, HB>(A, B, r0, lane, (unsigned int)j, (unsigned int)(g * RPW), 0, a.theta, a.step, rk0, rk1, ac, tq);
     int anti, ups;
     measure_rows<L>(A, B, r0, lane, anti, ups);
     anti = group_sum<G>(anti);
@@ -160,14 +172,13 @@ __device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void
     }
 }
 
-template <int L>
+template <int L, bool HB>
 __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare, long long item, int ipw, int lane,
-                                           int dry, unsigned long long *tq_eq, unsigned long long *tq_a4,
-                                           unsigned int *tq_code)
+                                           int dry, const TqBuf &qb)
 {
     constexpr int RPW = Geo<L>::RPW;
     if (ipw == 1) {  // uniform over the warp
-        batch_item_single<L>(a, spare, item, lane, dry, tq_eq, tq_a4, tq_code);
+        batch_item_single<L, HB>(a, spare, item, lane, dry, qb);
         return;
     }
     unsigned int rk0[10], rk1[10];
@@ -182,7 +193,7 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
     for (int k = 0; k < ipw; ++k) {
         const long long g = item * ipw + k;
         if (g * RPW >= R) break;  // uniform over the warp
-        batch_group<L>(a, spare, g, lane, dry, tq_eq, tq_a4, tq_code, rk0, rk1, v);
+        batch_group<L, HB>(a, spare, g, lane, dry, qb, rk0, rk1, v);
     }
     // every replica of the item belongs to one run: one atomic per sum and item
 #pragma unroll
@@ -198,6 +209,30 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
     }
 }
 
+// The run's spin update decides the instantiation (uniform over the warp).
+template <int L>
+__device__ __forceinline__ void batch_item_update(const SweepArgs &a, const void *spare, long long item, int ipw,
+                                                  int lane, int dry, const TqBuf &qb)
+{
+    if (a.update == PA_UPDATE_HEATBATH) batch_item<L, true>(a, spare, item, ipw, lane, dry, qb);
+    else batch_item<L, false>(a, spare, item, ipw, lane, dry, qb);
+}
+
+// Tie queues of the kBatchWarps warps of a block of a kernel with TQ entries per warp:
+// eq, a4, inv (8-byte entries) and code (4-byte entries), in dynamic shared memory.
+constexpr size_t tq_smem_bytes(int TQ) { return (size_t)kBatchWarps * TQ * (3 * 8 + 4); }
+
+__device__ __forceinline__ TqBuf warp_tq(unsigned long long *sh, int TQ)
+{
+    const int wib = threadIdx.x >> 5;
+    TqBuf qb;
+    qb.eq = sh + (size_t)wib * TQ;
+    qb.a4 = sh + (size_t)kBatchWarps * TQ + (size_t)wib * TQ;
+    qb.inv = sh + (size_t)2 * kBatchWarps * TQ + (size_t)wib * TQ;
+    qb.code = reinterpret_cast<unsigned int *>(sh + (size_t)3 * kBatchWarps * TQ) + (size_t)wib * TQ;
+    return qb;
+}
+
 // Persistent sweep over the work items of the runs with lattice size L (group g): warps
 // take items from the group's counter; the item's run is found by bisection over the
 // group's order positions.
@@ -208,12 +243,8 @@ __global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_swe
     constexpr int g = batch_group_of(L);
     const int lane = threadIdx.x & 31;
     const int dry = ctl->dry;
-    constexpr int TQ = SweepStyle<L>::TQ_LEN;  // per warp
-    __shared__ unsigned long long tq_eq[kBatchWarps * TQ], tq_a4[kBatchWarps * TQ];
-    __shared__ unsigned int tq_code[kBatchWarps * TQ];
-    const int wib = threadIdx.x >> 5;
-    unsigned long long *qe = tq_eq + wib * TQ, *qa = tq_a4 + wib * TQ;
-    unsigned int *qc = tq_code + wib * TQ;
+    extern __shared__ unsigned long long sh_tq[];
+    const TqBuf qb = warp_tq(sh_tq, SweepStyle<L>::TQ_LEN);
     const long long end = ctl->end[g];
     const int p0 = ctl->pbeg[g], p1 = ctl->pend[g];
     for (;;) {
@@ -235,7 +266,7 @@ __global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_swe
         a.t0 = 0;
         a.theta = run.theta;
         const void *spare = run.sw[s.cur ^ 1].spins;
-        batch_item<L>(a, spare, item - item_start[lo], run.ipw, lane, dry, qe, qa, qc);
+        batch_item_update<L>(a, spare, item - item_start[lo], run.ipw, lane, dry, qb);
     }
 }
 
@@ -243,7 +274,13 @@ template <int L>
 static cudaError_t launch_b_sweep_t(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
                                     const long long *item_start, int grid, cudaStream_t s)
 {
-    k_b_sweep<L><<<grid, PA_BATCH_THREADS, 0, s>>>(runs, state, ctl, order, item_start);
+    constexpr size_t smem = tq_smem_bytes(SweepStyle<L>::TQ_LEN);
+    static PerDeviceOnce once;
+    cudaError_t e = once([] {
+        return cudaFuncSetAttribute(k_b_sweep<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
+    k_b_sweep<L><<<grid, PA_BATCH_THREADS, smem, s>>>(runs, state, ctl, order, item_start);
     return cudaGetLastError();
 }
 
@@ -272,12 +309,8 @@ __global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_swe
 {
     const int lane = threadIdx.x & 31;
     const int dry = ctl->dry;
-    constexpr int TQ = tq_len_max();  // per warp
-    __shared__ unsigned long long tq_eq[kBatchWarps * TQ], tq_a4[kBatchWarps * TQ];
-    __shared__ unsigned int tq_code[kBatchWarps * TQ];
-    const int wib = threadIdx.x >> 5;
-    unsigned long long *qe = tq_eq + wib * TQ, *qa = tq_a4 + wib * TQ;
-    unsigned int *qc = tq_code + wib * TQ;
+    extern __shared__ unsigned long long sh_tq[];
+    const TqBuf qb = warp_tq(sh_tq, tq_len_max());
     const long long end = ctl->total_items;
     for (;;) {
         long long item = 0;
@@ -300,15 +333,15 @@ __global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_swe
         const void *spare = run.sw[s.cur ^ 1].spins;
         const long long it = item - item_start[lo];
         switch (run.L) {
-            case 4: batch_item<4>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
-            case 8: batch_item<8>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
-            case 12: batch_item<12>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
-            case 16: batch_item<16>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
-            case 24: batch_item<24>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
-            case 32: batch_item<32>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
-            case 48: batch_item<48>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
-            case 64: batch_item<64>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
-            case 128: batch_item<128>(a, spare, it, run.ipw, lane, dry, qe, qa, qc); break;
+            case 4: batch_item_update<4>(a, spare, it, run.ipw, lane, dry, qb); break;
+            case 8: batch_item_update<8>(a, spare, it, run.ipw, lane, dry, qb); break;
+            case 12: batch_item_update<12>(a, spare, it, run.ipw, lane, dry, qb); break;
+            case 16: batch_item_update<16>(a, spare, it, run.ipw, lane, dry, qb); break;
+            case 24: batch_item_update<24>(a, spare, it, run.ipw, lane, dry, qb); break;
+            case 32: batch_item_update<32>(a, spare, it, run.ipw, lane, dry, qb); break;
+            case 48: batch_item_update<48>(a, spare, it, run.ipw, lane, dry, qb); break;
+            case 64: batch_item_update<64>(a, spare, it, run.ipw, lane, dry, qb); break;
+            case 128: batch_item_update<128>(a, spare, it, run.ipw, lane, dry, qb); break;
             default: break;
         }
     }
@@ -318,7 +351,13 @@ cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, Ba
                                const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s)
 {
     if (plan.unified) {
-        k_b_sweep_all<<<plan.grid_all, PA_BATCH_THREADS, 0, s>>>(runs, state, ctl, order, item_start, plan.n);
+        constexpr size_t smem = tq_smem_bytes(tq_len_max());
+        static PerDeviceOnce once;
+        cudaError_t e = once([] {
+            return cudaFuncSetAttribute(k_b_sweep_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        if (e != cudaSuccess) return e;
+        k_b_sweep_all<<<plan.grid_all, PA_BATCH_THREADS, smem, s>>>(runs, state, ctl, order, item_start, plan.n);
         return cudaGetLastError();
     }
     cudaError_t e = cudaEventRecord(plan.fork, s);
@@ -346,16 +385,22 @@ cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, Ba
 template <int L>
 static int b_sweep_occupancy()
 {
+    constexpr size_t smem = tq_smem_bytes(SweepStyle<L>::TQ_LEN);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep<L>, PA_BATCH_THREADS, 0) != cudaSuccess) return 1;
+    if (cudaFuncSetAttribute(k_b_sweep<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep<L>, PA_BATCH_THREADS, smem) != cudaSuccess)
+        return 1;
     return b > 0 ? b : 1;
 }
 
 int batch_sweep_max_blocks_per_sm(int L)
 {
     if (L == 0) {  // the kernel over every size
+        constexpr size_t smem = tq_smem_bytes(tq_len_max());
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep_all, PA_BATCH_THREADS, 0) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_b_sweep_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep_all, PA_BATCH_THREADS, smem) != cudaSuccess)
+            return 1;
         return b > 0 ? b : 1;
     }
     switch (L) {

@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 
 def _single(spec):
     from paper_2102_06611_gb300 import PopulationAnnealing
-    pa = PopulationAnnealing(spec.L, spec.R, spec.seed, resample=spec.resample, capacity=spec.capacity)
+    pa = PopulationAnnealing(spec.L, spec.R, spec.seed, resample=spec.resample, capacity=spec.capacity,
+                             update=spec.update)
     for i in range(1, spec.n_temps):
         pa.resample(i / (spec.n_temps - 1))
         pa.anneal_step(spec.theta)
@@ -62,6 +63,41 @@ def test_mixed_batch_matches_single_runs(shape):
     if shape is None:
         assert t["chosen"] in t["candidates"] and t["chosen"]["ms"] == min(c["ms"] for c in t["candidates"])
         assert {c["unified"] for c in t["candidates"]} == {0, 1}
+
+
+HEATBATH_MIX = [
+    # L, R, seed, n_temps, theta, resample, update
+    (64, 500, 31, 6, 3, "nearest", "heatbath"),
+    (64, 600, 32, 5, 2, "nearest", "metropolis"),
+    (16, 1500, 33, 8, 4, "poisson", "heatbath"),
+    (32, 700, 34, 7, 1, "nearest", "heatbath"),
+    (8, 900, 35, 9, 5, "nearest", "metropolis"),
+    (128, 30, 36, 4, 2, "nearest", "heatbath"),
+    (12, 800, 37, 5, 3, "nearest", "heatbath"),
+]
+
+
+@pytest.mark.parametrize("shape", [None, (1, 1, 1)])
+def test_batch_with_heatbath_runs_matches_single_runs(shape):
+    """Heatbath (Sec. IV) and Metropolis runs in one batch, each bit-identical to its single
+    run, with the per-size launches and with the launch over every size."""
+    from paper_2102_06611_gb300.batch import Batch, RunSpec
+    specs = [RunSpec(L, R, seed, nT, th, kind, update=u) for (L, R, seed, nT, th, kind, u) in HEATBATH_MIX]
+    b = Batch(specs)
+    if shape is not None:
+        b.set_shape(*shape)
+    b.run_to_end()
+    active, status, step = b.status()
+    assert not active.any() and not status.any()
+    recs = b.observables()
+    for i, s in enumerate(specs):
+        pa = _single(s)
+        assert np.array_equal(b.hashes(i), pa.hashes()), i
+        o = pa.observables()
+        for k in ("step", "R", "lnQ", "minus_betaF", "sum_E", "sum_E2", "sum_absM", "sum_M2", "families"):
+            assert recs[i][k] == o[k], (i, k, recs[i][k], o[k])
+        pa.close()
+    b.close()
 
 
 def test_batch_run_against_oracle():
