@@ -25,7 +25,8 @@ class RunSpec:
 
     def desc(self) -> _lib.pa_run_desc:
         cap = self.capacity if self.capacity is not None else default_capacity(self.R)
-        kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON}[self.resample]
+        kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON,
+                "multinomial": _lib.PA_RESAMPLE_MULTINOMIAL}[self.resample]
         upd = {"metropolis": _lib.PA_UPDATE_METROPOLIS, "heatbath": _lib.PA_UPDATE_HEATBATH}[self.update]
         return _lib.pa_run_desc(_lib.pa_config(L=self.L, resample=kind, R=self.R, capacity=cap, seed=self.seed,
                                                update=upd),

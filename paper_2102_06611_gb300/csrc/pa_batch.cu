@@ -91,8 +91,8 @@ bool valid_desc(const pa_run_desc &d)
     return batch_supported_L(d.cfg.L) && d.cfg.R >= 1 && d.cfg.capacity >= d.cfg.R &&
            d.cfg.capacity <= 2147483647LL && d.cfg.pad == 0 &&
            (d.cfg.update == PA_UPDATE_METROPOLIS || d.cfg.update == PA_UPDATE_HEATBATH) &&
-           (d.cfg.resample == PA_RESAMPLE_NEAREST ||
-                                              d.cfg.resample == PA_RESAMPLE_POISSON) &&
+           (d.cfg.resample == PA_RESAMPLE_NEAREST || d.cfg.resample == PA_RESAMPLE_POISSON ||
+            d.cfg.resample == PA_RESAMPLE_MULTINOMIAL) &&
            d.n_temps >= 2 && d.theta >= 0 && d.theta <= (1 << 26);
 }
 
@@ -115,6 +115,7 @@ struct pa_batch {
     pa::BatchSweepPlan plan;
     std::vector<pa::BatchRun> table;  // host copy of the run table
     int occ[pa::kBatchGroups], occ_all, max_bps;
+    int mn_draw_blocks;               // grid of the multinomial draws (0: no multinomial run)
 };
 
 namespace {
@@ -143,7 +144,7 @@ cudaError_t capture_step(pa_batch *b)
             reinterpret_cast<const pa::BatchRun *>(tb + b->t.runs), reinterpret_cast<pa::BatchState *>(tb + b->t.state),
             reinterpret_cast<pa::BatchCtl *>(tb + b->t.ctl), reinterpret_cast<const int *>(tb + b->t.order),
             reinterpret_cast<long long *>(tb + b->t.item_start), reinterpret_cast<pa_obs *>(tb + b->t.records), b->n,
-            b->nblk_max, b->nlev_max, b->plan, b->cs);
+            b->nblk_max, b->nlev_max, b->mn_draw_blocks, b->plan, b->cs);
         e = cudaStreamEndCapture(b->cs, &b->graph);
         if (le != cudaSuccess) e = le;
     }
@@ -196,6 +197,12 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     size_t off = b->t.end;
     b->nblk_max = 1;
     b->nlev_max = 1;
+    b->mn_draw_blocks = 0;
+    for (int i = 0; i < n_runs; ++i)
+        if (runs[i].cfg.resample == PA_RESAMPLE_MULTINOMIAL) {
+            const long long blocks = (runs[i].cfg.R + 255) / 256;
+            b->mn_draw_blocks = (int)std::max<long long>(b->mn_draw_blocks, std::min<long long>(blocks, 4096));
+        }
     for (int i = 0; i < n_runs; ++i) {
         b->lay.push_back(layout_run(runs[i], off));
         off = b->lay.back().end;
@@ -248,6 +255,8 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
             a.counts = reinterpret_cast<int *>(work + L.ws.counts);
             a.blocksum = reinterpret_cast<long long *>(work + L.ws.blocksum);
             a.nblk = L.ws.nblk;
+            a.wint = reinterpret_cast<unsigned long long *>(work + L.ws.wint);
+            a.cdf = reinterpret_cast<unsigned long long *>(work + L.ws.cdf);
             a.spins_src = base + L.spins[cur];
             a.spins_dst = base + L.spins[nxt];
             a.level_src = reinterpret_cast<const int *>(base + L.level[cur]);

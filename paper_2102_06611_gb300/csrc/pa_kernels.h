@@ -280,7 +280,7 @@ struct BatchSweepPlan {
 };
 
 cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
-                              long long *item_start, pa_obs *records, int n, int nblk_max, int nlev_max,
+                              long long *item_start, pa_obs *records, int n, int nblk_max, int nlev_max, int mn_draw_blocks,
                               const BatchSweepPlan &plan, cudaStream_t s);
 cudaError_t launch_batch_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
                                long long *item_start, int n, int dry, cudaStream_t s);

@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kCountThreads) k_counts(ResampleArgs a) { coun
 //   k_mn_draw   child c: X = Philox words 1:0, U = floor(X T / 2^64), parent = first j with
 //               C_j > U (binary search), counts[j] += 1
 //   k_mn_csum   per-block sums of the counts, for k_scan and k_copy
-__global__ void __launch_bounds__(kCountThreads) k_mn_wsum(ResampleArgs a)
+__device__ __forceinline__ void mn_wsum_body(const ResampleArgs &a)
 {
     if (a.st->error) return;
     const long long Rp = a.st->R_prev;
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kCountThreads) k_mn_wsum(ResampleArgs a)
     if (threadIdx.x == 0) a.blocksum[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(1024) k_mn_wscan(ResampleArgs a)
+__device__ __forceinline__ void mn_wscan_body(const ResampleArgs &a)
 {
     DevState *st = a.st;
     if (st->error) return;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(1024) k_mn_wscan(ResampleArgs a)
     if (threadIdx.x == 0) st->mn_total = (unsigned long long)carry;
 }
 
-__global__ void __launch_bounds__(kCountThreads) k_mn_cdf(ResampleArgs a)
+__device__ __forceinline__ void mn_cdf_body(const ResampleArgs &a)
 {
     if (a.st->error) return;
     const long long Rp = a.st->R_prev;
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kCountThreads) k_mn_cdf(ResampleArgs a)
     }
 }
 
-__global__ void __launch_bounds__(kCountThreads) k_mn_draw(ResampleArgs a)
+__device__ __forceinline__ void mn_draw_body(const ResampleArgs &a)
 {
     const DevState *st = a.st;
     if (st->error) return;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kCountThreads) k_mn_draw(ResampleArgs a)
     }
 }
 
-__global__ void __launch_bounds__(kCountThreads) k_mn_csum(ResampleArgs a)
+__device__ __forceinline__ void mn_csum_body(const ResampleArgs &a)
 {
     if (a.st->error) return;
     const long long Rp = a.st->R_prev;
@@ -373,6 +373,12 @@ __global__ void __launch_bounds__(kCountThreads) k_mn_csum(ResampleArgs a)
     const long long t = block_sum<long long, kCountThreads>(sum);
     if (threadIdx.x == 0) a.blocksum[blockIdx.x] = t;
 }
+
+__global__ void __launch_bounds__(kCountThreads) k_mn_wsum(ResampleArgs a) { mn_wsum_body(a); }
+__global__ void __launch_bounds__(1024) k_mn_wscan(ResampleArgs a) { mn_wscan_body(a); }
+__global__ void __launch_bounds__(kCountThreads) k_mn_cdf(ResampleArgs a) { mn_cdf_body(a); }
+__global__ void __launch_bounds__(kCountThreads) k_mn_draw(ResampleArgs a) { mn_draw_body(a); }
+__global__ void __launch_bounds__(kCountThreads) k_mn_csum(ResampleArgs a) { mn_csum_body(a); }
 
 // ------------------------------------------------------------------------------ scan
 constexpr int kScanThreads = 1024;
@@ -737,8 +743,43 @@ __global__ void __launch_bounds__(kTableThreads) k_b_table(const BatchRun *runs,
 __global__ void __launch_bounds__(kCountThreads) k_b_counts(const BatchRun *runs, const BatchState *state)
 {
     const BatchState s = state[blockIdx.y];
-    if (!s.active || blockIdx.x >= runs[blockIdx.y].rs[0].nblk) return;
+    if (!s.active || blockIdx.x >= runs[blockIdx.y].rs[0].nblk ||
+        runs[blockIdx.y].rs[0].kind == PA_RESAMPLE_MULTINOMIAL)
+        return;
     counts_body(batch_resample_args(runs[blockIdx.y], s));
+}
+
+// Multinomial resampling of the batch's multinomial runs (the single-run kernels' bodies).
+__device__ __forceinline__ bool b_mn_run(const BatchRun *runs, const BatchState *state, bool per_block)
+{
+    const BatchState &s = state[blockIdx.y];
+    return s.active && runs[blockIdx.y].rs[0].kind == PA_RESAMPLE_MULTINOMIAL &&
+           (!per_block || blockIdx.x < runs[blockIdx.y].rs[0].nblk);
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_b_mn_wsum(const BatchRun *runs, const BatchState *state)
+{
+    if (b_mn_run(runs, state, true)) mn_wsum_body(batch_resample_args(runs[blockIdx.y], state[blockIdx.y]));
+}
+
+__global__ void __launch_bounds__(1024) k_b_mn_wscan(const BatchRun *runs, const BatchState *state)
+{
+    if (b_mn_run(runs, state, false)) mn_wscan_body(batch_resample_args(runs[blockIdx.y], state[blockIdx.y]));
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_b_mn_cdf(const BatchRun *runs, const BatchState *state)
+{
+    if (b_mn_run(runs, state, true)) mn_cdf_body(batch_resample_args(runs[blockIdx.y], state[blockIdx.y]));
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_b_mn_draw(const BatchRun *runs, const BatchState *state)
+{
+    if (b_mn_run(runs, state, false)) mn_draw_body(batch_resample_args(runs[blockIdx.y], state[blockIdx.y]));
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_b_mn_csum(const BatchRun *runs, const BatchState *state)
+{
+    if (b_mn_run(runs, state, true)) mn_csum_body(batch_resample_args(runs[blockIdx.y], state[blockIdx.y]));
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_b_scan(const BatchRun *runs, const BatchState *state)
@@ -850,7 +891,7 @@ cudaError_t launch_batch_record(const BatchRun *runs, BatchState *state, pa_obs 
 
 cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
                               long long *item_start, pa_obs *records, int n, int nblk_max, int nlev_max,
-                              const BatchSweepPlan &plan, cudaStream_t s)
+                              int mn_draw_blocks, const BatchSweepPlan &plan, cudaStream_t s)
 {
     {
         static PerDeviceOnce once;
@@ -867,6 +908,14 @@ cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_b_counts<<<dim3(nblk_max, n), kCountThreads, 0, s>>>(runs, state);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (mn_draw_blocks > 0) {
+        k_b_mn_wsum<<<dim3(nblk_max, n), kCountThreads, 0, s>>>(runs, state);
+        k_b_mn_wscan<<<dim3(1, n), 1024, 0, s>>>(runs, state);
+        k_b_mn_cdf<<<dim3(nblk_max, n), kCountThreads, 0, s>>>(runs, state);
+        k_b_mn_draw<<<dim3(mn_draw_blocks, n), kCountThreads, 0, s>>>(runs, state);
+        k_b_mn_csum<<<dim3(nblk_max, n), kCountThreads, 0, s>>>(runs, state);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     k_b_scan<<<dim3(1, n), kScanThreads, 0, s>>>(runs, state);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_b_copy<<<dim3(nblk_max, n), kCountThreads, 0, s>>>(runs, state);

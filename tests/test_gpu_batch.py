@@ -68,19 +68,21 @@ def test_mixed_batch_matches_single_runs(shape):
 HEATBATH_MIX = [
     # L, R, seed, n_temps, theta, resample, update
     (64, 500, 31, 6, 3, "nearest", "heatbath"),
-    (64, 600, 32, 5, 2, "nearest", "metropolis"),
+    (64, 600, 32, 5, 2, "multinomial", "metropolis"),
     (16, 1500, 33, 8, 4, "poisson", "heatbath"),
     (32, 700, 34, 7, 1, "nearest", "heatbath"),
-    (8, 900, 35, 9, 5, "nearest", "metropolis"),
+    (8, 900, 35, 9, 5, "multinomial", "metropolis"),
     (128, 30, 36, 4, 2, "nearest", "heatbath"),
-    (12, 800, 37, 5, 3, "nearest", "heatbath"),
+    (12, 800, 37, 5, 3, "multinomial", "heatbath"),
+    (24, 2500, 38, 6, 2, "nearest", "metropolis"),
 ]
 
 
 @pytest.mark.parametrize("shape", [None, (1, 1, 1)])
-def test_batch_with_heatbath_runs_matches_single_runs(shape):
-    """Heatbath (Sec. IV) and Metropolis runs in one batch, each bit-identical to its single
-    run, with the per-size launches and with the launch over every size."""
+def test_batch_with_heatbath_and_multinomial_runs_matches_single_runs(shape):
+    """Heatbath (Sec. IV) and Metropolis runs, with nearest-integer, Poisson and fixed-size
+    multinomial resampling (Sec. II), in one batch: each bit-identical to its single run, with
+    the per-size launches and with the launch over every size."""
     from paper_2102_06611_gb300.batch import Batch, RunSpec
     specs = [RunSpec(L, R, seed, nT, th, kind, update=u) for (L, R, seed, nT, th, kind, u) in HEATBATH_MIX]
     b = Batch(specs)
