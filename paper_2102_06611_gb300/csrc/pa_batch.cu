@@ -17,18 +17,15 @@
 
 namespace {
 
-bool batch_supported_L(int L)
-{
-    switch (L) {
-        case 4: case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 128: return true;
-        default: return false;
-    }
-}
+bool batch_supported_L(int L) { return L >= 4 && L <= 128 && (L % 2) == 0; }
+
+bool register_L(int L) { return pa::batch_group_of(L) != pa::kBatchAnyGroup; }
 
 int rpw_for(int L)
 {
-    // replicas per work item: 32 / (lanes per replica); lanes per replica = L / rows per lane
-    return 32 / (L / pa::rows_per_lane(L));
+    // replicas per replica group: 32 / (lanes per replica), lanes per replica = L / rows per lane
+    // (register kernels); the replicas of one warp pass of the shared-memory sweep otherwise
+    return register_L(L) ? 32 / (L / pa::rows_per_lane(L)) : pa::any_replicas_per_pass(L);
 }
 
 // Replica groups per work item: runs whose groups are small (below 2^14 attempts: small L or
@@ -126,7 +123,8 @@ cudaError_t apply_shape(pa_batch *b, int unified, int bps, int scale)
 {
     b->plan.unified = unified;
     b->plan.grid_all = b->num_sms * std::min(bps, b->occ_all);
-    for (int i = 0; i < b->plan.ngroups; ++i) b->plan.grid[i] = b->num_sms * std::min(bps, b->occ[i]);
+    for (int i = 0; i < b->plan.ngroups; ++i)
+        b->plan.grid[i] = register_L(b->plan.L[i]) ? b->num_sms * std::min(bps, b->occ[i]) : b->plan.any_grid;
     for (int i = 0; i < b->n; ++i)
         b->table[(size_t)i].ipw = std::min(16, ipw_for(b->desc[(size_t)i].cfg.L, b->desc[(size_t)i].theta) * scale);
     b->sweep_grid = unified ? b->plan.grid_all : b->num_sms * std::min(bps, b->max_bps);
@@ -362,9 +360,23 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     // or one per size, persistent blocks per SM (each kernel capped by its occupancy), and
     // replica groups per work item (the default count, or twice it)
     b->max_bps = 1;
+    b->plan.any_present = 0;
+    b->plan.any_kw = 0;
+    for (int i = 0; i < n_runs; ++i)
+        if (!register_L(runs[i].cfg.L)) {
+            b->plan.any_present = 1;
+            b->plan.any_kw = std::max(b->plan.any_kw, pa::any_warp_words(runs[i].cfg.L));
+        }
+    int any_occ = 1;
+    if (b->plan.any_present) {
+        const size_t smem = pa::batch_any_smem(b->plan.any_kw);
+        if (e == cudaSuccess) e = pa::prepare_batch_sweep_any(smem);
+        any_occ = pa::batch_any_blocks_per_sm(smem);
+        b->plan.any_grid = b->num_sms * any_occ;
+    }
     for (int i = 0; i < b->plan.ngroups; ++i) {
-        b->occ[i] = pa::batch_sweep_max_blocks_per_sm(b->plan.L[i]);
-        b->max_bps = std::max(b->max_bps, b->occ[i]);
+        b->occ[i] = register_L(b->plan.L[i]) ? pa::batch_sweep_max_blocks_per_sm(b->plan.L[i]) : any_occ;
+        if (register_L(b->plan.L[i])) b->max_bps = std::max(b->max_bps, b->occ[i]);
     }
     b->occ_all = pa::batch_sweep_max_blocks_per_sm(0);
     b->plan.n = n_runs;

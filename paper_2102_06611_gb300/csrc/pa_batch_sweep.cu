@@ -358,7 +358,11 @@ cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, Ba
         });
         if (e != cudaSuccess) return e;
         k_b_sweep_all<<<plan.grid_all, PA_BATCH_THREADS, smem, s>>>(runs, state, ctl, order, item_start, plan.n);
-        return cudaGetLastError();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // the runs without a register kernel (skipped above) by their own persistent sweep
+        if (plan.any_present)
+            e = launch_batch_sweep_any(runs, state, ctl, order, item_start, plan.any_grid, plan.any_kw, s);
+        return e;
     }
     cudaError_t e = cudaEventRecord(plan.fork, s);
     for (int i = 0; i < plan.ngroups && e == cudaSuccess; ++i) {
@@ -374,7 +378,9 @@ cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, Ba
             case 48: e = launch_b_sweep_t<48>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
             case 64: e = launch_b_sweep_t<64>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
             case 128: e = launch_b_sweep_t<128>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            default: e = cudaErrorInvalidValue; break;
+            default:  // the group of every even L without a register kernel
+                e = launch_batch_sweep_any(runs, state, ctl, order, item_start, plan.grid[i], plan.any_kw, t);
+                break;
         }
         if (e == cudaSuccess) e = cudaEventRecord(plan.join[i], t);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan.join[i], 0);

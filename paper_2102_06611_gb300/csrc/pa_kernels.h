@@ -248,11 +248,14 @@ struct BatchState {       // per run, mutable
 };
 
 // Lattice sizes of batches, one persistent sweep kernel each.
-constexpr int kBatchGroups = 9;
+// Lattice-size groups of a batch: one per size with a register sweep kernel, and one for
+// every other even L (the shared-memory sweep).
+constexpr int kBatchGroups = 10;
+constexpr int kBatchAnyGroup = kBatchGroups - 1;
 __host__ __device__ constexpr int batch_group_of(int L)
 {
     return L == 4 ? 0 : L == 8 ? 1 : L == 12 ? 2 : L == 16 ? 3 : L == 24 ? 4 : L == 32 ? 5 : L == 48 ? 6
-           : L == 64 ? 7 : L == 128 ? 8 : -1;
+           : L == 64 ? 7 : L == 128 ? 8 : kBatchAnyGroup;
 }
 
 struct BatchCtl {
@@ -277,6 +280,8 @@ struct BatchSweepPlan {
     cudaEvent_t fork, join[kBatchGroups];
     // one launch over every size (k_b_sweep_all, grid_all blocks) instead of one per size
     int unified, grid_all, n;
+    // the runs without a register kernel (group kBatchAnyGroup): present, warp staging words
+    int any_present, any_kw, any_grid;
 };
 
 cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
@@ -289,6 +294,18 @@ cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, Ba
 cudaError_t launch_batch_record(const BatchRun *runs, BatchState *state, pa_obs *records, int n,
                                 cudaStream_t s);
 int batch_sweep_max_blocks_per_sm(int L);
+
+// Batched shared-memory sweep (pa_sweep_any.cu) for the runs whose L has no register kernel:
+// replicas per warp pass, the staging words a warp needs for L, dynamic shared memory per block
+// for a largest warp need of max_kw words (the limit is raised by prepare_batch_sweep_any, to
+// be called before any capture), resident blocks per SM, and the persistent launch.
+int any_replicas_per_pass(int L);
+int any_warp_words(int L);
+size_t batch_any_smem(int max_kw);
+cudaError_t prepare_batch_sweep_any(size_t smem);
+int batch_any_blocks_per_sm(size_t smem);
+cudaError_t launch_batch_sweep_any(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
+                                   const long long *item_start, int grid, int max_kw, cudaStream_t s);
 
 cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
                           unsigned long long *out, cudaStream_t s);

@@ -328,16 +328,96 @@ __device__ void init_any(u64 *S, const AnyGeo &g, unsigned int slot, unsigned in
     }
 }
 
+// One pass of a warp over the k replicas [base, base + k) of a population of R replicas
+// (replica j = base + sub staged in S, the warp's k replicas in Sw): simple sampling (INIT) or
+// a load, the theta sweeps, the measurement, the store; the level, magnetisation (and family
+// id) of each replica are written.  The group's first lane of an active replica returns its
+// level and fills v with its seven exact sums (|M|, M^2, k0, k0^2, k1, k1^2, k0 k1); others
+// return -1.
+template <bool INIT>
+__device__ __forceinline__ int any_pass(const SweepArgs &a, const AnyGeo &g, int L, long long R, long long base,
+                                        u64 *Sw, const ClassThr &th, unsigned long long *v)
+{
+    const int N = L * L, W2 = 2 * L;  // words per replica
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / g.Gc, c0 = lane % g.Gc;  // replica within the warp, lane within its group
+    u64 *S = Sw + sub * W2;
+    const int KW = g.k * W2;  // words of the warp's replicas
+    const long long j = base + sub;
+    const bool active = j < R;
+    const unsigned int slot = (unsigned int)j + a.slot_base;  // global replica slot
+    // the warp's k replicas are consecutive in HBM; slots past R read as zero
+    if (INIT) {
+        init_any(S, g, slot, a.k0, a.k1, c0);
+    } else if (g.wide) {
+        const u64 *src = reinterpret_cast<const u64 *>(a.spins) + (size_t)base * W2;
+        for (int w = lane; w < KW; w += 32) Sw[w] = (base + w / W2 < R) ? src[w] : 0ull;
+    } else {
+        const unsigned int *src = reinterpret_cast<const unsigned int *>(a.spins) + (size_t)base * W2;
+        for (int w = lane; w < KW; w += 32) Sw[w] = (base + w / W2 < R) ? src[w] : 0u;
+    }
+    __syncwarp();
+    for (int t = 0; t < a.theta; ++t)
+        for (int q = 0; q < 2; ++q) {
+            const unsigned int tag = (unsigned int)(2 * (a.t0 + t) + q);
+            if (g.wide) half_sweep_rows(S, g, q, slot, tag, a.step, a.k0, a.k1, th, c0);
+            else half_sweep_chunks(S, g, q, slot, tag, a.step, a.k0, a.k1, th, c0);
+            __syncwarp();
+        }
+    // measurement: antiparallel bonds (row r: (2p, 2p+1), (2p+1, 2p+2); column: r, r+1)
+    int anti = 0, ups = 0;
+    for (int r = c0; r < L; r += g.Gc) {
+        const int rn = (r == L - 1) ? 0 : r + 1;
+        const u64 E = S[2 * r], O = S[2 * r + 1];
+        const u64 En = ((E >> 1) | (E << (g.H - 1))) & g.hmask;
+        anti += __popcll(E ^ O) + __popcll(O ^ En) + __popcll(E ^ S[2 * rn]) + __popcll(O ^ S[2 * rn + 1]);
+        ups += __popcll(E) + __popcll(O);
+    }
+    for (int o = g.Gc / 2; o > 0; o >>= 1) {  // sum over the replica's lane group
+        anti += __shfl_xor_sync(0xffffffffu, anti, o);
+        ups += __shfl_xor_sync(0xffffffffu, ups, o);
+    }
+    if (INIT || a.theta > 0) {
+        if (g.wide) {
+            u64 *dst = reinterpret_cast<u64 *>(a.spins) + (size_t)base * W2;
+            for (int w = lane; w < KW; w += 32)
+                if (base + w / W2 < R) dst[w] = Sw[w];
+        } else {
+            unsigned int *dst = reinterpret_cast<unsigned int *>(a.spins) + (size_t)base * W2;
+            for (int w = lane; w < KW; w += 32)
+                if (base + w / W2 < R) dst[w] = (unsigned int)Sw[w];
+        }
+    }
+    __syncwarp();  // the stores have read S before the next replicas overwrite it
+    if (c0 != 0 || !active) return -1;
+    const int level = anti >> 1;
+    const int M = 2 * ups - N;
+    v[0] = (unsigned long long)(M < 0 ? -M : M);
+    v[1] = (unsigned long long)((long long)M * M);
+    for (int i = 2; i < 7; ++i) v[i] = 0;
+    if (!INIT) {
+        const unsigned long long k0 = (unsigned long long)(a.t0 == 0 ? a.level[j] : a.level_snap[j]);
+        const unsigned long long k1 = (unsigned long long)level;
+        if (a.t0 == 0) a.level_snap[j] = (int)k0;
+        v[2] = k0;
+        v[3] = k0 * k0;
+        v[4] = k1;
+        v[5] = k1 * k1;
+        v[6] = k0 * k1;
+    }
+    a.level[j] = level;
+    a.mag[j] = M;
+    if (INIT) a.fam[j] = (int)slot;
+    return level;
+}
+
 template <bool INIT>
 __global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_sweep_any(SweepArgs a, int L)
 {
     const AnyGeo g = any_geo(L);
     extern __shared__ u64 sh_dyn[];
     const int N = L * L, W2 = 2 * L;  // words per replica
-    const int lane = threadIdx.x & 31;
-    const int sub = lane / g.Gc, c0 = lane % g.Gc;  // replica within the warp, lane within its group
     u64 *Sw = sh_dyn + (size_t)(threadIdx.x >> 5) * g.k * W2;  // the warp's k replicas
-    u64 *S = Sw + sub * W2;
     int *sh_hist = reinterpret_cast<int *>(sh_dyn + (size_t)kAnyWarps * g.k * W2);
     __shared__ unsigned long long sh_sum[7];
     for (int k = threadIdx.x; k <= N; k += blockDim.x) sh_hist[k] = 0;
@@ -350,78 +430,15 @@ __global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_sweep_any
     const ClassThr th = class_thresholds(a.update, a.T4, a.T8);
     if (!INIT && blockIdx.x == 0 && threadIdx.x == 0 && (a.T4 != a.st->T4 || a.T8 != a.st->T8))
         set_error(a.st, PA_ERR_NUMERIC);  // host and device thresholds disagree (never expected)
-    const int KW = g.k * W2;  // words of the warp's replicas
 
     for (long long base = warp * g.k; base < R; base += nwarps * g.k) {
-        const long long j = base + sub;
-        const bool active = j < R;
-        const unsigned int slot = (unsigned int)j + a.slot_base;  // global replica slot
-        // the warp's k replicas are consecutive in HBM; slots past R read as zero
-        if (INIT) {
-            init_any(S, g, slot, a.k0, a.k1, c0);
-        } else if (g.wide) {
-            const u64 *src = reinterpret_cast<const u64 *>(a.spins) + (size_t)base * W2;
-            for (int w = lane; w < KW; w += 32) Sw[w] = (base + w / W2 < R) ? src[w] : 0ull;
-        } else {
-            const unsigned int *src = reinterpret_cast<const unsigned int *>(a.spins) + (size_t)base * W2;
-            for (int w = lane; w < KW; w += 32) Sw[w] = (base + w / W2 < R) ? src[w] : 0u;
-        }
-        __syncwarp();
-        for (int t = 0; t < a.theta; ++t)
-            for (int q = 0; q < 2; ++q) {
-                const unsigned int tag = (unsigned int)(2 * (a.t0 + t) + q);
-                if (g.wide) half_sweep_rows(S, g, q, slot, tag, a.step, a.k0, a.k1, th, c0);
-                else half_sweep_chunks(S, g, q, slot, tag, a.step, a.k0, a.k1, th, c0);
-                __syncwarp();
-            }
-        // measurement: antiparallel bonds (row r: (2p, 2p+1), (2p+1, 2p+2); column: r, r+1)
-        int anti = 0, ups = 0;
-        for (int r = c0; r < L; r += g.Gc) {
-            const int rn = (r == L - 1) ? 0 : r + 1;
-            const u64 E = S[2 * r], O = S[2 * r + 1];
-            const u64 En = ((E >> 1) | (E << (g.H - 1))) & g.hmask;
-            anti += __popcll(E ^ O) + __popcll(O ^ En) + __popcll(E ^ S[2 * rn]) + __popcll(O ^ S[2 * rn + 1]);
-            ups += __popcll(E) + __popcll(O);
-        }
-        for (int o = g.Gc / 2; o > 0; o >>= 1) {  // sum over the replica's lane group
-            anti += __shfl_xor_sync(0xffffffffu, anti, o);
-            ups += __shfl_xor_sync(0xffffffffu, ups, o);
-        }
-        if (INIT || a.theta > 0) {
-            if (g.wide) {
-                u64 *dst = reinterpret_cast<u64 *>(a.spins) + (size_t)base * W2;
-                for (int w = lane; w < KW; w += 32)
-                    if (base + w / W2 < R) dst[w] = Sw[w];
-            } else {
-                unsigned int *dst = reinterpret_cast<unsigned int *>(a.spins) + (size_t)base * W2;
-                for (int w = lane; w < KW; w += 32)
-                    if (base + w / W2 < R) dst[w] = (unsigned int)Sw[w];
-            }
-        }
-        __syncwarp();  // the stores have read S before the next replicas overwrite it
-        if (c0 == 0 && active) {
-            const int level = anti >> 1;
-            const int M = 2 * ups - N;
-            unsigned long long v[7] = {(unsigned long long)(M < 0 ? -M : M), (unsigned long long)((long long)M * M),
-                                       0, 0, 0, 0, 0};
-            if (!INIT) {
-                const unsigned long long k0 = (unsigned long long)(a.t0 == 0 ? a.level[j] : a.level_snap[j]);
-                const unsigned long long k1 = (unsigned long long)level;
-                if (a.t0 == 0) a.level_snap[j] = (int)k0;
-                v[2] = k0;
-                v[3] = k0 * k0;
-                v[4] = k1;
-                v[5] = k1 * k1;
-                v[6] = k0 * k1;
-            }
-            a.level[j] = level;
-            a.mag[j] = M;
-            if (INIT) a.fam[j] = (int)slot;
+        unsigned long long v[7];
+        const int level = any_pass<INIT>(a, g, L, R, base, Sw, th, v);
+        if (level >= 0) {
             atomicAdd(&sh_hist[level], 1);
             for (int i = 0; i < (INIT ? 2 : 7); ++i) atomicAdd(&sh_sum[i], v[i]);
         }
     }
-
     __syncthreads();
     if (threadIdx.x == 0) {
         atomicAdd(&a.st->sum_absM, sh_sum[0]);
@@ -437,6 +454,70 @@ __global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_sweep_any
     for (int k = threadIdx.x; k <= N; k += blockDim.x) {
         const int v = sh_hist[k];
         if (v) atomicAdd(&a.hist[k], v);
+    }
+}
+
+// Batched form: a persistent sweep over the work items of the batch's runs without a register
+// kernel (group kBatchAnyGroup); an item is ipw warp passes (k replicas each) of one run, whose
+// thresholds come from its device state; levels go to the run's histogram, the seven sums once
+// per item.  Dry (autotuning) launches do nothing.
+__global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_b_sweep_any(const BatchRun *runs,
+                                                                                const BatchState *state,
+                                                                                BatchCtl *ctl, const int *order,
+                                                                                const long long *item_start,
+                                                                                int max_kw)
+{
+    extern __shared__ u64 sh_dyn[];
+    if (ctl->dry) return;
+    const int lane = threadIdx.x & 31;
+    u64 *Sw = sh_dyn + (size_t)(threadIdx.x >> 5) * max_kw;
+    const long long end = ctl->end[kBatchAnyGroup];
+    const int p0 = ctl->pbeg[kBatchAnyGroup], p1 = ctl->pend[kBatchAnyGroup];
+    for (;;) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(&ctl->next[kBatchAnyGroup], 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= end) break;
+        int lo = p0, hi = p1;  // largest lo with item_start[lo] <= item
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (item_start[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int r = order[lo];
+        const BatchState s = state[r];
+        const BatchRun &run = runs[r];
+        SweepArgs a = run.sw[s.cur];
+        a.step = (unsigned int)s.step;
+        a.t0 = 0;
+        a.theta = run.theta;
+        const int L = run.L;
+        const AnyGeo g = any_geo(L);
+        const ClassThr th = class_thresholds(a.update, a.st->T4, a.st->T8);
+        const long long R = a.st->R_cur;
+        const long long it = item - item_start[lo];
+        unsigned long long acc[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < run.ipw; ++k) {
+            const long long base = (it * run.ipw + k) * g.k;
+            if (base >= R) break;  // uniform over the warp
+            unsigned long long v[7];
+            const int level = any_pass<false>(a, g, L, R, base, Sw, th, v);
+            if (level >= 0) {
+                atomicAdd(&a.hist[level], 1);
+                for (int i = 0; i < 7; ++i) acc[i] += v[i];
+            }
+        }
+        for (int i = 0; i < 7; ++i)
+            for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+        if (lane == 0) {
+            atomicAdd(&a.st->sum_absM, acc[0]);
+            atomicAdd(&a.st->sum_M2, acc[1]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c0), acc[2]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c00), acc[3]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c1), acc[4]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c11), acc[5]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st->c01), acc[6]);
+        }
     }
 }
 
@@ -471,6 +552,29 @@ cudaError_t launch_any_t(int L, const SweepArgs &a, int num_sms, cudaStream_t s)
 }
 
 }  // namespace
+
+int any_replicas_per_pass(int L) { return any_geo(L).k; }
+int any_warp_words(int L) { return any_geo(L).k * 2 * L; }
+size_t batch_any_smem(int max_kw) { return (size_t)kAnyWarps * max_kw * sizeof(u64); }
+
+cudaError_t prepare_batch_sweep_any(size_t smem)
+{
+    return cudaFuncSetAttribute(k_b_sweep_any, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int batch_any_blocks_per_sm(size_t smem)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_b_sweep_any, 32 * kAnyWarps, smem) != cudaSuccess) return 1;
+    return b > 0 ? b : 1;
+}
+
+cudaError_t launch_batch_sweep_any(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
+                                   const long long *item_start, int grid, int max_kw, cudaStream_t s)
+{
+    k_b_sweep_any<<<grid, 32 * kAnyWarps, batch_any_smem(max_kw), s>>>(runs, state, ctl, order, item_start, max_kw);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sweep_any(int L, bool init, const SweepArgs &a, int num_sms, cudaStream_t s)
 {

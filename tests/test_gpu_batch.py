@@ -151,3 +151,61 @@ def test_full_mixed_batch_first_steps_match_single_runs():
             assert recs[i][key] == o[key], (i, key)
         pa.close()
     b.close()
+
+
+def test_full_mixed_batch_runs_against_oracle():
+    """The 64-run mixed workload at full size: after three batched temperature steps, eight of
+    its runs (every lattice size present but 64, small enough to replay) agree with the CPU
+    oracle's own runs -- spin hashes bit for bit, observables to 1e-12."""
+    from paper_2102_06611_gb300.batch import Batch, mixed_runs
+    specs = mixed_runs()
+    b = Batch(specs)
+    k = 3
+    for _ in range(k):
+        b.step()
+    recs = b.observables()
+    for i in (0, 2, 7, 14, 27, 40, 46, 63):
+        s = specs[i]
+        ref = oracle.PA(s.L, s.R, s.seed)
+        ref.init()
+        for j in range(1, k + 1):
+            assert ref.resample(j / (s.n_temps - 1)) == 0
+            ref.sweep(s.theta)
+        assert np.array_equal(b.hashes(i), ref.hashes()), (i, s)
+        assert_obs_close(recs[i], ref.observables(), f"run {i}")
+    b.close()
+
+
+ANY_L_MIX = [
+    # L, R, seed, n_temps, theta, resample, update: sizes without a register sweep kernel
+    (6, 3000, 41, 7, 3, "nearest", "metropolis"),
+    (10, 1200, 42, 6, 2, "poisson", "heatbath"),
+    (20, 900, 43, 5, 4, "nearest", "metropolis"),
+    (40, 400, 44, 6, 1, "multinomial", "metropolis"),
+    (100, 60, 45, 4, 2, "nearest", "heatbath"),
+    (64, 500, 46, 5, 2, "nearest", "metropolis"),
+    (16, 800, 47, 8, 3, "nearest", "metropolis"),
+]
+
+
+@pytest.mark.parametrize("shape", [None, (1, 1, 1)])
+def test_batch_with_every_even_L_matches_single_runs(shape):
+    """Runs of even L without a register kernel (the shared-memory sweep, batched) beside
+    register sizes in one batch, each bit-identical to its single run."""
+    from paper_2102_06611_gb300.batch import Batch, RunSpec
+    specs = [RunSpec(L, R, seed, nT, th, kind, update=u) for (L, R, seed, nT, th, kind, u) in ANY_L_MIX]
+    b = Batch(specs)
+    if shape is not None:
+        b.set_shape(*shape)
+    b.run_to_end()
+    active, status, step = b.status()
+    assert not active.any() and not status.any()
+    recs = b.observables()
+    for i, s in enumerate(specs):
+        pa = _single(s)
+        assert np.array_equal(b.hashes(i), pa.hashes()), i
+        o = pa.observables()
+        for k in ("step", "R", "lnQ", "minus_betaF", "sum_E", "sum_E2", "sum_absM", "sum_M2", "families", "theta"):
+            assert recs[i][k] == o[k], (i, k, recs[i][k], o[k])
+        pa.close()
+    b.close()
