@@ -246,7 +246,11 @@ __device__ __forceinline__ void init_rows(unsigned int slot, int r0, unsigned in
 // ------------------------------------------------------------------------------------
 template <int L>
 struct SweepStyle {
-    static constexpr bool XNOR = (L == 24 || L == 32 || L == 48 || L == 64);
+    // neighbour classes by the pair-mask form at every size: with one block of 512 threads per
+    // SM and plain-round plane calls it measured +8 % (L = 24), +7 % (48), +3 % (64), +2 % (32)
+    // against the XNOR form there and equal elsewhere (the XNOR form had been the faster at
+    // L = 24 - 64 with two blocks of 256)
+    static constexpr bool XNOR = false;
     // ties resolved through the warp's queue (below) when a lane holds 3 or more words;
     // with 1 or 2 words the lane's own loop is cheaper (measured)
     static constexpr int WORDS = Geo<L>::PACK ? Geo<L>::C : Geo<L>::RPL;
