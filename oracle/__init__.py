@@ -100,7 +100,7 @@ def lib():
                 "orc_resample_shard": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_int64,
                                                       ctypes.c_int64, i32p, ctypes.c_int64, ctypes.c_double,
                                                       ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64,
-                                                      ctypes.c_int, i32p, P(_Info)]),
+                                                      ctypes.c_int, i64p, i32p, P(_Info)]),
                 "orc_observables_from_sums": (None, [ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_double,
                                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_double, ctypes.c_uint32, ctypes.c_int, dp]),
@@ -243,16 +243,21 @@ def resample_levels(L, R_target, levels, beta_prev, beta_new, step, seed, kind, 
     return st, counts, info.lnQ, info.S, info.kmin, info.R_new
 
 
-def resample_shard(L, R_target, hist, R_prev, levels, parent_base, beta_prev, beta_new, step, seed, kind):
+def resample_shard(L, R_target, hist, R_prev, levels, parent_base, beta_prev, beta_new, step, seed, kind,
+                   hist_before=None):
     """Step 2 for the parents of one shard of a population split by slot ranges: tables from
     the whole population's histogram `hist` (R_prev parents), copy numbers of the local parents
-    keyed by their global index parent_base + j.  Returns (status, counts, lnQ, R_new_local)."""
+    keyed by their global index parent_base + j.  Multinomial resampling also needs
+    `hist_before`, the level histogram of the parents below parent_base.  Returns (status,
+    counts, lnQ, R_new_local)."""
     h = np.ascontiguousarray(hist, dtype=np.int64)
     lv = np.ascontiguousarray(levels, dtype=np.int32)
+    hb = None if hist_before is None else np.ascontiguousarray(hist_before, dtype=np.int64)
     counts = np.zeros(len(lv), dtype=np.int32)
     info = _Info()
     st = lib().orc_resample_shard(L, R_target, _ptr(h, ctypes.c_int64), R_prev, len(lv), _ptr(lv, ctypes.c_int32),
                                   parent_base, float(beta_prev), float(beta_new), step, seed, kind,
+                                  None if hb is None else _ptr(hb, ctypes.c_int64),
                                   _ptr(counts, ctypes.c_int32), ctypes.byref(info))
     return st, counts, info.lnQ, info.R_new
 

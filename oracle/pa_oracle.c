@@ -496,13 +496,22 @@ int orc_resample_levels(int L, int64_t R_target, int64_t R_prev, const int32_t *
    population of R_prev parents, so the tables (and ln Q_i) are those of the whole
    population, and local parent j has the global index parent_base + j, which keys its
    random numbers.  Every shard thus draws the numbers one unsplit population would draw.
-   Nearest-integer (kind 0) and Poisson (kind 1) only: multinomial draws need all parents'
-   weights.  info->R_new = this shard's children; 6 for an empty histogram, 1 for kind 2. */
+   Nearest-integer (kind 0) and Poisson (kind 1) need nothing else.  Multinomial (kind 2)
+   also needs h_before, the level histogram of the parents at global indices below
+   parent_base (the shards before this one): with the integer weights W_k of the whole
+   population's table, the running sum of the weights at this shard's first parent is
+   B = sum_k h_before_k W_k and the total is T = sum_k h_k W_k (exact integers, so the same as
+   summing parent by parent); every child c of the whole population draws its U as in
+   orc_resample_levels, and those with B <= U < B + (this shard's weight sum) land on one of
+   this shard's parents, found in the shard's own running sums.  info->R_new = this shard's
+   children; 6 for an empty histogram, 1 for an unknown kind or a missing h_before. */
 int orc_resample_shard(int L, int64_t R_target, const int64_t *h, int64_t R_prev, int64_t n,
                        const int32_t *level, int64_t parent_base, double beta_prev, double beta_new,
-                       uint32_t step, uint64_t seed, int kind, int32_t *counts_out, orc_resample_info *info)
+                       uint32_t step, uint64_t seed, int kind, const int64_t *h_before, int32_t *counts_out,
+                       orc_resample_info *info)
 {
-    if (kind != 0 && kind != 1) return 1;
+    if (kind != 0 && kind != 1 && kind != 2) return 1;
+    if (kind == 2 && !h_before) return 1;
     int N = L * L;
     double *w = (double *)calloc((size_t)N + 1, sizeof(double));
     double *tau = (double *)calloc((size_t)N + 1, sizeof(double));
@@ -510,7 +519,40 @@ int orc_resample_shard(int L, int64_t R_target, const int64_t *h, int64_t R_prev
     uint64_t *thr = (uint64_t *)calloc((size_t)N + 1, sizeof(uint64_t));
     int st = resample_tables(N, R_target, h, R_prev, beta_new - beta_prev, w, tau, fl, thr, info);
     int64_t R_new = 0;
-    for (int64_t j = 0; st == 0 && j < n; ++j) {
+    if (st == 0 && kind == 2) {
+        uint64_t T = 0, B = 0;
+        for (int k = 0; k <= N; ++k) {
+            if (h[k] == 0) continue;
+            const uint64_t Wk = (uint64_t)floor(w[k] * 4294967296.0);
+            T += (uint64_t)h[k] * Wk;
+            B += (uint64_t)h_before[k] * Wk;
+        }
+        uint64_t *C = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+        uint64_t run = B;
+        for (int64_t j = 0; j < n; ++j) {
+            run += (uint64_t)floor(w[level[j]] * 4294967296.0);
+            C[j] = run;
+            counts_out[j] = 0;
+        }
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        for (int64_t c = 0; n > 0 && c < R_target; ++c) {
+            uint32_t ctr[4] = {(uint32_t)c, 0, (uint32_t)STREAM_MULTINOMIAL << 28, step}, x[4];
+            orc_philox4x32_10(ctr, key, x);
+            const uint64_t X = ((uint64_t)x[1] << 32) | x[0];
+            const uint64_t U = (uint64_t)(((unsigned __int128)X * T) >> 64);
+            if (U < B || U >= C[n - 1]) continue;  /* a parent of another shard */
+            int64_t lo = 0, hi = n - 1;  /* first local j with C_j > U */
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (C[mid] > U) hi = mid;
+                else lo = mid + 1;
+            }
+            counts_out[lo] += 1;
+            R_new += 1;
+        }
+        free(C);
+    }
+    for (int64_t j = 0; st == 0 && kind != 2 && j < n; ++j) {
         int k = level[j];
         int64_t r = copy_number(kind, fl[k], thr[k], tau[k], seed, (uint32_t)(parent_base + j), step);
         counts_out[j] = (int32_t)r;

@@ -5,7 +5,8 @@ gloo ranks without a GPU, against the oracle's single population as the referenc
 
 The method's arithmetic stays in the oracle: simple sampling (init_replica), sweeps
 (sweep_replica), energies (energy_mag), the copy numbers of a shard's parents from the whole
-histogram (resample_shard, Sec. II Eqs. Q and taus) and the observables (observables_from_sums,
+histogram (resample_shard, Sec. II Eqs. Q and taus; multinomial draws also take the histogram
+of the shards before this one) and the observables (observables_from_sums,
 Sec. III).  This file only holds the population arrays, moves replicas, and merges family runs
 across shard boundaries."""
 from __future__ import annotations
@@ -71,6 +72,10 @@ class OracleShard:
         N1 = self.N + 1
         hist = a[:, :N1].sum(axis=0)
         R = int(a[:, N1].sum())
+        # levels of the parents in the shards before this one (rows in slot order): the
+        # multinomial draws need their weight sum
+        ends = np.cumsum(a[:, N1])
+        before = a[ends <= self.base, :N1].sum(axis=0)
         # family runs: walk the shards' run lists in slot order; a shard contributes its first
         # run, its inner runs (count, sum of squared lengths) and its last run, and a run that
         # continues across a boundary is joined
@@ -91,7 +96,7 @@ class OracleShard:
         s2 = sum(r[2] ** 2 if r[0] == "run" else r[2] for r in runs)
         sE = int((hist * (4 * np.arange(N1, dtype=np.int64) - 2 * self.N)).sum())
         sE2 = int((hist * (4 * np.arange(N1, dtype=np.int64) - 2 * self.N) ** 2).sum())
-        self.glob = {"hist": hist, "R": R,
+        self.glob = {"hist": hist, "R": R, "hist_before": before,
                      "isums": np.array([sE, sE2, a[:, N1 + 1].sum(), a[:, N1 + 2].sum(), f, s2], np.int64)}
 
     def resample(self, beta):
@@ -101,7 +106,8 @@ class OracleShard:
         lv, _, _, _ = self._arrays()
         self.step += 1
         st, counts, lnQ, R_new = oracle.resample_shard(self.L, self.R, g["hist"], g["R"], lv, self.base, self.beta,
-                                                       beta, self.step, self.seed, self.kind)
+                                                       beta, self.step, self.seed, self.kind,
+                                                       hist_before=g["hist_before"])
         assert st == 0
         self.counts = counts
         self.children = np.repeat(np.arange(self.n), counts)   # parent of each child, tree order

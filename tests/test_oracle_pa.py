@@ -266,10 +266,11 @@ def test_anneal_padded_rows_against_exact(L, update):
     assert abs(o["minus_betaF"] - lnZ) / N < 5e-3
 
 
-@pytest.mark.parametrize("kind", [oracle.NEAREST, oracle.POISSON])
+@pytest.mark.parametrize("kind", [oracle.NEAREST, oracle.POISSON, oracle.MULTINOMIAL])
 def test_resample_shard_equals_whole_population(kind):
     """Copy numbers drawn shard by shard (tables from the whole histogram, parents keyed by
-    their global index) are those of the whole population (Sec. II), for any split; ln Q_i
+    their global index; multinomial: the children whose draw falls in the shard's range of the
+    running weight sum) are those of the whole population (Sec. II), for any split; ln Q_i
     is the whole population's."""
     L, R = 8, 4000
     pa = oracle.PA(L, R, seed=21)
@@ -283,7 +284,9 @@ def test_resample_shard_equals_whole_population(kind):
     for cuts in ([0, R], [0, 1234, R], [0, 1, 2, 2999, R], [0, 1000, 1000, 2500, R]):
         parts, total = [], 0
         for a, b in zip(cuts[:-1], cuts[1:]):
-            s, c, q, n = oracle.resample_shard(L, R, hist, R, levels[a:b], a, 0.0, 0.35, 1, 21, kind)
+            before = np.bincount(levels[:a], minlength=L * L + 1)
+            s, c, q, n = oracle.resample_shard(L, R, hist, R, levels[a:b], a, 0.0, 0.35, 1, 21, kind,
+                                               hist_before=before)
             assert s == 0 and q == lnQ
             parts.append(c)
             total += n

@@ -118,6 +118,7 @@ def _compare(logs, ref):
     (2, 1, 301, oracle.NEAREST, [0.1, 0.25, 0.4, 0.55, 0.7]),
     (4, 1, 257, oracle.POISSON, [0.15, 0.3, 0.45, 0.6]),
     (2, 2, 203, oracle.NEAREST, [0.5, 1.0, 1.5, 2.0, 2.5]),   # harsh: a few families span whole shards
+    (2, 2, 211, oracle.MULTINOMIAL, [0.1, 0.3, 0.6, 1.0, 1.6]),
 ])
 def test_sharded_run_matches_one_population(world, per_rank, R, kind, betas):
     L, seed, theta = 8, 11, 2
