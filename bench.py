@@ -642,7 +642,8 @@ def run_sharded(args):
     K, W = args.steps, args.warmup
     assert W + K <= N_TEMPS - 1, "schedule has 300 steps"
     transport = LocalTransport() if world == 1 else DistTransport(shards_per_rank=k)
-    engines = gpu_shards(L, R, SEED, list(range(rank * k, (rank + 1) * k)), P, device=dev, stream=stream)
+    engines = gpu_shards(L, R, SEED, list(range(rank * k, (rank + 1) * k)), P, resample=args.resample,
+                         update=args.update, device=dev, stream=stream)
     run = ShardedRun(engines, P, transport)
     first = engines[rank * k]
     records = torch.zeros((K, (OBS_BYTES + 7) // 8), dtype=torch.int64, device=dev)
@@ -686,13 +687,15 @@ def run_sharded(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
                 "dtype": "u32", "data": "synthetic (simple sampling at beta=0, Philox4x32-10 seed 7)",
-                "config": {"workload": f"2D Ising PA L={L} R={R} theta={theta} beta=i/300 nearest",
+                "config": {"workload": f"2D Ising PA L={L} R={R} theta={theta} beta=i/300 {args.resample}"
+                                       + ("" if args.update == "metropolis" else f" {args.update}"),
                            "L": L, "R": R, "theta": theta, "temperatures": N_TEMPS,
                            "parallelism": f"one population sharded by slot ranges: {P} shards "
                                           f"({k} per rank, {world} rank(s))",
                            "beta_timed": [beta(W + 1), beta(W + K)],
                            "l2": "inputs larger than L2 (%.0f MB of spins per shard)" % (R / P * L * 2 * 4 * 2 / 1e6)},
-                "clocks": clk, "gpu_launches": (KERNELS_PER_STEP + 4) * K * k}
+                "clocks": clk,
+                "gpu_launches": (KERNELS_PER_STEP + 4 + (4 if args.resample == "multinomial" else 0)) * K * k}
         print(json.dumps(line), flush=True)
     for e in engines.values():
         e.close()

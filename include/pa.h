@@ -381,7 +381,11 @@ pa_status pa_export_spins(pa_ctx *ctx, long long first, long long count, unsigne
      pa_shard_adopt            once every range of this shard has arrived in its non-current
                                buffers: the new local size hi_t - lo_t and slot base lo_t; the
                                non-current buffers become current.
-   Nearest-integer and Poisson resampling (multinomial draws need every parent's weight); the
+   All three resampling kinds.  Multinomial: every shard draws all R children of the whole
+   population (their random numbers are keyed by the child index) and keeps those whose draw
+   falls in its parents' range of the whole population's running weight sum; the range starts
+   at the weight sum of the shards before it, formed by pa_shard_combine from their
+   histograms, so the copy numbers are those of the population held whole.  The
    schedule, feature, analysis and checkpoint calls need a whole population and return
    PA_ERR_STATE on a shard, as do the calls above out of order.  A shard's buffers hold its
    parents and its share of the next population, never all of its children, so its capacity
@@ -394,9 +398,10 @@ pa_status pa_export_spins(pa_ctx *ctx, long long first, long long count, unsigne
    0 <= slot_base, 1 <= R_local <= capacity and slot_base + R_local <= R.
    pa_shard_summary_len: int64 entries of one summary, N + 1 + 16 (0 for an unsupported L).
    pa_shard_summary: asynchronous; dev_out 8-byte aligned device memory.
-   pa_shard_combine: dev_all = n_shards summaries back to back in slot order (device);
-   asynchronous; an inconsistent set (histogram total != replicas, or none) sets the sticky
-   error PA_ERR_NUMERIC.
+   pa_shard_combine: dev_all = n_shards summaries back to back in slot order (device), one of
+   them this shard's (its rows before this shard's slot base are the shards before it);
+   asynchronous; an inconsistent set (histogram total != replicas, none, or no row of R_local
+   replicas starting at this shard's slot base) sets the sticky error PA_ERR_NUMERIC.
    pa_shard_copy: asynchronous; spins_dst 16-byte aligned (count replicas of
    pa_sizes.bytes_per_replica bytes), level/mag/fam_dst int32[count]; children outside
    [0, c_s) are not written.

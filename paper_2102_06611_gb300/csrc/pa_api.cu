@@ -278,7 +278,6 @@ pa_status pa_shard_init(const pa_config *cfg, long long slot_base, long long R_l
     local.R = local.capacity;
     pa_sizes sz;
     if (pa_query_sizes(&local, &sz) != PA_OK || cfg->R < 1 || cfg->R > 2147483647LL) return PA_ERR_INVALID_ARG;
-    if (cfg->resample != PA_RESAMPLE_NEAREST && cfg->resample != PA_RESAMPLE_POISSON) return PA_ERR_INVALID_ARG;
     if (slot_base < 0 || R_local < 1 || R_local > cfg->capacity || slot_base + R_local > cfg->R)
         return PA_ERR_INVALID_ARG;
     return create_ctx(cfg, buf, stream, slot_base, R_local, true, out);
@@ -297,6 +296,7 @@ pa_status pa_resample(pa_ctx *c, double beta_new)
     pa::ResampleArgs a{};
     a.sharded = c->shard ? 1 : 0;
     a.parent_base = (unsigned int)c->slot_base;
+    a.hist_before = at<int>(c, c->ws.hist_before);
     a.L = c->cfg.L;
     a.kind = c->cfg.resample;
     a.R_target = c->cfg.R;
@@ -847,7 +847,7 @@ pa_status pa_save(pa_ctx *c, void *host_buf, size_t n)
     char *p = static_cast<char *>(host_buf);
     CkptHeader h{};
     h.magic = kCkptMagic;
-    h.version = 2;
+    h.version = 3;
     h.cfg = c->cfg;
     h.step = c->step;
     h.R_cur = R;
@@ -888,7 +888,7 @@ pa_status pa_load(pa_ctx *c, const void *host_buf, size_t n)
     if (!host_buf || n < sizeof(CkptHeader)) return PA_ERR_INVALID_ARG;
     CkptHeader h;
     std::memcpy(&h, host_buf, sizeof(h));
-    if (h.magic != kCkptMagic || h.version != 2) return fail(c, PA_ERR_INVALID_ARG, "not a checkpoint");
+    if (h.magic != kCkptMagic || h.version != 3) return fail(c, PA_ERR_INVALID_ARG, "not a checkpoint");
     if (std::memcmp(&h.cfg, &c->cfg, sizeof(pa_config)) != 0)
         return fail(c, PA_ERR_INVALID_ARG, "checkpoint of a different configuration");
     if (h.R_cur < 1 || h.R_cur > c->cfg.capacity || h.R_prev < 0 || h.R_prev > c->cfg.capacity || h.n_log < 0 ||
@@ -961,7 +961,8 @@ pa_status pa_shard_combine(pa_ctx *c, const long long *dev_all, int n_shards)
         return fail(c, PA_ERR_INVALID_ARG, "bad shard summaries");
     if (!c->measured || c->combined) return fail(c, PA_ERR_STATE, "combine once after each measurement");
     DeviceGuard g(c->device);
-    cudaError_t e = pa::launch_shard_combine(c->st, at<int>(c, c->ws.hist), c->N, dev_all, n_shards, c->stream);
+    cudaError_t e = pa::launch_shard_combine(c->st, at<int>(c, c->ws.hist), at<int>(c, c->ws.hist_before), c->slot_base,
+                                             c->N, dev_all, n_shards, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "shard combine launch");
     c->combined = true;
     return PA_OK;

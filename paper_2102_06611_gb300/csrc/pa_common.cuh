@@ -218,6 +218,9 @@ struct DevState {
     unsigned long long mn_total;  // multinomial resampling: sum of the integer parent weights
     double sum_lnR;           // sum_k ln(R_{k-1} / R) over the resamplings so far
     long long R_glob;         // sharded population: the whole population's size (0 otherwise)
+    // multinomial resampling of a sharded population: the integer weight sum of the parents of
+    // the shards before this one (0 for a population held whole)
+    unsigned long long mn_base;
 };
 
 // Block-wide exclusive prefix sum (every thread gets its prefix; *total the block sum) and

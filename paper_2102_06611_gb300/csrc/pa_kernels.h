@@ -62,6 +62,7 @@ struct Workspace {
     size_t wint;        // uint64[N + 1]  multinomial: integer weights floor(w_k 2^32)
     size_t cdf;         // uint64[capacity] multinomial: running sum of the parents' weights
     size_t search;      // SearchState        temperature-step search
+    size_t hist_before; // int32[N + 1]   sharded population: level histogram of the shards before this one
     size_t total;
     long long nblk;     // blocks of the copy-count / copy kernels
 };
@@ -135,6 +136,9 @@ struct ResampleArgs {
     // used for ln Q_i) and local parent j has the global index parent_base + j
     int sharded;
     unsigned int parent_base;
+    // sharded multinomial resampling: level histogram of the parents of the shards before this
+    // one (their weight sum places this shard's parents in the whole population's running sum)
+    const int *hist_before;
     // the replica copy writes only children [win_lo, win_lo + win_n) (local child indices, in
     // tree order) to destination index child - win_lo; win_n = 0: every child, at its index
     long long win_lo, win_n;
@@ -168,7 +172,8 @@ cudaError_t launch_observables(const ObsArgs &a, cudaStream_t s);
 constexpr int kShardExtra = 16;  // int64 entries after the N + 1 histogram entries
 cudaError_t launch_shard_summary(const DevState *st, const int *hist, const int *fam, const long long *fampart,
                                  int N, long long *out, cudaStream_t s);
-cudaError_t launch_shard_combine(DevState *st, int *hist, int N, const long long *all, int n_shards, cudaStream_t s);
+cudaError_t launch_shard_combine(DevState *st, int *hist, int *hist_before, long long slot_base, int N,
+                                 const long long *all, int n_shards, cudaStream_t s);
 cudaError_t launch_set_population(DevState *st, long long R, cudaStream_t s);
 
 // Weighted average over independent runs' records (pa_analysis.cu).

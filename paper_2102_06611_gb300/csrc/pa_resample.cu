@@ -57,6 +57,7 @@ Workspace plan_workspace(int L, long long capacity)
     w.wint = off;     off = align256(off + nlev * 8);
     w.cdf = off;      off = align256(off + (size_t)capacity * 8);
     w.search = off;   off = align256(off + sizeof(SearchState));
+    w.hist_before = off; off = align256(off + (size_t)nlev * 4);
     w.total = off;
     w.nblk = nblk;
     return w;
@@ -182,15 +183,31 @@ __device__ __forceinline__ void table_body(const ResampleArgs &a)
     __syncthreads();
     const double S = sh_S;
     const double Rt = (double)a.R_target;
+    unsigned long long wt = 0, wb = 0;  // this thread's levels: sum h_k W_k, and over the shards before
     for (int k = k_lo; k < k_hi; ++k) {
-        if (a.hist[k] > 0) {
+        const int h = a.hist[k];
+        if (h > 0) {
             const double tau = __ddiv_rn(__dmul_rn(Rt, a.w[k]), S);
             const double f = floor(tau);
             a.tau[k] = tau;
             a.fl[k] = (int)f;
             a.thr[k] = (unsigned int)floor(__dmul_rn(__dsub_rn(tau, f), 4294967296.0));
-            if (a.kind == PA_RESAMPLE_MULTINOMIAL)
-                a.wint[k] = (unsigned long long)floor(__dmul_rn(a.w[k], 4294967296.0));
+            if (a.kind == PA_RESAMPLE_MULTINOMIAL) {
+                const unsigned long long W = (unsigned long long)floor(__dmul_rn(a.w[k], 4294967296.0));
+                a.wint[k] = W;
+                wt += (unsigned long long)h * W;
+                if (a.sharded) wb += (unsigned long long)a.hist_before[k] * W;
+            }
+        }
+    }
+    if (a.kind == PA_RESAMPLE_MULTINOMIAL && a.sharded) {
+        // a shard's parents take the range [B, B + its own weight sum) of the whole population's
+        // running weight sum, whose total is T (exact integers: every shard gets the same T)
+        wt = block_sum<unsigned long long, kTableThreads>(wt);
+        wb = block_sum<unsigned long long, kTableThreads>(wb);
+        if (tid == 0) {
+            st->mn_total = wt;
+            st->mn_base = wb;
         }
     }
     if (tid == 0) {
@@ -299,7 +316,9 @@ __device__ __forceinline__ void mn_wscan_body(const ResampleArgs &a)
     DevState *st = a.st;
     if (st->error) return;
     const long long nb = (st->R_prev + kCountBlockItems - 1) / kCountBlockItems;
-    long long carry = 0;
+    // a shard's running sum starts at the weight of the shards before it (k_table set it and
+    // the whole population's total)
+    long long carry = a.sharded ? (long long)st->mn_base : 0;
     for (long long start = 0; start < nb; start += 1024) {
         const long long b = start + threadIdx.x;
         const long long v = b < nb ? a.blocksum[b] : 0;
@@ -308,7 +327,7 @@ __device__ __forceinline__ void mn_wscan_body(const ResampleArgs &a)
         if (b < nb) a.blocksum[b] = carry + ex;
         carry += tot;
     }
-    if (threadIdx.x == 0) st->mn_total = (unsigned long long)carry;
+    if (threadIdx.x == 0 && !a.sharded) st->mn_total = (unsigned long long)carry;
 }
 
 __device__ __forceinline__ void mn_cdf_body(const ResampleArgs &a)
@@ -343,12 +362,17 @@ __device__ __forceinline__ void mn_draw_body(const ResampleArgs &a)
     const DevState *st = a.st;
     if (st->error) return;
     const long long Rp = st->R_prev;
+    if (Rp < 1) return;
     const unsigned long long T = st->mn_total;
+    // the range of the running weight sum held by these parents: [0, T) for a whole
+    // population; a shard draws every child and keeps those that land on its parents
+    const unsigned long long w_lo = a.sharded ? st->mn_base : 0ull, w_hi = a.cdf[Rp - 1];
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < a.R_target;
          c += (long long)gridDim.x * blockDim.x) {
         const uint4 x = philox(make_uint4((unsigned int)c, 0u, kStreamMultinomial << 28, a.step), a.k0, a.k1);
         const unsigned long long X = ((unsigned long long)x.y << 32) | x.x;
         const unsigned long long U = __umul64hi(X, T);
+        if (U < w_lo || U >= w_hi) continue;
         long long lo = 0, hi = Rp - 1;  // first j with C_j > U
         while (lo < hi) {
             const long long mid = lo + (hi - lo) / 2;
@@ -581,7 +605,17 @@ cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s)
     k_table<<<1, kTableThreads, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_counts<<<(unsigned int)a.nblk, kCountThreads, 0, s>>>(a);
+    const unsigned int nblk = (unsigned int)a.nblk;
+    if (a.kind == PA_RESAMPLE_MULTINOMIAL) {
+        k_mn_wsum<<<nblk, kCountThreads, 0, s>>>(a);
+        k_mn_wscan<<<1, 1024, 0, s>>>(a);
+        k_mn_cdf<<<nblk, kCountThreads, 0, s>>>(a);
+        const long long dblk = (a.R_target + kCountThreads - 1) / kCountThreads;
+        k_mn_draw<<<(unsigned int)(dblk < 4096 ? dblk : 4096), kCountThreads, 0, s>>>(a);
+        k_mn_csum<<<nblk, kCountThreads, 0, s>>>(a);
+    } else {
+        k_counts<<<nblk, kCountThreads, 0, s>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scan<<<1, kScanThreads, 0, s>>>(a);
     return cudaGetLastError();

@@ -100,27 +100,38 @@ __global__ void __launch_bounds__(kShardThreads) k_shard_summary(const DevState 
 
 // All shards' summaries (n_shards rows of N + 1 + kShardExtra, in slot order) into the
 // whole population's state: h_k summed, the exact sums summed, and the families merged where
-// one run of equal ids crosses shard boundaries (a run may span several shards).
-__global__ void __launch_bounds__(kShardThreads) k_shard_combine(DevState *st, int *hist, int N, const long long *all,
+// one run of equal ids crosses shard boundaries (a run may span several shards).  The rows
+// that end at or below this shard's first slot (slot_base) are the shards before it: their
+// summed histogram goes to hist_before (multinomial resampling places this shard's parents
+// in the whole population's running weight sum with it).
+__global__ void __launch_bounds__(kShardThreads) k_shard_combine(DevState *st, int *hist, int *hist_before,
+                                                                 long long slot_base, int N, const long long *all,
                                                                  int n_shards)
 {
     __shared__ long long part[kShardThreads / 32];
     const int V = N + 1 + kShardExtra;
     long long tot = 0;
     for (int k = threadIdx.x; k <= N; k += kShardThreads) {
-        long long h = 0;
-        for (int s = 0; s < n_shards; ++s) h += all[(size_t)s * V + k];
+        long long h = 0, hb = 0, end = 0;
+        for (int s = 0; s < n_shards; ++s) {
+            const long long v = all[(size_t)s * V + k];
+            end += all[(size_t)s * V + N + 1];
+            h += v;
+            if (end <= slot_base) hb += v;
+        }
         hist[k] = (int)h;
+        hist_before[k] = (int)hb;
         tot += h;
     }
     tot = block_sum_ll(tot, part);
     if (threadIdx.x != 0) return;
     long long R = 0, sums[7] = {0, 0, 0, 0, 0, 0, 0};
     long long f = 0, s2 = 0, open_id = 0, open_len = 0;
-    bool open = false;
+    bool open = false, own = false;
     for (int s = 0; s < n_shards; ++s) {
         const long long *x = all + (size_t)s * V + N + 1;
         const long long Rs = x[0];
+        if (R == slot_base && Rs == st->R_cur) own = true;  // this shard's own row
         R += Rs;
         for (int i = 0; i < 7; ++i) sums[i] += x[1 + i];
         if (Rs <= 0) continue;
@@ -159,7 +170,8 @@ __global__ void __launch_bounds__(kShardThreads) k_shard_combine(DevState *st, i
     st->c01 = sums[6];
     st->fam_count = f;
     st->fam_size2 = s2;
-    if (tot != R || R < 1) set_error(st, PA_ERR_NUMERIC);  // inconsistent summaries or no replicas
+    // inconsistent summaries (not in slot order, or without this shard's row) or no replicas
+    if (tot != R || R < 1 || !own) set_error(st, PA_ERR_NUMERIC);
 }
 
 __global__ void k_set_population(DevState *st, long long R)
@@ -176,9 +188,10 @@ cudaError_t launch_shard_summary(const DevState *st, const int *hist, const int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_shard_combine(DevState *st, int *hist, int N, const long long *all, int n_shards, cudaStream_t s)
+cudaError_t launch_shard_combine(DevState *st, int *hist, int *hist_before, long long slot_base, int N,
+                                 const long long *all, int n_shards, cudaStream_t s)
 {
-    k_shard_combine<<<1, kShardThreads, 0, s>>>(st, hist, N, all, n_shards);
+    k_shard_combine<<<1, kShardThreads, 0, s>>>(st, hist, hist_before, slot_base, N, all, n_shards);
     return cudaGetLastError();
 }
 

@@ -155,7 +155,8 @@ class GpuShard:
                  stream: torch.cuda.Stream | None = None):
         self.lib = _lib.lib()
         self.L, self.N, self.R = int(L), int(L) * int(L), int(R)
-        kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON}[resample]
+        kind = {"nearest": _lib.PA_RESAMPLE_NEAREST, "poisson": _lib.PA_RESAMPLE_POISSON,
+                "multinomial": _lib.PA_RESAMPLE_MULTINOMIAL}[resample]
         upd = {"metropolis": _lib.PA_UPDATE_METROPOLIS, "heatbath": _lib.PA_UPDATE_HEATBATH}[update]
         self.device = torch.device(device if device is not None else "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -70,11 +70,13 @@ def test_philox_rate_rejects_bad_arguments():
     assert lib.pa_philox_xor(1, 10, 4, None, None) == _lib.PA_ERR_INVALID_ARG
 
 
-def test_batches_take_register_sizes_only():
-    """Batches run the per-size register kernels: an even L without one is rejected."""
+def test_batches_take_every_even_size():
+    """Batches take every even 4 <= L <= 128 (register kernels or the shared-memory sweep) and
+    reject the sizes a single run rejects."""
     lib = _lib.lib()
     n = ctypes.c_size_t()
-    for L, st in ((16, _lib.PA_OK), (20, _lib.PA_ERR_INVALID_ARG), (100, _lib.PA_ERR_INVALID_ARG)):
+    for L, st in ((16, _lib.PA_OK), (20, _lib.PA_OK), (100, _lib.PA_OK), (6, _lib.PA_OK), (7, _lib.PA_ERR_INVALID_ARG),
+                  (2, _lib.PA_ERR_INVALID_ARG), (130, _lib.PA_ERR_INVALID_ARG)):
         d = (_lib.pa_run_desc * 1)(_lib.pa_run_desc(_lib.pa_config(L=L, resample=0, R=100, capacity=200, seed=1),
                                                     5, 1))
         assert lib.pa_batch_query_sizes(1, d, ctypes.byref(n)) == st

@@ -56,12 +56,15 @@ def _check_step(run, engines, whole, ref, with_counts):
     (10, 1999, 4, "poisson", "metropolis", [0.15, 0.3, 0.45, 0.6]),       # shared-memory sweep kernel
     (8, 777, 4, "nearest", "heatbath", [0.5, 1.0, 1.5, 2.0, 2.5, 3.0]),   # families span whole shards
     (32, 500, 1, "nearest", "metropolis", [0.2, 0.4]),                    # one shard
+    (16, 2503, 3, "multinomial", "metropolis", [0.1, 0.25, 0.4, 0.6, 0.9]),
+    (12, 1201, 4, "multinomial", "heatbath", [0.4, 0.9, 1.5, 2.2]),       # weights concentrated in few shards
 ])
 def test_sharded_population_equals_whole(L, R, P, kind, update, betas):
     seed, theta = 9, 3
     run, engines = _sharded(L, R, seed, P, kind, update)
     whole = _whole(L, R, seed, kind, update)
-    ref = oracle.PA(L, R, seed, kind=oracle.POISSON if kind == "poisson" else oracle.NEAREST,
+    ref = oracle.PA(L, R, seed, kind={"nearest": oracle.NEAREST, "poisson": oracle.POISSON,
+                                      "multinomial": oracle.MULTINOMIAL}[kind],
                     update=oracle.HEATBATH if update == "heatbath" else oracle.METROPOLIS)
     ref.init()
     _check_step(run, engines, whole, ref, False)
@@ -79,12 +82,13 @@ def test_sharded_population_equals_whole(L, R, P, kind, update, betas):
     whole.close()
 
 
-def test_sharded_full_size_L64_R1e6():
+@pytest.mark.parametrize("kind", ["nearest", "multinomial"])
+def test_sharded_full_size_L64_R1e6(kind):
     """The headline population (L = 64, R = 10^6) in 4 shards: three temperature steps equal
     the whole population's, hash for hash."""
     L, R, P, seed, theta = 64, 1_000_000, 4, 7, 10
-    run, engines = _sharded(L, R, seed, P, "nearest", "metropolis")
-    whole = _whole(L, R, seed, "nearest", "metropolis")
+    run, engines = _sharded(L, R, seed, P, kind, "metropolis")
+    whole = _whole(L, R, seed, kind, "metropolis")
     for i in (1, 2, 3):
         b = i / 300
         run.resample(b)
@@ -124,6 +128,19 @@ def test_shard_call_order_is_enforced():
     with pytest.raises(PAError):
         e.copy_children(0, 1, e.views(0, 1))   # likewise
     e.anneal_step(1)
+    e.close()
+
+
+def test_shard_combine_needs_its_own_row():
+    """Summaries without a row of this shard's size at its slot base (e.g. not in slot order)
+    set the sticky numeric error: the next synchronising call reports it."""
+    from paper_2102_06611_gb300 import PAError
+    from paper_2102_06611_gb300.shard import gpu_shards
+    e = gpu_shards(8, 100, 1, [1], 2)[1]         # slots [50, 100)
+    only = e.summary().unsqueeze(0)               # one row, starting at slot 0
+    e.combine(only)
+    with pytest.raises(PAError, match="NUMERIC"):
+        e.observables()
     e.close()
 
 
