@@ -66,7 +66,7 @@ RunLayout layout_run(const pa_run_desc &d, size_t off)
 }
 
 struct Tables {
-    size_t runs, state, ctl, order, item_start, records, end;
+    size_t runs, state, ctl, order, item_start, records, desc, end;
 };
 
 Tables layout_tables(int n)
@@ -79,6 +79,7 @@ Tables layout_tables(int n)
     t.order = off;      off = a256(off + sizeof(int) * (size_t)n);
     t.item_start = off; off = a256(off + sizeof(long long) * ((size_t)n + 1));
     t.records = off;    off = a256(off + sizeof(pa_obs) * (size_t)n);
+    t.desc = off;       off = a256(off + sizeof(pa::BatchDesc) * (size_t)n);
     t.end = off;
     return t;
 }
@@ -319,6 +320,7 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
     });
     pa::BatchCtl ctl{};
     ctl.n = n_runs;
+    ctl.desc = reinterpret_cast<pa::BatchDesc *>(b->arena + b->t.desc);
     for (int g = 0; g < pa::kBatchGroups; ++g) ctl.pbeg[g] = ctl.pend[g] = 0;
     for (int p = 0; p < n_runs; ++p) {
         const int g = pa::batch_group_of(runs[order[(size_t)p]].cfg.L);

@@ -20,7 +20,10 @@ namespace pa {
 // One persistent launch per lattice size present sweeps the active runs of that size (the
 // launches run concurrently on side streams): warps take work items (ipw consecutive
 // replica groups of one run) from the size's counter, largest items first (runs are
-// ordered by cost within a size).  The per-replica arithmetic
+// ordered by cost within a size); an item finds its run's sweep descriptor (BatchDesc,
+// written by k_b_items for this step) by a search of the item offsets and one load, which
+// measured 3 % faster at L = 32, 64 than following the run table and the run's state.  The
+// per-replica arithmetic
 // is exactly the single-run kernel's, with the histogram and sums going to the run's own
 // workspace: level counts aggregated over the warp, the seven exact sums once per item.
 // A warp's tie queue in the kernel's dynamic shared memory (inv: heatbath only).
@@ -38,8 +41,8 @@ __device__ __forceinline__ TieQueue<typename Geo<L>::W> tie_queue(const TqBuf &q
 }
 
 template <int L, bool HB>
-__device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
-                                            const TqBuf &qb, const unsigned int *rk0, const unsigned int *rk1,
+__device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spare, long long g, long long R, int lane,
+                                            int dry, const TqBuf &qb, const unsigned int *rk0, const unsigned int *rk1,
                                             unsigned long long *v)
 {
     using Gm = Geo<L>;
@@ -48,10 +51,9 @@ __device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spar
     const int q = lane & (G - 1);
     const int sub = lane / G;
     const int r0 = q * RPL;
-    const long long R = a.st->R_cur;
     const long long j = g * RPW + sub;
     const bool active = j < R;
-    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
+    const Accept<W> ac = make_accept<L>(a.T4, a.T8);
     W A[RPL], B[RPL];
     W *rep = reinterpret_cast<W *>(a.spins) + (size_t)(active ? j : 0) * (2 * L);
     if (active) load_rows<L>(rep, r0, A, B);
@@ -101,8 +103,8 @@ __device__ __forceinline__ void batch_group(const SweepArgs &a, const void *spar
 // Items of one group (ipw = 1) take this form, which nvcc compiles to faster code for them
 // than the general loop below (measured).
 template <int L, bool HB>
-__device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void *spare, long long g, int lane, int dry,
-                                                  const TqBuf &qb)
+__device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void *spare, long long g, long long R,
+                                                  int lane, int dry, const TqBuf &qb)
 {
     using Gm = Geo<L>;
     using W = typename Gm::W;
@@ -110,7 +112,6 @@ __device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void
     const int q = lane & (G - 1);
     const int sub = lane / G;
     const int r0 = q * RPL;
-    const long long R = a.st->R_cur;
     const long long j = g * RPW + sub;
     const bool active = j < R;
     unsigned int rk0[10], rk1[10];
@@ -119,7 +120,7 @@ __device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void
         rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
         rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
     }
-    const Accept<W> ac = make_accept<L>(a.st->T4, a.st->T8);
+    const Accept<W> ac = make_accept<L>(a.T4, a.T8);
     W A[RPL], B[RPL];
     W *rep = reinterpret_cast<W *>(a.spins) + (size_t)(active ? j : 0) * (2 * L);
     if (active) load_rows<L>(rep, r0, A, B);
@@ -173,12 +174,12 @@ __device__ __forceinline__ void batch_item_single(const SweepArgs &a, const void
 }
 
 template <int L, bool HB>
-__device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare, long long item, int ipw, int lane,
-                                           int dry, const TqBuf &qb)
+__device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare, long long item, int ipw, long long R,
+                                           int lane, int dry, const TqBuf &qb)
 {
     constexpr int RPW = Geo<L>::RPW;
     if (ipw == 1) {  // uniform over the warp
-        batch_item_single<L, HB>(a, spare, item, lane, dry, qb);
+        batch_item_single<L, HB>(a, spare, item, R, lane, dry, qb);
         return;
     }
     unsigned int rk0[10], rk1[10];
@@ -187,13 +188,12 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
         rk0[i] = a.k0 + (unsigned int)i * kPhiloxW0;
         rk1[i] = a.k1 + (unsigned int)i * kPhiloxW1;
     }
-    const long long R = a.st->R_cur;
     unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 1
     for (int k = 0; k < ipw; ++k) {
         const long long g = item * ipw + k;
         if (g * RPW >= R) break;  // uniform over the warp
-        batch_group<L, HB>(a, spare, g, lane, dry, qb, rk0, rk1, v);
+        batch_group<L, HB>(a, spare, g, R, lane, dry, qb, rk0, rk1, v);
     }
     // every replica of the item belongs to one run: one atomic per sum and item
 #pragma unroll
@@ -211,11 +211,11 @@ __device__ __forceinline__ void batch_item(const SweepArgs &a, const void *spare
 
 // The run's spin update decides the instantiation (uniform over the warp).
 template <int L>
-__device__ __forceinline__ void batch_item_update(const SweepArgs &a, const void *spare, long long item, int ipw,
-                                                  int lane, int dry, const TqBuf &qb)
+__device__ __forceinline__ void batch_item_update(const BatchDesc &d, long long item, int lane, int dry,
+                                                  const TqBuf &qb)
 {
-    if (a.update == PA_UPDATE_HEATBATH) batch_item<L, true>(a, spare, item, ipw, lane, dry, qb);
-    else batch_item<L, false>(a, spare, item, ipw, lane, dry, qb);
+    if (d.a.update == PA_UPDATE_HEATBATH) batch_item<L, true>(d.a, d.spare, item, d.ipw, d.R, lane, dry, qb);
+    else batch_item<L, false>(d.a, d.spare, item, d.ipw, d.R, lane, dry, qb);
 }
 
 // Tie queues of the kBatchWarps warps of a block of a kernel with TQ entries per warp:
@@ -247,26 +247,14 @@ __global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_swe
     const TqBuf qb = warp_tq(sh_tq, SweepStyle<L>::TQ_LEN);
     const long long end = ctl->end[g];
     const int p0 = ctl->pbeg[g], p1 = ctl->pend[g];
+    const BatchDesc *desc = ctl->desc;
     for (;;) {
         long long item = 0;
         if (lane == 0) item = (long long)atomicAdd(&ctl->next[g], 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= end) break;
-        int lo = p0, hi = p1;  // largest lo with item_start[lo] <= item
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (item_start[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int r = order[lo];
-        const BatchState s = state[r];
-        const BatchRun &run = runs[r];
-        SweepArgs a = run.sw[s.cur];
-        a.step = (unsigned int)s.step;
-        a.t0 = 0;
-        a.theta = run.theta;
-        const void *spare = run.sw[s.cur ^ 1].spins;
-        batch_item_update<L>(a, spare, item - item_start[lo], run.ipw, lane, dry, qb);
+        const BatchDesc d = desc[item_position(item_start, item, p0, p1)];
+        batch_item_update<L>(d, item - d.item0, lane, dry, qb);
     }
 }
 
@@ -312,36 +300,24 @@ __global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_swe
     extern __shared__ unsigned long long sh_tq[];
     const TqBuf qb = warp_tq(sh_tq, tq_len_max());
     const long long end = ctl->total_items;
+    const BatchDesc *desc = ctl->desc;
     for (;;) {
         long long item = 0;
         if (lane == 0) item = (long long)atomicAdd(&ctl->next_item, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= end) break;
-        int lo = 0, hi = n;  // largest lo with item_start[lo] <= item
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (item_start[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int r = order[lo];
-        const BatchState s = state[r];
-        const BatchRun &run = runs[r];
-        SweepArgs a = run.sw[s.cur];
-        a.step = (unsigned int)s.step;
-        a.t0 = 0;
-        a.theta = run.theta;
-        const void *spare = run.sw[s.cur ^ 1].spins;
-        const long long it = item - item_start[lo];
-        switch (run.L) {
-            case 4: batch_item_update<4>(a, spare, it, run.ipw, lane, dry, qb); break;
-            case 8: batch_item_update<8>(a, spare, it, run.ipw, lane, dry, qb); break;
-            case 12: batch_item_update<12>(a, spare, it, run.ipw, lane, dry, qb); break;
-            case 16: batch_item_update<16>(a, spare, it, run.ipw, lane, dry, qb); break;
-            case 24: batch_item_update<24>(a, spare, it, run.ipw, lane, dry, qb); break;
-            case 32: batch_item_update<32>(a, spare, it, run.ipw, lane, dry, qb); break;
-            case 48: batch_item_update<48>(a, spare, it, run.ipw, lane, dry, qb); break;
-            case 64: batch_item_update<64>(a, spare, it, run.ipw, lane, dry, qb); break;
-            case 128: batch_item_update<128>(a, spare, it, run.ipw, lane, dry, qb); break;
+        const BatchDesc d = desc[item_position(item_start, item, 0, n)];
+        const long long it = item - d.item0;
+        switch (d.L) {
+            case 4: batch_item_update<4>(d, it, lane, dry, qb); break;
+            case 8: batch_item_update<8>(d, it, lane, dry, qb); break;
+            case 12: batch_item_update<12>(d, it, lane, dry, qb); break;
+            case 16: batch_item_update<16>(d, it, lane, dry, qb); break;
+            case 24: batch_item_update<24>(d, it, lane, dry, qb); break;
+            case 32: batch_item_update<32>(d, it, lane, dry, qb); break;
+            case 48: batch_item_update<48>(d, it, lane, dry, qb); break;
+            case 64: batch_item_update<64>(d, it, lane, dry, qb); break;
+            case 128: batch_item_update<128>(d, it, lane, dry, qb); break;
             default: break;
         }
     }

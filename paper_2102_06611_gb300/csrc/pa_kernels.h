@@ -263,6 +263,29 @@ __host__ __device__ constexpr int batch_group_of(int L)
            : L == 64 ? 7 : L == 128 ? 8 : kBatchAnyGroup;
 }
 
+// What the sweep of one run needs for the current step, per order position, written by
+// k_b_items just before the sweep phase: a work item finds it with one load after the search
+// for its position (instead of a chain of loads through the run table and the run's state).
+struct BatchDesc {
+    SweepArgs a;          // current buffers; step, t0 = 0, theta and the thresholds T4 / T8 set
+    const void *spare;    // the other spin buffer (dry sweeps write there)
+    long long item0;      // the run's first work item
+    long long R;          // the run's population size R_i
+    int ipw, L;
+};
+
+// Order position of a work item: the largest p in [lo, hi) with item_start[p] <= item
+// (read-only loads: item_start does not change during the sweep phase).
+__device__ __forceinline__ int item_position(const long long *item_start, long long item, int lo, int hi)
+{
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(item_start + mid) <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 struct BatchCtl {
     unsigned long long next_item;  // work counter (unused by the per-size kernels)
     long long total_items;
@@ -273,6 +296,7 @@ struct BatchCtl {
     int pbeg[kBatchGroups], pend[kBatchGroups];
     long long begin[kBatchGroups], end[kBatchGroups];
     unsigned long long next[kBatchGroups];
+    BatchDesc *desc;      // per order position (n entries, in the batch's table memory)
 };
 
 // Host plan of the sweep phase: one persistent kernel per lattice size present, launched on

@@ -835,11 +835,12 @@ __global__ void __launch_bounds__(kCountThreads) k_b_copy(const BatchRun *runs, 
 __global__ void __launch_bounds__(1024) k_b_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl,
                                                   const int *order, long long *item_start, int n, int flip)
 {
-    // one thread per run position (chunks of 1024), work items per run, exclusive scan
+    // one thread per run position (chunks of 1024), work items per run, exclusive scan, and
+    // the position's sweep descriptor
     long long carry = 0;
     for (int base = 0; base < n; base += 1024) {
         const int p = base + (int)threadIdx.x;
-        long long items = 0;
+        long long items = 0, R = 0;
         if (p < n) {
             const int r = order[p];
             BatchState &s = state[r];
@@ -847,7 +848,7 @@ __global__ void __launch_bounds__(1024) k_b_items(const BatchRun *runs, BatchSta
                 const DevState *dst = runs[r].rs[s.cur].st;
                 if (!dst->error) {
                     if (flip) s.cur ^= 1;
-                    const long long R = dst->R_cur;
+                    R = dst->R_cur;
                     const long long per_item = (long long)runs[r].rpw * runs[r].ipw;
                     items = (R + per_item - 1) / per_item;
                 }
@@ -855,7 +856,25 @@ __global__ void __launch_bounds__(1024) k_b_items(const BatchRun *runs, BatchSta
         }
         long long tot;
         const long long ex = block_exclusive_scan<long long, 1024>(items, &tot);
-        if (p < n) item_start[p] = carry + ex;
+        if (p < n) {
+            item_start[p] = carry + ex;
+            const int r = order[p];
+            const BatchState s = state[r];
+            const BatchRun &run = runs[r];
+            BatchDesc d;
+            d.a = run.sw[s.cur];
+            d.a.step = (unsigned int)s.step;
+            d.a.t0 = 0;
+            d.a.theta = run.theta;
+            d.a.T4 = d.a.st->T4;
+            d.a.T8 = d.a.st->T8;
+            d.spare = run.sw[s.cur ^ 1].spins;
+            d.item0 = carry + ex;
+            d.R = R;
+            d.ipw = run.ipw;
+            d.L = run.L;
+            ctl->desc[p] = d;
+        }
         carry += tot;
     }
     __syncthreads();

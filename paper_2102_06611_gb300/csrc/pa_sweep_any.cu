@@ -473,32 +473,23 @@ __global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_b_sweep_a
     u64 *Sw = sh_dyn + (size_t)(threadIdx.x >> 5) * max_kw;
     const long long end = ctl->end[kBatchAnyGroup];
     const int p0 = ctl->pbeg[kBatchAnyGroup], p1 = ctl->pend[kBatchAnyGroup];
+    const BatchDesc *desc = ctl->desc;
     for (;;) {
         long long item = 0;
         if (lane == 0) item = (long long)atomicAdd(&ctl->next[kBatchAnyGroup], 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= end) break;
-        int lo = p0, hi = p1;  // largest lo with item_start[lo] <= item
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (item_start[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int r = order[lo];
-        const BatchState s = state[r];
-        const BatchRun &run = runs[r];
-        SweepArgs a = run.sw[s.cur];
-        a.step = (unsigned int)s.step;
-        a.t0 = 0;
-        a.theta = run.theta;
-        const int L = run.L;
+        const BatchDesc &d = desc[item_position(item_start, item, p0, p1)];
+        const SweepArgs a = d.a;
+        const int L = d.L;
         const AnyGeo g = any_geo(L);
-        const ClassThr th = class_thresholds(a.update, a.st->T4, a.st->T8);
-        const long long R = a.st->R_cur;
-        const long long it = item - item_start[lo];
+        const ClassThr th = class_thresholds(a.update, a.T4, a.T8);
+        const long long R = d.R;
+        const long long it = item - d.item0;
+        const int ipw = d.ipw;
         unsigned long long acc[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int k = 0; k < run.ipw; ++k) {
-            const long long base = (it * run.ipw + k) * g.k;
+        for (int k = 0; k < ipw; ++k) {
+            const long long base = (it * ipw + k) * g.k;
             if (base >= R) break;  // uniform over the warp
             unsigned long long v[7];
             const int level = any_pass<false>(a, g, L, R, base, Sw, th, v);
