@@ -80,6 +80,11 @@ def _parse_args():
                    help="batch workload: temperature steps to run (0: every run to completion)")
     p.add_argument("--no-sequential", action="store_true",
                    help="batch workload: skip the one-after-another comparison")
+    p.add_argument("--batch-homog", default=None, metavar="L,R,N",
+                   help="batch workload: N runs of one size L, R replicas each, 301 temperatures, theta 10, "
+                        "seeds 100.. (profiling; the default is the 64 mixed runs)")
+    p.add_argument("--batch-shape", default=None, metavar="UNIFIED,BPS,SCALE",
+                   help="batch workload: fix the sweep phase's shape instead of the autotuner's choice")
     return p.parse_args()
 
 
@@ -533,23 +538,35 @@ def run_reference(args):
     }), flush=True)
 
 
-def batch_eval(dev, steps: int = 0, sequential: bool = True) -> dict:
+def batch_eval(dev, steps: int = 0, sequential: bool = True, homog: str | None = None,
+               shape: str | None = None) -> dict:
     """64 independent runs (mixed L, R, temperature count, theta), batched (one graph replay per
     temperature step) and, for comparison, the same runs one after another through the
-    single-run API; `steps` > 0 bounds both to the first `steps` temperature steps."""
+    single-run API; `steps` > 0 bounds both to the first `steps` temperature steps.  `homog`
+    ("L,R,N") replaces the mix by N runs of one size; `shape` ("UNIFIED,BPS,SCALE") fixes the
+    sweep phase's shape."""
     import ctypes
 
     import torch
 
     from paper_2102_06611_gb300 import OBS_BYTES, PopulationAnnealing, pa_obs
-    from paper_2102_06611_gb300.batch import Batch, mixed_runs
+    from paper_2102_06611_gb300.batch import Batch, RunSpec, mixed_runs
 
-    specs = mixed_runs()
+    if homog:
+        hL, hR, hN = (int(x) for x in homog.split(","))
+        specs = [RunSpec(hL, hR, 100 + i, N_TEMPS, THETA) for i in range(hN)]
+        what = f"{hN} independent runs of L={hL}, R={hR}, {N_TEMPS} temperatures, theta {THETA}, seeds 100-{99 + hN}"
+    else:
+        specs = mixed_runs()
+        what = ("64 independent runs: L in {8..64}, R log-uniform [1e3, 2e5], 51-301 temperatures, "
+                "theta in {1, 5, 10}, seeds 100-163")
     n = len(specs)
     total_steps = max(s.n_temps for s in specs) - 1
     steps = min(total_steps, steps) if steps > 0 else total_steps
     words = (OBS_BYTES + 7) // 8
     b = Batch(specs, device=dev)
+    if shape:
+        b.set_shape(*(int(x) for x in shape.split(",")))
     rec = torch.zeros((steps, n, words), dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -591,9 +608,7 @@ def batch_eval(dev, steps: int = 0, sequential: bool = True) -> dict:
         torch.cuda.empty_cache()
     return {"value": attempts / (ms * 1e6), "unit": UNIT, "runs": n, "steps": steps,
             "steps_bounded": steps < total_steps, "batch_ms": ms, "attempts": attempts,
-            "workload": "64 independent runs: L in {8..64}, R log-uniform [1e3, 2e5], 51-301 temperatures, "
-                        "theta in {1, 5, 10}, seeds 100-163"
-                        + (f"; first {steps} temperature steps of every run" if steps < total_steps else ""),
+            "workload": what + (f"; first {steps} temperature steps of every run" if steps < total_steps else ""),
             "sequential_single_run": ({"value": attempts / (ms_seq * 1e6), "unit": UNIT, "ms": ms_seq}
                                       if ms_seq else None),
             "gain_over_sequential": ms_seq / ms if ms_seq else None, "tuning": tuning,
@@ -605,8 +620,9 @@ def run_batch(args):
     import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    r = batch_eval(dev, args.batch_steps, not args.no_sequential)
-    line = {"metric": METRIC + " (64 mixed runs, batched)", "value": r["value"], "unit": UNIT,
+    r = batch_eval(dev, args.batch_steps, not args.no_sequential, args.batch_homog, args.batch_shape)
+    what = f"{r['runs']} runs of one size" if args.batch_homog else "64 mixed runs"
+    line = {"metric": METRIC + f" ({what}, batched)", "value": r["value"], "unit": UNIT,
             "n_gpus": 1, "steps": r["steps"], "warmup": 0, "ms_per_step": r["batch_ms"] / r["steps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": {"workload": r["workload"], "runs": r["runs"]},
