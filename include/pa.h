@@ -164,7 +164,8 @@ pa_status pa_query_sizes(const pa_config *cfg, pa_sizes *out);
 pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_ctx **out);
 
 /* Step 2 (Sec. II, Eqs. Q, taus, resampling-factors): move from the current beta to
-   beta_new >= beta.  Uses the energies measured before resampling; builds the level
+   beta_new >= beta.  Uses the energies measured before resampling (a population resampled
+   again with no sweep in between is measured first); builds the level
    table in binary64 (w_k = exp(-dbeta (E_k - E_ref)), S = sum_k h_k w_k in ascending k,
    tau_hat_k = R w_k / S), draws copy numbers, prefix-sums them on the device and copies
    children to consecutive slots in parent order (tree order).  Advances the step index.

@@ -283,6 +283,8 @@ pa_status pa_shard_init(const pa_config *cfg, long long slot_base, long long R_l
     return create_ctx(cfg, buf, stream, slot_base, R_local, true, out);
 }
 
+static pa_status sweep_and_measure(pa_ctx *c, int theta);
+
 pa_status pa_resample(pa_ctx *c, double beta_new)
 {
     pa_status s = check_live(c);
@@ -292,6 +294,9 @@ pa_status pa_resample(pa_ctx *c, double beta_new)
     if (c->shard && (!c->combined || c->adopt_pending))
         return fail(c, PA_ERR_STATE, "a shard resamples after pa_shard_combine of the current measurement");
     DeviceGuard g(c->device);
+    // Eqs. Q and taus need the parents' histogram: measure a population resampled again
+    // without a sweep in between (a shard's histogram is the combined one)
+    if (!c->shard && !c->measured && (s = sweep_and_measure(c, 0)) != PA_OK) return s;
     const int nxt = c->cur ^ 1;
     pa::ResampleArgs a{};
     a.sharded = c->shard ? 1 : 0;
@@ -796,7 +801,8 @@ const char *ckpt_invalid(const pa_ctx *c, const CkptHeader &h, const char *p)
     const char *counts = ints(h.R_prev);
     for (long long j = 0; j < h.R_cur; ++j) {
         const int k = get(level, j), m = get(mag, j), f = get(fam, j), k0 = get(snap, j);
-        if (k < 0 || k > N || k0 < 0 || k0 > N) return "energy level out of range";
+        // the step-start levels are written by the step's first sweep and read only after it
+        if (k < 0 || k > N || (h.sweeps_in_step > 0 && (k0 < 0 || k0 > N))) return "energy level out of range";
         if (m < -N || m > N || ((m + N) & 1)) return "magnetisation out of range";
         if (f < 0 || f >= c->cfg.R || (j > 0 && f < get(fam, j - 1))) return "family ids out of range or order";
     }
