@@ -452,7 +452,8 @@ pa_status pa_copy_numbers_static(int L, long long R_target, long long R_prev, co
    one persistent launch per lattice size (concurrent); that choice, the persistent blocks per
    SM and the replica groups per work item are chosen at initialisation by timing candidate
    shapes on the batch's own data (dry sweeps into the spare buffers, which change no run's
-   state). */
+   state): the fastest, except that the fastest single-launch shape is kept when within 2 %
+   of it. */
 typedef struct pa_batch pa_batch;
 
 typedef struct {

@@ -421,6 +421,14 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
                 chosen = (int)c;
             }
         }
+        // the single persistent launch is kept unless another shape is more than 2 % faster
+        // (the dry-sweep timings of nearby shapes differ by about that much from call to call)
+        int best_unified = -1;
+        for (int c = 0; c < b->tuning.n_candidates; ++c)
+            if (shapes[(size_t)c].unified &&
+                (best_unified < 0 || b->tuning.cand[c].ms < b->tuning.cand[best_unified].ms))
+                best_unified = c;
+        if (best_unified >= 0 && b->tuning.cand[best_unified].ms <= 1.02f * best) chosen = best_unified;
         if (e == cudaSuccess) e = apply(shapes[(size_t)chosen]);
         b->tuning.chosen = chosen;
         b->tuning.chosen_grid = b->sweep_grid;

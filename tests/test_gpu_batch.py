@@ -61,7 +61,14 @@ def test_mixed_batch_matches_single_runs(shape):
         pa.close()
     t = b.tuning()
     if shape is None:
-        assert t["chosen"] in t["candidates"] and t["chosen"]["ms"] == min(c["ms"] for c in t["candidates"])
+        # the fastest shape, or the fastest single launch within 2 % of it
+        fastest = min(c["ms"] for c in t["candidates"])
+        best_one = min(c["ms"] for c in t["candidates"] if c["unified"])
+        assert t["chosen"] in t["candidates"]
+        if best_one <= 1.02 * fastest:
+            assert t["chosen"]["unified"] == 1 and t["chosen"]["ms"] == best_one
+        else:
+            assert t["chosen"]["ms"] == fastest
         assert {c["unified"] for c in t["candidates"]} == {0, 1}
 
 
