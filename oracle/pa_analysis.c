@@ -1,5 +1,5 @@
 /* Population analysis of population annealing (arXiv:2102.06611): the quantities the paper
- * uses to judge a run from its final population.  TEST INFRASTRUCTURE (oracle): plain
+ * uses to assess a run from its final population.  TEST INFRASTRUCTURE (oracle): plain
  * single-threaded C written from the paper's definitions, one step after another; it
  * shares no code with the CUDA path.
  *
