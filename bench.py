@@ -507,7 +507,7 @@ def _reference_worker(job):
 
 
 def run_reference(args):
-    """The CPU oracle as it stands, timed on the host: the reference arm of this build.  Every
+    """The CPU oracle as it stands, timed on the host: the benchmark's reference arm.  Every
     core of the process's affinity set runs its own oracle population (spawned processes, a
     replica-parallel split of the workload); the rate is the summed attempts over the slowest
     worker's time."""
