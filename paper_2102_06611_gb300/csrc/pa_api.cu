@@ -489,6 +489,8 @@ static pa_status launch_feature_pass(pa_ctx *c, int theta0, const float *norm)
     a.norm = norm;
     a.raw = at<float>(c, c->ws.feat);
     a.x = at<float>(c, c->ws.feat) + 16;
+    a.zeros = reinterpret_cast<unsigned long long *>(at<float>(c, c->ws.feat) + 32);
+    a.capacity = c->cfg.capacity;
     e = pa::launch_features(a, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "features launch");
     return PA_OK;

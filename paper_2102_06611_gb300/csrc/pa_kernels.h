@@ -54,7 +54,7 @@ struct Workspace {
     size_t occ_h;       // int32[N + 1]   their counts
     size_t occ_w;       // double[N + 1]  reweighting factors at a trial step
     size_t occ_t;       // double[N + 1]  overlap terms at a trial step
-    size_t feat;        // float[32]      learned-schedule features (raw, standardised)
+    size_t feat;        // float[32]      learned-schedule features (raw, standardised), then a uint64 zero count
     size_t snap;        // int32[capacity] levels at the start of the temperature step
     size_t ana_blk;     // int64[4 * kMaxAnaBlocks] analysis block sums
     size_t ana_sizes;   // int32[capacity + 1]     family-size histogram (entry 0: largest size)
@@ -225,6 +225,8 @@ struct FeatureArgs {
     const float *norm;   // x_mean[12], x_std[12], y_mean[2], y_std[2] (may be null: raw only)
     float *raw;          // 12 features
     float *x;            // 12 standardised features
+    unsigned long long *zeros;  // scratch: parents with zero copies (counted by many blocks)
+    long long capacity;  // replicas the buffers hold (grid of the zero count)
 };
 
 cudaError_t launch_features(const FeatureArgs &a, cudaStream_t s);

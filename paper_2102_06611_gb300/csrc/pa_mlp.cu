@@ -167,69 +167,75 @@ __global__ void k_mlp_round(const float *master, unsigned short *P)
 // fraction of parents with zero copies in the last resampling.
 __global__ void __launch_bounds__(1024) k_features(FeatureArgs a)
 {
-    __shared__ double red[32];
+    __shared__ double red[32][4];
+    __shared__ double tot[4];
     const int N = a.L * a.L, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    auto block_sum_d = [&](double v) -> double {
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid] = v;
+    // block sums of NV values, valid in every thread: a shuffle tree in each warp, then one
+    // over the 32 warp sums in warp 0 (binary64 work is slow here, so no serial loops)
+    auto block_sums = [&](double *v, int nv) {
+        for (int i = 0; i < nv; ++i)
+            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+        if (lane == 0)
+            for (int i = 0; i < nv; ++i) red[wid][i] = v[i];
         __syncthreads();
-        double t = 0.0;
-        if (tid == 0)
-            for (int i = 0; i < 32; ++i) t += red[i];
+        if (wid == 0)
+            for (int i = 0; i < nv; ++i) {
+                double t = red[lane][i];
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == 0) tot[i] = t;
+            }
         __syncthreads();
-        if (tid == 0) red[0] = t;
-        __syncthreads();
-        t = red[0];
-        __syncthreads();
-        return t;
+        for (int i = 0; i < nv; ++i) v[i] = tot[i];
+        __syncthreads();  // red and tot are reused by the next call
     };
-    // empty levels add exact zeros: skipping them leaves every sum unchanged and saves most
-    // of the (slow) binary64 work
-    double hsum = 0.0, esum = 0.0;
+    // empty levels add exact zeros: skipping them leaves every sum unchanged
+    double v1[2] = {0.0, 0.0};  // sum h, sum h E
     for (int k = tid; k <= N; k += 1024) {
-        if (a.hist[k] == 0) continue;
-        const double h = (double)a.hist[k];
-        hsum += h;
-        esum += h * (4.0 * k - 2.0 * N);
+        const int hk = a.hist[k];
+        if (hk == 0) continue;
+        const double h = (double)hk;
+        v1[0] += h;
+        v1[1] += h * (4.0 * k - 2.0 * N);
     }
-    const double R = block_sum_d(hsum);
-    const double mean = block_sum_d(esum) / R;
-    double s2 = 0.0, s3 = 0.0, s4 = 0.0;
+    block_sums(v1, 2);
+    const double R = v1[0], mean = v1[1] / R;
+    double v2[4] = {0.0, 0.0, 0.0, 0.0};  // central sums of order 2, 3, 4; sum of squared family sizes
     for (int k = tid; k <= N; k += 1024) {
-        if (a.hist[k] == 0) continue;
-        const double h = (double)a.hist[k];
+        const int hk = a.hist[k];
+        if (hk == 0) continue;
+        const double h = (double)hk;
         const double d = (4.0 * k - 2.0 * N) - mean;
-        s2 += h * d * d;
-        s3 += h * d * d * d;
-        s4 += h * d * d * d * d;
+        v2[0] += h * d * d;
+        v2[1] += h * d * d * d;
+        v2[2] += h * d * d * d * d;
     }
-    const double var = block_sum_d(s2) / R, m3 = block_sum_d(s3) / R, m4 = block_sum_d(s4) / R;
-    double f2 = 0.0;
-    for (int b = tid; b < kFamBlocks; b += 1024) f2 += (double)a.fampart[2 * b + 1];
-    const double size2 = block_sum_d(f2);
-    long long zeros = 0;  // an exact count (as the binary64 count was, below 2^53)
-    const long long R_prev = a.st->R_prev;
-    for (long long j = tid; j < R_prev; j += 1024) zeros += a.counts[j] == 0;
-    const double z = block_sum_d((double)zeros);
-    if (tid == 0) {
-        const double lnR = log(R);
-        double f[kIn];
-        f[0] = a.beta;
-        f[1] = log((double)a.L);
-        f[2] = lnR;
-        f[3] = mean / N;
-        f[4] = log(var / N + 1e-12);
-        f[5] = var > 0 ? m3 / pow(var, 1.5) : 0.0;
-        f[6] = var > 0 ? m4 / (var * var) - 3.0 : 0.0;
-        f[7] = a.dbeta_prev * a.L;
-        f[8] = a.theta_ratio_prev;
-        f[9] = a.alpha_prev;
-        f[10] = lnR > 0 ? log(size2 / R) / lnR : 0.0;
-        f[11] = R_prev > 0 ? z / (double)R_prev : 0.0;
-        for (int i = 0; i < kIn; ++i) {
-            a.raw[i] = (float)f[i];
-            a.x[i] = a.norm ? ((float)f[i] - a.norm[i]) / a.norm[kIn + i] : (float)f[i];
+    for (int b = tid; b < kFamBlocks; b += 1024) v2[3] += (double)a.fampart[2 * b + 1];
+    block_sums(v2, 4);
+    const double var = v2[0] / R, m3 = v2[1] / R, m4 = v2[2] / R, size2 = v2[3];
+    // one feature per warp (lane 0), so that the binary64 logarithms and powers run side by side
+    if (lane == 0 && wid < kIn) {
+        const long long R_prev = a.st->R_prev;
+        double f = 0.0;
+        switch (wid) {
+            case 0: f = a.beta; break;
+            case 1: f = log((double)a.L); break;
+            case 2: f = log(R); break;
+            case 3: f = mean / N; break;
+            case 4: f = log(var / N + 1e-12); break;
+            case 5: f = var > 0 ? m3 / pow(var, 1.5) : 0.0; break;
+            case 6: f = var > 0 ? m4 / (var * var) - 3.0 : 0.0; break;
+            case 7: f = a.dbeta_prev * a.L; break;
+            case 8: f = a.theta_ratio_prev; break;
+            case 9: f = a.alpha_prev; break;
+            case 10: {
+                const double lnR = log(R);
+                f = lnR > 0 ? log(size2 / R) / lnR : 0.0;
+                break;
+            }
+            default: f = R_prev > 0 ? (double)*a.zeros / (double)R_prev : 0.0; break;  // exact below 2^53
         }
+        a.raw[wid] = (float)f;
+        a.x[wid] = a.norm ? ((float)f - a.norm[wid]) / a.norm[kIn + wid] : (float)f;
     }
 }
 
@@ -263,8 +269,26 @@ __global__ void __launch_bounds__(kHid) k_mlp_propose(const unsigned short *P, c
     }
 }
 
+// Parents with zero copies in the last resampling, over many blocks (one block reading every
+// copy number took ~0.1 ms at R = 2e5): an exact integer count.
+__global__ void __launch_bounds__(256) k_count_zeros(const DevState *st, const int *counts, unsigned long long *out)
+{
+    const long long Rp = st->R_prev;
+    unsigned long long z = 0;
+    for (long long j = (long long)blockIdx.x * 256 + threadIdx.x; j < Rp; j += (long long)gridDim.x * 256)
+        z += counts[j] == 0;
+    z = block_sum<unsigned long long, 256>(z);
+    if (threadIdx.x == 0 && z) atomicAdd(out, z);
+}
+
 cudaError_t launch_features(const FeatureArgs &a, cudaStream_t s)
 {
+    cudaError_t e = cudaMemsetAsync(a.zeros, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const long long want = (a.capacity + 1023) / 1024;
+    const unsigned int blocks = (unsigned int)(want < 1 ? 1 : (want > 608 ? 608 : want));
+    k_count_zeros<<<blocks, 256, 0, s>>>(a.st, a.counts, a.zeros);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_features<<<1, 1024, 0, s>>>(a);
     return cudaGetLastError();
 }

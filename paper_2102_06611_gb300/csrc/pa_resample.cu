@@ -49,7 +49,7 @@ Workspace plan_workspace(int L, long long capacity)
     w.occ_h = off;    off = align256(off + nlev * 4);
     w.occ_w = off;    off = align256(off + nlev * 8);
     w.occ_t = off;    off = align256(off + nlev * 8);
-    w.feat = off;     off = align256(off + 32 * 4);
+    w.feat = off;     off = align256(off + 32 * 4 + 8);
     w.snap = off;     off = align256(off + (size_t)capacity * 4);
     w.ana_blk = off;  off = align256(off + (size_t)kMaxAnaBlocks * 4 * 8);
     w.ana_sizes = off; off = align256(off + ((size_t)capacity + 1) * 4);
