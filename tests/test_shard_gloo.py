@@ -26,7 +26,7 @@ def _free_port():
     return p
 
 
-def _rank_main(rank, world, port, outdir, L, R, seed, kind, betas, theta, per_rank):
+def _rank_main(rank, world, port, outdir, L, R, seed, kind, betas, theta, per_rank, update):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -46,7 +46,7 @@ def _rank_main(rank, world, port, outdir, L, R, seed, kind, betas, theta, per_ra
     engines = {}
     for s in range(rank * per_rank, (rank + 1) * per_rank):
         lo, hi = split(R, P, s)
-        engines[s] = OracleShard(L, R, seed, lo, hi - lo, cap, kind=kind)
+        engines[s] = OracleShard(L, R, seed, lo, hi - lo, cap, kind=kind, update=update)
     run = ShardedRun(engines, P, DistTransport(shards_per_rank=per_rank))
     log = []
 
@@ -68,8 +68,8 @@ def _rank_main(rank, world, port, outdir, L, R, seed, kind, betas, theta, per_ra
     dist.destroy_process_group()
 
 
-def _reference(L, R, seed, kind, betas, theta):
-    pa = oracle.PA(L, R, seed, kind=kind)
+def _reference(L, R, seed, kind, betas, theta, update=oracle.METROPOLIS):
+    pa = oracle.PA(L, R, seed, kind=kind, update=update)
     pa.init()
     out = []
 
@@ -87,12 +87,12 @@ def _reference(L, R, seed, kind, betas, theta):
     return out
 
 
-def _run_sharded(world, per_rank, L, R, seed, kind, betas, theta):
+def _run_sharded(world, per_rank, L, R, seed, kind, betas, theta, update=oracle.METROPOLIS):
     import pickle
 
     import torch.multiprocessing as mp
     with tempfile.TemporaryDirectory() as d:
-        mp.start_processes(_rank_main, args=(world, _free_port(), d, L, R, seed, kind, betas, theta, per_rank),
+        mp.start_processes(_rank_main, args=(world, _free_port(), d, L, R, seed, kind, betas, theta, per_rank, update),
                            nprocs=world, join=True, start_method="spawn")
         logs = [pickle.load(open(os.path.join(d, f"rank{r}.pkl"), "rb")) for r in range(world)]
     return logs
@@ -114,16 +114,17 @@ def _compare(logs, ref):
             assert np.array_equal(np.concatenate([shards[s]["counts"] for s in order]), want["counts"]), i
 
 
-@pytest.mark.parametrize("world,per_rank,R,kind,betas", [
-    (2, 1, 301, oracle.NEAREST, [0.1, 0.25, 0.4, 0.55, 0.7]),
-    (4, 1, 257, oracle.POISSON, [0.15, 0.3, 0.45, 0.6]),
-    (2, 2, 203, oracle.NEAREST, [0.5, 1.0, 1.5, 2.0, 2.5]),   # harsh: a few families span whole shards
-    (2, 2, 211, oracle.MULTINOMIAL, [0.1, 0.3, 0.6, 1.0, 1.6]),
+@pytest.mark.parametrize("world,per_rank,R,kind,betas,update", [
+    (2, 1, 301, oracle.NEAREST, [0.1, 0.25, 0.4, 0.55, 0.7], oracle.METROPOLIS),
+    (4, 1, 257, oracle.POISSON, [0.15, 0.3, 0.45, 0.6], oracle.METROPOLIS),
+    (2, 2, 203, oracle.NEAREST, [0.5, 1.0, 1.5, 2.0, 2.5], oracle.METROPOLIS),   # harsh: families span shards
+    (2, 2, 211, oracle.MULTINOMIAL, [0.1, 0.3, 0.6, 1.0, 1.6], oracle.METROPOLIS),
+    (2, 1, 233, oracle.POISSON, [0.2, 0.4, 0.7, 1.0], oracle.HEATBATH),
 ])
-def test_sharded_run_matches_one_population(world, per_rank, R, kind, betas):
+def test_sharded_run_matches_one_population(world, per_rank, R, kind, betas, update):
     L, seed, theta = 8, 11, 2
-    ref = _reference(L, R, seed, kind, betas, theta)
-    logs = _run_sharded(world, per_rank, L, R, seed, kind, betas, theta)
+    ref = _reference(L, R, seed, kind, betas, theta, update)
+    logs = _run_sharded(world, per_rank, L, R, seed, kind, betas, theta, update)
     _compare(logs, ref)
     if betas[-1] >= 2.0:  # the harsh schedule did collapse the families below the shard count
         assert ref[-1]["obs"]["families"] < world * per_rank
