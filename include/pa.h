@@ -166,7 +166,8 @@ pa_status pa_init(const pa_config *cfg, const pa_buffers *buf, void *stream, pa_
 /* Step 2 (Sec. II, Eqs. Q, taus, resampling-factors): move from the current beta to
    beta_new >= beta.  Uses the energies measured before resampling (a population resampled
    again with no sweep in between is measured first); builds the level
-   table in binary64 (w_k = exp(-dbeta (E_k - E_ref)), S = sum_k h_k w_k in ascending k,
+   table in binary64 (w_k = exp(-dbeta (E_k - E_ref)), S = sum_k h_k w_k over the occupied
+   levels in ascending k, in a fixed pairwise order: 1024 consecutive chunks, then a tree,
    tau_hat_k = R w_k / S), draws copy numbers, prefix-sums them on the device and copies
    children to consecutive slots in parent order (tree order).  Advances the step index.
    Asynchronous; a capacity overflow surfaces at the next synchronising call. */

@@ -380,9 +380,30 @@ typedef struct {
     int64_t R_new;     /* new population size */
 } orc_resample_info;
 
+/* A sum in a fixed pairwise order (the reading shared by every level sum of binary64 terms):
+   the n terms are cut into 1024 consecutive chunks of ceil(n / 1024) terms, each chunk is
+   summed from its first term, and the 1024 chunk sums are added as a binary tree
+   (x_j += x_{j + s} for s = 512, 256, ..., 1). */
+#define ORC_CHUNKS 1024
+
+static double pairwise_sum(const double *x, int n)
+{
+    double part[ORC_CHUNKS];
+    int c = (n + ORC_CHUNKS - 1) / ORC_CHUNKS;
+    for (int j = 0; j < ORC_CHUNKS; ++j) {
+        double s = 0.0;
+        for (int i = j * c; i < (j + 1) * c && i < n; ++i) s = s + x[i];
+        part[j] = s;
+    }
+    for (int s = ORC_CHUNKS / 2; s > 0; s /= 2)
+        for (int j = 0; j < s; ++j) part[j] = part[j] + part[j + s];
+    return part[0];
+}
+
 /* Step 2's tables from the level histogram h of the R_prev parents (Eqs. Q and taus):
    E_ref = the lowest occupied level's energy, w_k = exp(-dbeta (E_k - E_ref)) for occupied k,
-   S = sum over occupied k, ascending, of h_k w_k, ln Q_i = -dbeta E_ref + ln(S / R_prev),
+   S = the pairwise sum (above) of h_k w_k over the occupied k, ascending,
+   ln Q_i = -dbeta E_ref + ln(S / R_prev),
    tau_k = R_target w_k / S, fl_k = floor(tau_k), thr_k = floor((tau_k - fl_k) 2^32).
    Returns 6 (numeric) for an empty histogram, else 0. */
 static int resample_tables(int N, int64_t R_target, const int64_t *h, int64_t R_prev, double dbeta,
@@ -397,9 +418,12 @@ static int resample_tables(int N, int64_t R_target, const int64_t *h, int64_t R_
         int Ek = 4 * k - 2 * N;
         w[k] = orc_exp(-(dbeta * (double)(Ek - Eref)));
     }
-    double S = 0.0;
+    double *t = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    int n = 0;
     for (int k = 0; k <= N; ++k)
-        if (h[k] != 0) S = S + (double)h[k] * w[k];
+        if (h[k] != 0) t[n++] = (double)h[k] * w[k];
+    double S = pairwise_sum(t, n);
+    free(t);
     double lnQ = -(dbeta * (double)Eref) + log(S / (double)R_prev);
     for (int k = 0; k <= N; ++k) {
         if (h[k] == 0) continue;
@@ -773,22 +797,7 @@ void orc_pa_observables(const orc_pa *p, double *out, int64_t *isums)
  * [x_{m*}, x_{m*+1}) (x_0 = lo, x_64 = hi).  If no point ever qualifies, the step is the
  * smallest tried (the final hi).
  * ---------------------------------------------------------------------------------- */
-#define ORC_CHUNKS 1024
 #define ORC_SEARCH_K 64
-
-static double pairwise_sum(const double *x, int n)
-{
-    double part[ORC_CHUNKS];
-    int c = (n + ORC_CHUNKS - 1) / ORC_CHUNKS;
-    for (int j = 0; j < ORC_CHUNKS; ++j) {
-        double s = 0.0;
-        for (int i = j * c; i < (j + 1) * c && i < n; ++i) s = s + x[i];
-        part[j] = s;
-    }
-    for (int s = ORC_CHUNKS / 2; s > 0; s /= 2)
-        for (int j = 0; j < s; ++j) part[j] = part[j] + part[j + s];
-    return part[0];
-}
 
 double orc_overlap(int N, const int64_t *h, double dbeta)
 {

@@ -5,8 +5,9 @@
 //
 // Step 2 on the device, for the energies measured before resampling:
 //   k_table   one block: level histogram h_k -> E_ref (lowest occupied level),
-//             w_k = exp(-dbeta (E_k - E_ref)), S = sum over occupied k in ascending order
-//             of h_k w_k (one thread, fixed order), ln Q_i = -dbeta E_ref + ln(S / R_{i-1})
+//             w_k = exp(-dbeta (E_k - E_ref)), S = sum of h_k w_k over the occupied k in
+//             ascending order, in a fixed pairwise order (1024 consecutive chunks, each summed
+//             from its first term, then a binary tree), ln Q_i = -dbeta E_ref + ln(S / R_{i-1})
 //             (Eq. Q), tau_hat_k = R w_k / S (Eq. taus), floor(tau_hat_k) and the integer
 //             threshold floor(frac(tau_hat_k) 2^32).  All binary64 arithmetic uses explicitly
 //             rounded intrinsics; this file is also built with -fmad=false.
@@ -175,10 +176,23 @@ __device__ __forceinline__ void table_body(const ResampleArgs &a)
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        double S = 0.0;
-        for (int i = 0; i < nocc; ++i) S = __dadd_rn(S, sh_prod[i]);
-        sh_S = S;
+    // S in the fixed pairwise order: the nocc products (ascending levels) in 1024 consecutive
+    // chunks of ceil(nocc / 1024), thread t summing chunk t from its first term, then a binary
+    // tree over the chunk sums
+    {
+        static_assert(kTableThreads == 1024, "one chunk of the pairwise sum per thread");
+        __shared__ double sh_part[kTableThreads];
+        const int c = (nocc + kTableThreads - 1) / kTableThreads;
+        const int i0 = min(tid * c, nocc), i1 = min(i0 + c, nocc);
+        double part = 0.0;
+        for (int i = i0; i < i1; ++i) part = __dadd_rn(part, sh_prod[i]);
+        sh_part[tid] = part;
+        __syncthreads();
+        for (int s = kTableThreads / 2; s > 0; s >>= 1) {
+            if (tid < s) sh_part[tid] = __dadd_rn(sh_part[tid], sh_part[tid + s]);
+            __syncthreads();
+        }
+        if (tid == 0) sh_S = sh_part[0];
     }
     __syncthreads();
     const double S = sh_S;
