@@ -165,53 +165,141 @@ __global__ void k_mlp_round(const float *master, unsigned short *P)
 // beta, ln L, ln R, <E>/N, ln(Var(E)/N + 1e-12), skewness, excess kurtosis, dbeta_prev L,
 // theta_prev / theta0, alpha_prev, ln(rho_t)/ln(R) (rho_t = sum of squared family sizes / R),
 // fraction of parents with zero copies in the last resampling.
+// A 128-bit two's-complement integer as two 64-bit words (exact sums of high powers).
+struct I128 {
+    unsigned long long lo, hi;
+};
+__device__ __forceinline__ I128 i128_add(I128 x, I128 y)
+{
+    I128 r;
+    r.lo = x.lo + y.lo;
+    r.hi = x.hi + y.hi + (r.lo < x.lo ? 1ull : 0ull);
+    return r;
+}
+__device__ __forceinline__ I128 i128_from_prod(long long p, long long q)  // p * q, |p q| < 2^126
+{
+    const bool neg = (p < 0) != (q < 0);
+    const unsigned long long up = (unsigned long long)(p < 0 ? -p : p), uq = (unsigned long long)(q < 0 ? -q : q);
+    I128 r{up * uq, __umul64hi(up, uq)};
+    if (neg) {  // two's complement
+        r.lo = ~r.lo + 1ull;
+        r.hi = ~r.hi + (r.lo == 0ull ? 1ull : 0ull);
+    }
+    return r;
+}
+__device__ __forceinline__ double i128_to_double(I128 x)
+{
+    const bool neg = (long long)x.hi < 0;
+    if (neg) {
+        x.lo = ~x.lo + 1ull;
+        x.hi = ~x.hi + (x.lo == 0ull ? 1ull : 0ull);
+    }
+    const double v = __dadd_rn(__dmul_rn((double)x.hi, 18446744073709551616.0), (double)x.lo);
+    return neg ? -v : v;
+}
+__device__ __forceinline__ I128 i128_shfl_xor(I128 x, int o)
+{
+    return I128{__shfl_xor_sync(0xffffffffu, x.lo, o), __shfl_xor_sync(0xffffffffu, x.hi, o)};
+}
+
+// The moments come from exact integer sums over the occupied levels (this GPU's binary64
+// pipe is narrow, so the per-level work stays on the integer pipes): with the level index k,
+// h_k replicas and d = k - k_ref about the rounded mean level k_ref, the sums of h d^p for
+// p = 0 .. 4 are exact (128 bits for p = 3, 4), and the central moments of E = 4 k - 2 N
+// follow in binary64 from them.  The binary64 features then take one warp each.
 __global__ void __launch_bounds__(1024) k_features(FeatureArgs a)
 {
-    __shared__ double red[32][4];
-    __shared__ double tot[4];
+    constexpr int kW = 1024 / 32;
+    __shared__ long long sh_a[kW][2];
+    __shared__ long long sh_b[kW][3];
+    __shared__ I128 sh_c[kW][2];
+    __shared__ long long sh_kref;
+    __shared__ double sh_m[5];  // R, <E>, var, m3, m4
+    __shared__ double sh_size2;
     const int N = a.L * a.L, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    // block sums of NV values, valid in every thread: a shuffle tree in each warp, then one
-    // over the 32 warp sums in warp 0 (binary64 work is slow here, so no serial loops)
-    auto block_sums = [&](double *v, int nv) {
-        for (int i = 0; i < nv; ++i)
-            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-        if (lane == 0)
-            for (int i = 0; i < nv; ++i) red[wid][i] = v[i];
-        __syncthreads();
-        if (wid == 0)
-            for (int i = 0; i < nv; ++i) {
-                double t = red[lane][i];
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                if (lane == 0) tot[i] = t;
-            }
-        __syncthreads();
-        for (int i = 0; i < nv; ++i) v[i] = tot[i];
-        __syncthreads();  // red and tot are reused by the next call
-    };
-    // empty levels add exact zeros: skipping them leaves every sum unchanged
-    double v1[2] = {0.0, 0.0};  // sum h, sum h E
+
+    // pass 1: sum h, sum h k (exact) -> the rounded mean level
+    long long s0 = 0, s1 = 0;
     for (int k = tid; k <= N; k += 1024) {
-        const int hk = a.hist[k];
-        if (hk == 0) continue;
-        const double h = (double)hk;
-        v1[0] += h;
-        v1[1] += h * (4.0 * k - 2.0 * N);
+        const long long h = a.hist[k];
+        s0 += h;
+        s1 += h * k;
     }
-    block_sums(v1, 2);
-    const double R = v1[0], mean = v1[1] / R;
-    double v2[4] = {0.0, 0.0, 0.0, 0.0};  // central sums of order 2, 3, 4; sum of squared family sizes
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+        sh_a[wid][0] = s0;
+        sh_a[wid][1] = s1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long t0 = 0, t1 = 0;
+        for (int w = 0; w < kW; ++w) {
+            t0 += sh_a[w][0];
+            t1 += sh_a[w][1];
+        }
+        sh_a[0][0] = t0;
+        sh_kref = t0 > 0 ? (t1 + t0 / 2) / t0 : 0;
+    }
+    __syncthreads();
+    const long long R_int = sh_a[0][0], kref = sh_kref;
+
+    // pass 2: sum h d, h d^2 (64 bits), h d^3, h d^4 (128 bits), sum of squared family sizes
+    long long p1 = 0, p2 = 0, f2 = 0;
+    I128 p3{0, 0}, p4{0, 0};
     for (int k = tid; k <= N; k += 1024) {
-        const int hk = a.hist[k];
-        if (hk == 0) continue;
-        const double h = (double)hk;
-        const double d = (4.0 * k - 2.0 * N) - mean;
-        v2[0] += h * d * d;
-        v2[1] += h * d * d * d;
-        v2[2] += h * d * d * d * d;
+        const long long h = a.hist[k];
+        if (h == 0) continue;
+        const long long d = (long long)k - kref, hd2 = h * d * d;
+        p1 += h * d;
+        p2 += hd2;
+        p3 = i128_add(p3, i128_from_prod(hd2, d));
+        p4 = i128_add(p4, i128_from_prod(hd2, d * d));
     }
-    for (int b = tid; b < kFamBlocks; b += 1024) v2[3] += (double)a.fampart[2 * b + 1];
-    block_sums(v2, 4);
-    const double var = v2[0] / R, m3 = v2[1] / R, m4 = v2[2] / R, size2 = v2[3];
+    for (int b = tid; b < kFamBlocks; b += 1024) f2 += a.fampart[2 * b + 1];
+    for (int o = 16; o > 0; o >>= 1) {
+        p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+        p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+        f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+        p3 = i128_add(p3, i128_shfl_xor(p3, o));
+        p4 = i128_add(p4, i128_shfl_xor(p4, o));
+    }
+    if (lane == 0) {
+        sh_b[wid][0] = p1;
+        sh_b[wid][1] = p2;
+        sh_b[wid][2] = f2;
+        sh_c[wid][0] = p3;
+        sh_c[wid][1] = p4;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long t1 = 0, t2 = 0, tf = 0;
+        I128 t3{0, 0}, t4{0, 0};
+        for (int w = 0; w < kW; ++w) {
+            t1 += sh_b[w][0];
+            t2 += sh_b[w][1];
+            tf += sh_b[w][2];
+            t3 = i128_add(t3, sh_c[w][0]);
+            t4 = i128_add(t4, sh_c[w][1]);
+        }
+        // central moments in level units from the raw ones about k_ref, then of E = 4 k - 2 N
+        const double R = (double)R_int;
+        const double mu = (double)t1 / R, r2 = (double)t2 / R, r3 = i128_to_double(t3) / R,
+                     r4 = i128_to_double(t4) / R;
+        const double c2 = r2 - mu * mu;
+        const double c3 = r3 - 3.0 * mu * r2 + 2.0 * mu * mu * mu;
+        const double c4 = r4 - 4.0 * mu * r3 + 6.0 * mu * mu * r2 - 3.0 * mu * mu * mu * mu;
+        sh_m[0] = R;
+        sh_m[1] = 4.0 * ((double)kref + mu) - 2.0 * N;
+        sh_m[2] = 16.0 * c2;
+        sh_m[3] = 64.0 * c3;
+        sh_m[4] = 256.0 * c4;
+        sh_size2 = (double)tf;
+    }
+    __syncthreads();
+    const double R = sh_m[0], mean = sh_m[1], var = sh_m[2], m3 = sh_m[3], m4 = sh_m[4], size2 = sh_size2;
     // one feature per warp (lane 0), so that the binary64 logarithms and powers run side by side
     if (lane == 0 && wid < kIn) {
         const long long R_prev = a.st->R_prev;
@@ -222,7 +310,7 @@ __global__ void __launch_bounds__(1024) k_features(FeatureArgs a)
             case 2: f = log(R); break;
             case 3: f = mean / N; break;
             case 4: f = log(var / N + 1e-12); break;
-            case 5: f = var > 0 ? m3 / pow(var, 1.5) : 0.0; break;
+            case 5: f = var > 0 ? m3 / (var * sqrt(var)) : 0.0; break;
             case 6: f = var > 0 ? m4 / (var * var) - 3.0 : 0.0; break;
             case 7: f = a.dbeta_prev * a.L; break;
             case 8: f = a.theta_ratio_prev; break;
