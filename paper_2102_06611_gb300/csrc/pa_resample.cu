@@ -129,10 +129,13 @@ cudaError_t launch_setup(DevState *st, long long R, int *hist, int N, int update
 
 // ------------------------------------------------------------------------------ k_table
 constexpr int kTableThreads = 1024;
+// k_table's dynamic shared memory per level: the compacted products h_k w_k (binary64) and
+// the occupied levels' indices (int32)
+constexpr size_t kTableSmemPerLevel = sizeof(double) + sizeof(int);
 
 __device__ __forceinline__ void table_body(const ResampleArgs &a)
 {
-    extern __shared__ double sh_prod[];  // compacted h_k w_k, ascending k
+    extern __shared__ double sh_prod[];  // compacted h_k w_k, ascending k; then the levels k
     __shared__ int sh_kmin;
     __shared__ double sh_S;
     DevState *st = a.st;
@@ -159,21 +162,25 @@ __device__ __forceinline__ void table_body(const ResampleArgs &a)
     const double dbeta = __dsub_rn(a.beta_new, a.beta_prev);
     const int Eref = 4 * kmin - 2 * N;
 
-    // each thread owns a contiguous chunk of levels; compact the occupied ones in order
+    // each thread owns a contiguous chunk of levels; compact the occupied ones in order, then
+    // spread their binary64 work over the threads (position i of the occupied list: thread
+    // i mod 1024), since the occupied levels are few and adjacent
+    int *sh_occ = reinterpret_cast<int *>(sh_prod + nlev);
     const int chunk = (nlev + kTableThreads - 1) / kTableThreads;
     const int k_lo = min(tid * chunk, nlev), k_hi = min(k_lo + chunk, nlev);
     int occ = 0;
     for (int k = k_lo; k < k_hi; ++k) occ += a.hist[k] > 0;
     int nocc;
     int pos = block_exclusive_scan<int, kTableThreads>(occ, &nocc);
-    for (int k = k_lo; k < k_hi; ++k) {
-        const int h = a.hist[k];
-        if (h > 0) {
-            const int Ek = 4 * k - 2 * N;
-            const double wk = det_exp(-__dmul_rn(dbeta, (double)(Ek - Eref)));
-            a.w[k] = wk;
-            sh_prod[pos++] = __dmul_rn((double)h, wk);
-        }
+    for (int k = k_lo; k < k_hi; ++k)
+        if (a.hist[k] > 0) sh_occ[pos++] = k;
+    __syncthreads();
+    for (int i = tid; i < nocc; i += kTableThreads) {
+        const int k = sh_occ[i];
+        const int Ek = 4 * k - 2 * N;
+        const double wk = det_exp(-__dmul_rn(dbeta, (double)(Ek - Eref)));
+        a.w[k] = wk;
+        sh_prod[i] = __dmul_rn((double)a.hist[k], wk);
     }
     __syncthreads();
     // S in the fixed pairwise order: the nocc products (ascending levels) in 1024 consecutive
@@ -198,20 +205,20 @@ __device__ __forceinline__ void table_body(const ResampleArgs &a)
     const double S = sh_S;
     const double Rt = (double)a.R_target;
     unsigned long long wt = 0, wb = 0;  // this thread's levels: sum h_k W_k, and over the shards before
-    for (int k = k_lo; k < k_hi; ++k) {
+    for (int i = tid; i < nocc; i += kTableThreads) {
+        const int k = sh_occ[i];
         const int h = a.hist[k];
-        if (h > 0) {
-            const double tau = __ddiv_rn(__dmul_rn(Rt, a.w[k]), S);
-            const double f = floor(tau);
-            a.tau[k] = tau;
-            a.fl[k] = (int)f;
-            a.thr[k] = (unsigned int)floor(__dmul_rn(__dsub_rn(tau, f), 4294967296.0));
-            if (a.kind == PA_RESAMPLE_MULTINOMIAL) {
-                const unsigned long long W = (unsigned long long)floor(__dmul_rn(a.w[k], 4294967296.0));
-                a.wint[k] = W;
-                wt += (unsigned long long)h * W;
-                if (a.sharded) wb += (unsigned long long)a.hist_before[k] * W;
-            }
+        const double wk = a.w[k];
+        const double tau = __ddiv_rn(__dmul_rn(Rt, wk), S);
+        const double f = floor(tau);
+        a.tau[k] = tau;
+        a.fl[k] = (int)f;
+        a.thr[k] = (unsigned int)floor(__dmul_rn(__dsub_rn(tau, f), 4294967296.0));
+        if (a.kind == PA_RESAMPLE_MULTINOMIAL) {
+            const unsigned long long W = (unsigned long long)floor(__dmul_rn(wk, 4294967296.0));
+            a.wint[k] = W;
+            wt += (unsigned long long)h * W;
+            if (a.sharded) wb += (unsigned long long)a.hist_before[k] * W;
         }
     }
     if (a.kind == PA_RESAMPLE_MULTINOMIAL && a.sharded) {
@@ -562,11 +569,11 @@ static PerDeviceOnce table_smem_once;
 cudaError_t launch_resample(const ResampleArgs &a, cudaStream_t s)
 {
     const int nlev = a.L * a.L + 1;
-    const size_t smem = (size_t)nlev * sizeof(double);
+    const size_t smem = (size_t)nlev * kTableSmemPerLevel;
     {
         cudaError_t e = table_smem_once([] {
             return cudaFuncSetAttribute(k_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+                                        (int)((size_t)(128 * 128 + 1) * kTableSmemPerLevel));
         });
         if (e != cudaSuccess) return e;
     }
@@ -608,11 +615,11 @@ cudaError_t launch_copy(const ResampleArgs &a, cudaStream_t s)
 cudaError_t launch_copy_numbers(const ResampleArgs &a, cudaStream_t s)
 {
     const int nlev = a.L * a.L + 1;
-    const size_t smem = (size_t)nlev * sizeof(double);
+    const size_t smem = (size_t)nlev * kTableSmemPerLevel;
     {
         cudaError_t e = table_smem_once([] {
             return cudaFuncSetAttribute(k_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+                                        (int)((size_t)(128 * 128 + 1) * kTableSmemPerLevel));
         });
         if (e != cudaSuccess) return e;
     }
@@ -964,14 +971,14 @@ cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl 
         static PerDeviceOnce once;
         cudaError_t e = once([] {
             return cudaFuncSetAttribute(k_b_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)((size_t)(128 * 128 + 1) * sizeof(double)));
+                                        (int)((size_t)(128 * 128 + 1) * kTableSmemPerLevel));
         });
         if (e != cudaSuccess) return e;
     }
     cudaError_t e;
     k_b_begin<<<1, 256, 0, s>>>(runs, state, n);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_b_table<<<dim3(1, n), kTableThreads, (size_t)nlev_max * sizeof(double), s>>>(runs, state);
+    k_b_table<<<dim3(1, n), kTableThreads, (size_t)nlev_max * kTableSmemPerLevel, s>>>(runs, state);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_b_counts<<<dim3(nblk_max, n), kCountThreads, 0, s>>>(runs, state);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
