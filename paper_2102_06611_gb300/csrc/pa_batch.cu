@@ -406,7 +406,7 @@ pa_status pa_batch_init(int n_runs, const pa_run_desc *runs, void *arena, size_t
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                 e = pa::launch_batch_items(d_runs, d_state, d_ctl, d_order, d_items, n_runs, 0, b->user);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, b->user);
-                if (e == cudaSuccess) e = pa::launch_batch_sweep(d_runs, d_state, d_ctl, d_order, d_items, b->plan, b->user);
+                if (e == cudaSuccess) e = pa::launch_batch_sweep(d_ctl, d_items, b->plan, b->user);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, b->user);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);

@@ -237,8 +237,7 @@ __device__ __forceinline__ TqBuf warp_tq(unsigned long long *sh, int TQ)
 // take items from the group's counter; the item's run is found by bisection over the
 // group's order positions.
 template <int L>
-__global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl,
-                                                     const int *order, const long long *item_start)
+__global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_sweep(BatchCtl *ctl, const long long *item_start)
 {
     constexpr int g = batch_group_of(L);
     const int lane = threadIdx.x & 31;
@@ -259,8 +258,7 @@ __global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_swe
 }
 
 template <int L>
-static cudaError_t launch_b_sweep_t(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
-                                    const long long *item_start, int grid, cudaStream_t s)
+static cudaError_t launch_b_sweep_t(BatchCtl *ctl, const long long *item_start, int grid, cudaStream_t s)
 {
     constexpr size_t smem = tq_smem_bytes(SweepStyle<L>::TQ_LEN);
     static PerDeviceOnce once;
@@ -268,7 +266,7 @@ static cudaError_t launch_b_sweep_t(const BatchRun *runs, const BatchState *stat
         return cudaFuncSetAttribute(k_b_sweep<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (e != cudaSuccess) return e;
-    k_b_sweep<L><<<grid, PA_BATCH_THREADS, smem, s>>>(runs, state, ctl, order, item_start);
+    k_b_sweep<L><<<grid, PA_BATCH_THREADS, smem, s>>>(ctl, item_start);
     return cudaGetLastError();
 }
 
@@ -290,9 +288,7 @@ constexpr int tq_len_max()
     return m;
 }
 
-__global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_sweep_all(const BatchRun *runs,
-                                                                          const BatchState *state, BatchCtl *ctl,
-                                                                          const int *order,
+__global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_sweep_all(BatchCtl *ctl,
                                                                           const long long *item_start, int n)
 {
     const int lane = threadIdx.x & 31;
@@ -323,8 +319,7 @@ __global__ void __launch_bounds__(PA_BATCH_THREADS, PA_BATCH_MIN_BLOCKS) k_b_swe
     }
 }
 
-cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
-                               const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s)
+cudaError_t launch_batch_sweep(BatchCtl *ctl, const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s)
 {
     if (plan.unified) {
         constexpr size_t smem = tq_smem_bytes(tq_len_max());
@@ -333,11 +328,11 @@ cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, Ba
             return cudaFuncSetAttribute(k_b_sweep_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         });
         if (e != cudaSuccess) return e;
-        k_b_sweep_all<<<plan.grid_all, PA_BATCH_THREADS, smem, s>>>(runs, state, ctl, order, item_start, plan.n);
+        k_b_sweep_all<<<plan.grid_all, PA_BATCH_THREADS, smem, s>>>(ctl, item_start, plan.n);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // the runs without a register kernel (skipped above) by their own persistent sweep
         if (plan.any_present)
-            e = launch_batch_sweep_any(runs, state, ctl, order, item_start, plan.any_grid, plan.any_kw, s);
+            e = launch_batch_sweep_any(ctl, item_start, plan.any_grid, plan.any_kw, s);
         return e;
     }
     cudaError_t e = cudaEventRecord(plan.fork, s);
@@ -345,17 +340,17 @@ cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, Ba
         cudaStream_t t = plan.side[i];
         if ((e = cudaStreamWaitEvent(t, plan.fork, 0)) != cudaSuccess) break;
         switch (plan.L[i]) {
-            case 4: e = launch_b_sweep_t<4>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            case 8: e = launch_b_sweep_t<8>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            case 12: e = launch_b_sweep_t<12>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            case 16: e = launch_b_sweep_t<16>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            case 24: e = launch_b_sweep_t<24>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            case 32: e = launch_b_sweep_t<32>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            case 48: e = launch_b_sweep_t<48>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            case 64: e = launch_b_sweep_t<64>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
-            case 128: e = launch_b_sweep_t<128>(runs, state, ctl, order, item_start, plan.grid[i], t); break;
+            case 4: e = launch_b_sweep_t<4>(ctl, item_start, plan.grid[i], t); break;
+            case 8: e = launch_b_sweep_t<8>(ctl, item_start, plan.grid[i], t); break;
+            case 12: e = launch_b_sweep_t<12>(ctl, item_start, plan.grid[i], t); break;
+            case 16: e = launch_b_sweep_t<16>(ctl, item_start, plan.grid[i], t); break;
+            case 24: e = launch_b_sweep_t<24>(ctl, item_start, plan.grid[i], t); break;
+            case 32: e = launch_b_sweep_t<32>(ctl, item_start, plan.grid[i], t); break;
+            case 48: e = launch_b_sweep_t<48>(ctl, item_start, plan.grid[i], t); break;
+            case 64: e = launch_b_sweep_t<64>(ctl, item_start, plan.grid[i], t); break;
+            case 128: e = launch_b_sweep_t<128>(ctl, item_start, plan.grid[i], t); break;
             default:  // the group of every even L without a register kernel
-                e = launch_batch_sweep_any(runs, state, ctl, order, item_start, plan.grid[i], plan.any_kw, t);
+                e = launch_batch_sweep_any(ctl, item_start, plan.grid[i], plan.any_kw, t);
                 break;
         }
         if (e == cudaSuccess) e = cudaEventRecord(plan.join[i], t);

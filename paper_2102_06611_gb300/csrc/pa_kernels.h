@@ -320,8 +320,7 @@ cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl 
                               const BatchSweepPlan &plan, cudaStream_t s);
 cudaError_t launch_batch_items(const BatchRun *runs, BatchState *state, BatchCtl *ctl, const int *order,
                                long long *item_start, int n, int dry, cudaStream_t s);
-cudaError_t launch_batch_sweep(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
-                               const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s);
+cudaError_t launch_batch_sweep(BatchCtl *ctl, const long long *item_start, const BatchSweepPlan &plan, cudaStream_t s);
 cudaError_t launch_batch_record(const BatchRun *runs, BatchState *state, pa_obs *records, int n,
                                 cudaStream_t s);
 int batch_sweep_max_blocks_per_sm(int L);
@@ -335,8 +334,7 @@ int any_warp_words(int L);
 size_t batch_any_smem(int max_kw);
 cudaError_t prepare_batch_sweep_any(size_t smem);
 int batch_any_blocks_per_sm(size_t smem);
-cudaError_t launch_batch_sweep_any(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
-                                   const long long *item_start, int grid, int max_kw, cudaStream_t s);
+cudaError_t launch_batch_sweep_any(BatchCtl *ctl, const long long *item_start, int grid, int max_kw, cudaStream_t s);
 
 cudaError_t launch_hashes(int L, const void *spins, long long R, const DevState *st,
                           unsigned long long *out, cudaStream_t s);

@@ -997,7 +997,7 @@ cudaError_t launch_batch_step(const BatchRun *runs, BatchState *state, BatchCtl 
     if ((e = launch_batch_items(runs, state, ctl, order, item_start, n, 1, s)) != cudaSuccess) return e;
     k_b_zero<<<dim3((nlev_max + 1023) / 1024, n), 1024, 0, s>>>(runs, state);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_batch_sweep(runs, state, ctl, order, item_start, plan, s)) != cudaSuccess) return e;
+    if ((e = launch_batch_sweep(ctl, item_start, plan, s)) != cudaSuccess) return e;
     return launch_batch_record(runs, state, records, n, s);
 }
 

@@ -459,11 +459,10 @@ __global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_sweep_any
 
 // Batched form: a persistent sweep over the work items of the batch's runs without a register
 // kernel (group kBatchAnyGroup); an item is ipw warp passes (k replicas each) of one run, whose
-// thresholds come from its device state; levels go to the run's histogram, the seven sums once
-// per item.  Dry (autotuning) launches do nothing.
-__global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_b_sweep_any(const BatchRun *runs,
-                                                                                const BatchState *state,
-                                                                                BatchCtl *ctl, const int *order,
+// buffers, key and thresholds come from its sweep descriptor (BatchDesc, written for the step
+// by k_b_items); levels go to the run's histogram, the seven sums once per item.  Dry
+// (autotuning) launches do nothing.
+__global__ void __launch_bounds__(32 * kAnyWarps, PA_ANY_MIN_BLOCKS) k_b_sweep_any(BatchCtl *ctl,
                                                                                 const long long *item_start,
                                                                                 int max_kw)
 {
@@ -560,10 +559,9 @@ int batch_any_blocks_per_sm(size_t smem)
     return b > 0 ? b : 1;
 }
 
-cudaError_t launch_batch_sweep_any(const BatchRun *runs, const BatchState *state, BatchCtl *ctl, const int *order,
-                                   const long long *item_start, int grid, int max_kw, cudaStream_t s)
+cudaError_t launch_batch_sweep_any(BatchCtl *ctl, const long long *item_start, int grid, int max_kw, cudaStream_t s)
 {
-    k_b_sweep_any<<<grid, 32 * kAnyWarps, batch_any_smem(max_kw), s>>>(runs, state, ctl, order, item_start, max_kw);
+    k_b_sweep_any<<<grid, 32 * kAnyWarps, batch_any_smem(max_kw), s>>>(ctl, item_start, max_kw);
     return cudaGetLastError();
 }
 
