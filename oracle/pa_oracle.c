@@ -819,9 +819,11 @@ double orc_overlap(int N, const int64_t *h, double dbeta)
         t[i] = (double)h[k] * w;
     }
     double S = pairwise_sum(t, n);
+    /* p_k = h_k (1 / R), q_k = t_k (1 / S): the reciprocals formed once */
+    const double invR = 1.0 / (double)R, invS = 1.0 / S;
     for (int i = 0; i < n; ++i) {
-        double pk = (double)h[occ[i]] / (double)R;
-        double qk = t[i] / S;
+        double pk = (double)h[occ[i]] * invR;
+        double qk = t[i] * invS;
         m[i] = pk < qk ? pk : qk;
     }
     double alpha = pairwise_sum(m, n);

@@ -207,6 +207,7 @@ struct SearchBracket {
 struct SearchState {
     int nocc, kmin, done, source;
     long long R;
+    double invR;                         // 1 / R (binary64)
     double hi0, dbeta, alpha;
     SearchBracket br[2];                 // bracket of the last two rounds
     double alpha_pts[2][kSearchK];       // overlaps at the points of the last two rounds

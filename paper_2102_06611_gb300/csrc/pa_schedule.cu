@@ -4,7 +4,8 @@
 //
 // Overlap of the current energy distribution with its reweighting to beta + dbeta:
 //   alpha(dbeta) = sum over occupied levels k of min(p_k, q_k),
-//   p_k = h_k / R,  t_k = h_k w_k,  w_k = exp(-dbeta (E_k - E_ref)),  q_k = t_k / S,  S = sum t_k,
+//   p_k = h_k (1 / R),  t_k = h_k w_k,  w_k = exp(-dbeta (E_k - E_ref)),  q_k = t_k (1 / S),
+//   S = sum t_k (the reciprocals formed once: binary64 division is slow on this GPU),
 // with E_ref the lowest occupied level's energy.  Both sums run over the occupied levels in
 // ascending order in a fixed pairwise order: the n terms are cut into 1024 consecutive chunks
 // of c = ceil(n / 1024) terms, each chunk is summed from its first term, and the 1024 chunk
@@ -37,7 +38,7 @@ constexpr int kMaxChunk = (128 * 128 + 1 + kSearchThreads - 1) / kSearchThreads;
 struct Levels {
     const int *k, *h;
     int n, N, Eref;
-    double R;
+    double invR;  // 1 / R
 };
 
 // alpha(dbeta) for one block (all threads call; the result is valid in every thread).
@@ -60,12 +61,14 @@ __device__ double overlap_block(const Levels &lv, double dbeta, double *sh)
         if (tid < s) sh[tid] = __dadd_rn(sh[tid], sh[tid + s]);
         __syncthreads();
     }
-    const double S = sh[0];
+    if (tid == 0) sh[0] = __ddiv_rn(1.0, sh[0]);  // 1 / S
+    __syncthreads();
+    const double invS = sh[0];
     __syncthreads();
     part = 0.0;
     for (int i = i0; i < i1; ++i) {
-        const double pk = __ddiv_rn((double)lv.h[i], lv.R);
-        const double qk = __ddiv_rn(t[i - i0], S);
+        const double pk = __dmul_rn((double)lv.h[i], lv.invR);
+        const double qk = __dmul_rn(t[i - i0], invS);
         part = __dadd_rn(part, pk < qk ? pk : qk);
     }
     sh[tid] = part;
@@ -81,7 +84,7 @@ __device__ double overlap_block(const Levels &lv, double dbeta, double *sh)
 
 __device__ __forceinline__ Levels levels_of(const BisectArgs &a, const SearchState *ss)
 {
-    return Levels{a.occ_k, a.occ_h, ss->nocc, a.L * a.L, 4 * ss->kmin - 2 * a.L * a.L, (double)ss->R};
+    return Levels{a.occ_k, a.occ_h, ss->nocc, a.L * a.L, 4 * ss->kmin - 2 * a.L * a.L, ss->invR};
 }
 
 // The bracket after a round: m* = length of the qualifying prefix of the K - 1 points.
@@ -126,16 +129,21 @@ __global__ void __launch_bounds__(kSearchThreads) k_search_prep(BisectArgs a, Se
             ++pos;
         }
     }
-    if (tid == 0) sh_R = R;
+    __shared__ double sh_invR;
+    if (tid == 0) {
+        sh_R = R;
+        sh_invR = __ddiv_rn(1.0, (double)R);
+    }
     __syncthreads();
     if (tid == 0) {
         ss->nocc = nocc;
         ss->R = sh_R;
+        ss->invR = sh_invR;
         ss->kmin = nocc > 0 ? a.occ_k[0] : 0;
         sh_nocc = nocc;
     }
     __syncthreads();
-    const Levels lv{a.occ_k, a.occ_h, sh_nocc, N, nocc > 0 ? 4 * a.occ_k[0] - 2 * N : 0, (double)sh_R};
+    const Levels lv{a.occ_k, a.occ_h, sh_nocc, N, nocc > 0 ? 4 * a.occ_k[0] - 2 * N : 0, sh_invR};
 
     double hi = __dsub_rn(a.beta_final, a.beta);
     if (a.dbeta_max < hi) hi = a.dbeta_max;
