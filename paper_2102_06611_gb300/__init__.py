@@ -24,7 +24,7 @@ __all__ = ["PopulationAnnealing", "PAError", "pa_obs", "default_capacity", "SUPP
            "weighted_average"]
 
 SUPPORTED_L = tuple(range(4, 129, 2))              # even 4 <= L <= 128
-REGISTER_L = (4, 8, 12, 16, 24, 32, 48, 64, 128)   # sizes with register-resident sweep kernels
+REGISTER_L = (4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128)   # sizes with register-resident sweep kernels
 OBS_BYTES = ctypes.sizeof(pa_obs)
 
 

@@ -50,8 +50,9 @@ namespace pa {
 // ------------------------------------------------------------------------------------
 __host__ __device__ constexpr int rows_per_lane(int L)
 {
-    return L == 4 ? 4 : L == 8 ? 8 : L == 12 ? 12 : L == 16 ? PA_RPL_16 : L == 24 ? PA_RPL_24 : L == 32 ? PA_RPL_32
-           : L == 48 ? PA_RPL_48 : L == 64 ? PA_RPL_64 : PA_RPL_128;
+    return L == 4 ? 4 : L == 8 ? 8 : L == 12 ? 12 : L == 16 ? PA_RPL_16 : L == 20 ? 10 : L == 24 ? PA_RPL_24
+           : L == 32 ? PA_RPL_32 : L == 40 ? 5 : L == 48 ? PA_RPL_48 : L == 64 ? PA_RPL_64 : L == 80 ? 5
+           : L == 96 ? 6 : PA_RPL_128;
 }
 
 __host__ __device__ constexpr int padded_half(int L)

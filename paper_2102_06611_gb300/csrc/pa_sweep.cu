@@ -9,7 +9,9 @@ namespace pa {
 bool sweep_has_template(int L)
 {
     switch (L) {
-        case 4: case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 128: return true;
+        case 4: case 8: case 12: case 16: case 20: case 24: case 32: case 40: case 48: case 64: case 80: case 96:
+        case 128:
+            return true;
         default: return false;
     }
 }
@@ -26,10 +28,14 @@ cudaError_t launch_sweep(int L, bool init, const SweepArgs &a, int num_sms, cuda
         PA_SWEEP_CASE(8)
         PA_SWEEP_CASE(12)
         PA_SWEEP_CASE(16)
+        PA_SWEEP_CASE(20)
         PA_SWEEP_CASE(24)
         PA_SWEEP_CASE(32)
+        PA_SWEEP_CASE(40)
         PA_SWEEP_CASE(48)
         PA_SWEEP_CASE(64)
+        PA_SWEEP_CASE(80)
+        PA_SWEEP_CASE(96)
         PA_SWEEP_CASE(128)
         default:
             return cudaErrorInvalidValue;

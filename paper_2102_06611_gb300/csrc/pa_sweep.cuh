@@ -22,7 +22,7 @@
 
 // Block shape of the sweep kernel, set to the measured best: one block per SM of 512 threads
 // (16 warps, at most 128 registers), except L = 128: 384 threads (12 warps, at most 170
-// registers).  Measured at beta = 0.2 / 0.44 / 0.8 against two blocks of 256 per SM (one at
+// registers; also taken by the other 64-bit-word sizes, 80 and 96, which spill at 128).  Measured at beta = 0.2 / 0.44 / 0.8 against two blocks of 256 per SM (one at
 // L = 8 and 128), the previous shape: +3 to +7 % at every size (L = 64 +4.5 %, L = 16 +7 %),
 // L = 128 +5.7 % with 384 threads (+1 % with 512); 320, 448 and 640 threads and two blocks of
 // 192 or three of 128 were slower.  PA_SWEEP_THREADS / PA_SWEEP_MIN_BLOCKS override the shape
@@ -30,7 +30,7 @@
 #ifdef PA_SWEEP_THREADS
 constexpr int sweep_threads(int) { return PA_SWEEP_THREADS; }
 #else
-constexpr int sweep_threads(int L) { return L == 128 ? 384 : 512; }
+constexpr int sweep_threads(int L) { return L >= 80 ? 384 : 512; }
 #endif
 #ifndef PA_SWEEP_MIN_BLOCKS
 #define PA_SWEEP_MIN_BLOCKS 1

@@ -1,7 +1,8 @@
 // pa_sweep_any.cu -- step 1 (simple-sampling initialisation) and step 3 (theta checkerboard
 // sweeps, Metropolis or heatbath) of population annealing (arXiv:2102.06611, Sec. II) for
 // any even lattice size 4 <= L <= 128 that has no kernel template of its own (the sizes
-// 4, 8, 12, 16, 24, 32, 48, 64 and 128 run the register-resident kernels of pa_sweep.cuh).
+// 4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96 and 128 run the register-resident kernels of
+// pa_sweep.cuh; batches run the others through the batched form below).
 //
 // A warp stages its replicas in shared memory in their HBM layout (per row the even-column
 // half-row word, then the odd-column one, bit p = column 2p or 2p + 1, widened to 64 bits).

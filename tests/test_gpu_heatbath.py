@@ -33,6 +33,10 @@ RUNS = [
     (48, 120, "nearest", [0.4, 0.8], 2),
     (64, 400, "nearest", [0.45, 0.7, 0.95], 3),
     (128, 150, "nearest", [0.5, 1.0], 2),
+    (20, 300, "nearest", [0.3, 0.6, 1.0], 2),
+    (40, 150, "poisson", [0.3, 0.6], 2),
+    (80, 50, "nearest", [0.44, 0.9], 2),
+    (96, 40, "nearest", [0.44, 1.0], 2),
 ]
 
 

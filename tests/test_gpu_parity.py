@@ -24,8 +24,8 @@ def _pa(*a, **k):
 
 
 # ------------------------------------------------------------------------------ init
-@pytest.mark.parametrize("L,R", [(4, 300), (8, 300), (12, 200), (16, 200), (24, 100), (32, 100),
-                                 (48, 50), (64, 40), (128, 9)])
+@pytest.mark.parametrize("L,R", [(4, 300), (8, 300), (12, 200), (16, 200), (20, 150), (24, 100), (32, 100),
+                                 (40, 60), (48, 50), (64, 40), (80, 20), (96, 15), (128, 9)])
 def test_init_parity(L, R):
     gpu = _pa(L, R, seed=11)
     ref = oracle.PA(L, R, seed=11)
@@ -34,14 +34,16 @@ def test_init_parity(L, R):
     assert_obs_close(gpu.observables(), ref.observables(), "init")
 
 
-@pytest.mark.parametrize("L", [4, 8, 12, 24, 64, 128])
+@pytest.mark.parametrize("L", [4, 8, 12, 20, 24, 40, 64, 80, 96, 128])
 def test_sweep_at_beta_zero_inverts(L):
     """At beta = 0 every proposal is accepted: one sweep maps s -> -s (Sec. IV)."""
     gpu = _pa(L, 17, seed=2)
     before = gpu.export_spins()
     gpu.anneal_step(1)
     after = gpu.export_spins()
-    mask = np.uint32((1 << L) - 1) if L < 32 else np.uint32(0xFFFFFFFF)
+    # word w of a row holds columns 32 w .. 32 w + 31 (bits beyond L stay clear)
+    nw = before.shape[-1]
+    mask = np.array([(1 << min(32, L - 32 * w)) - 1 for w in range(nw)], dtype=np.uint64).astype(np.uint32)
     assert np.array_equal(after, (~before) & mask)
 
 
@@ -59,6 +61,10 @@ RUNS = [
     (48, 100, "nearest", 5, 2),
     (64, 150, "nearest", 5, 2),
     (128, 12, "nearest", 3, 1),
+    (20, 400, "nearest", 11, 3),     # the register kernels of the sizes 20, 40, 80, 96
+    (40, 200, "poisson", 8, 3),
+    (80, 60, "nearest", 5, 2),
+    (96, 40, "nearest", 4, 2),
 ]
 
 
