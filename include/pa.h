@@ -73,9 +73,10 @@ typedef enum {
 } pa_update_kind;
 
 /* Run configuration.  L even, 4 <= L <= 128 (periodic L x L lattice).  The sizes 4, 8, 12,
-   16, 24, 32, 48, 64 and 128 run kernels that hold a replica in registers; every other even
-   L runs a kernel that stages it in shared memory (same random numbers and decisions,
-   slower).  Batches (pa_batch_create) take the nine register sizes only.
+   16, 20, 24, 32, 40, 48, 64, 80, 96 and 128 run kernels that hold a replica in registers;
+   every other even L runs a kernel that stages it in shared memory (same random numbers and
+   decisions, slower).  Batches (pa_batch_init) take every even L as well (register kernels
+   for 4, 8, 12, 16, 24, 32, 48, 64 and 128, the shared-memory form for the others).
    1 <= R <= capacity <= 2^31 - 1.  beta_0 is always 0 (simple sampling, Sec. II). */
 typedef struct {
     int L;
