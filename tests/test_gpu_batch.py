@@ -197,8 +197,9 @@ ANY_L_MIX = [
 
 @pytest.mark.parametrize("shape", [None, (1, 1, 1)])
 def test_batch_with_every_even_L_matches_single_runs(shape):
-    """Runs of even L without a register kernel (the shared-memory sweep, batched) beside
-    register sizes in one batch, each bit-identical to its single run."""
+    """Runs of even L without a batched register kernel (the shared-memory sweep, batched)
+    beside register sizes in one batch, each bit-identical to its single run (which, at L =
+    20 and 40, runs the single-run register kernel: two kernels, one result)."""
     from paper_2102_06611_gb300.batch import Batch, RunSpec
     specs = [RunSpec(L, R, seed, nT, th, kind, update=u) for (L, R, seed, nT, th, kind, u) in ANY_L_MIX]
     b = Batch(specs)
